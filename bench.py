@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""PBAT benchmark: states/s of exact two-terminal reliability on one GB300.
+
+A step is one pass of the whole enumeration (prefix split, exact monotone
+prune, Gray walk, per-state PLSA connectivity, exact accumulation of R,
+N_k and dR/dp, fixed-order reduction) over the 2^m states of the workload,
+with the tables already resident on the device.  ``value`` is 2^m / device
+time of the fused R + N_k + dR/dp step (CUDA events on the launch stream,
+L2 flushed by a 256 MiB write between steps, outside the events);
+``r_only`` is the same for the R + N_k kernel, the plain GPU BAT it is
+compared with.  ``e2e`` times the public C-ABI call with host buffers
+(planning, table build, host -> device and device -> host copies included).
+
+--impl reference times the CPU oracle (test infrastructure: plain brute
+force, long double) on the host cores over a bounded sample of the same
+workload and reports it in the same metric.
+
+Multi-GPU: one process per GPU (torchrun); the path does not shard across
+GPUs here, so every rank runs an independent replica and ``value`` is the
+states of all replicas over the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "states/s (2^m/time) for R and R+∇R vs plain GPU BAT, rel err ≤1e-12"
+WORKLOADS = {
+    "grid-3x6": synth.workload_grid_3x6,
+    "random-undirected-n8-m16": synth.workload_small_random,
+    "random-directed-n20-m34": synth.workload_directed_20_34,
+    "random-undirected-n24-m40": synth.workload_random_24_40,
+}
+DEFAULT_WORKLOAD = "grid-3x6"
+
+# Warp instructions executed per state by the fused enumeration kernel on
+# each workload, from ncu (inst_executed of the launch / 2^m); the per-unit
+# figure of the issue-rate roofline.  Source: profiles/frontier_fused_grid3x6.md
+INST_PER_STATE = {}
+# DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum),
+# same capture; None until measured for the current kernel.
+DRAM_BYTES_PER_LAUNCH = {}
+
+SM_COUNT = 152
+ISSUE_PER_SM_CLK = 4          # warp instructions per clock per SM (4 schedulers)
+SM_MAX_MHZ = 2070.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def _oracle_division(args):
+    name, bits, div, grad = args
+    import oracle
+    net = WORKLOADS[name]()
+    t0 = time.perf_counter()
+    oracle.enumerate_states(net, prefix_bits=bits, prefix_lo=div, prefix_hi=div + 1, grad=grad)
+    return time.perf_counter() - t0
+
+
+def oracle_rate(name: str, target_s: float, pool, cores: int, grad: bool = True):
+    """States/s of the oracle on this host: calibrate one division, then run
+    enough evenly spread divisions on every core to fill ~target_s."""
+    net = WORKLOADS[name]()
+    m = net.m
+    sub = min(m, 12)                 # states per division: 2^sub
+    bits = m - sub
+    t1 = _oracle_division((name, bits, 0, grad))
+    per = max(t1, 1e-4)
+    n_div = max(cores, int(target_s * cores / per))
+    n_div = min(n_div, 1 << bits)
+    step = max(1, (1 << bits) // n_div)
+    divs = [(i * step) % (1 << bits) for i in range(n_div)]
+    t0 = time.perf_counter()
+    pool.map(_oracle_division, [(name, bits, d, grad) for d in divs])
+    wall = time.perf_counter() - t0
+    states = n_div * (1 << sub)
+    return states / wall, dict(states=states, divisions=n_div, division_states=1 << sub,
+                               wall_s=wall)
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    name = a.workload
+    net = WORKLOADS[name]()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        for _ in range(a.warmup):
+            oracle_rate(name, 1.0, pool, cores)
+        rates, walls, samples = [], [], []
+        for _ in range(a.steps):
+            r, info = oracle_rate(name, a.ref_seconds, pool, cores)
+            rates.append(r)
+            walls.append(info["wall_s"])
+            samples.append(info)
+    value = statistics.median(rates)
+    s0 = samples[0]
+    sample = (f"{s0['divisions']} equal divisions of {s0['division_states']} states "
+              f"(R, N_k, T1/T0 gradient) of {name}, spread over the 2^{net.m} space, "
+              f"extrapolated as states/s")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "states/s",
+        "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1000.0 * statistics.mean(walls), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f80/f128 long double",
+        "data": "synthetic",
+        "config": {"workload": name, "n": net.n, "m": net.m, "states": 2**net.m},
+        "cpu_baseline": {"value": value, "unit": "states/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "states/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU path
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.t0 = self.t1 = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), max=float(f[2]), hw=f[5], hwt=f[6], swt=f[7],
+                                 pcap=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, label in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                               ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(label)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["max"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def run_ours(a):
+    import torch
+    ws, rank, local = _dist()
+    cores = os.cpu_count() or 1
+    pool = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        # the oracle's process pool is started before the first GPU call
+        pool = mp.get_context("spawn").Pool(cores)
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2209_09711_gb300 import build
+    build.build()
+    import paper_2209_09711_gb300 as pb
+
+    net = WORKLOADS[a.workload]()
+    m = net.m
+    states = 2**m
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def time_plan(plan, steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                plan.execute(sp)
+            plan.read(sp)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            barrier()
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            for i in range(steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                plan.execute(sp)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - w0
+            barrier()
+            res = plan.read(sp)
+        step_ms = [s.elapsed_time(e) for s, e in ev]
+        kern_ms = res.stats[4] / 1e6 / max(1, res.stats[7])
+        return statistics.mean(step_ms), kern_ms, wall, res
+
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit()
+                           else local)
+    fused = pb.Plan(net, grad=True, stream=sp)
+    ms_f, kern_f, wall_f, res_f = time_plan(fused, a.steps, a.warmup)
+    clocks = sampler.stop()
+    plain = pb.Plan(net, grad=False, stream=sp)
+    ms_r, kern_r, _, res_r = time_plan(plain, a.steps, a.warmup)
+
+    # e2e: the public call with host buffers, copies included
+    e2e_t = []
+    o = pb.options()
+    for i in range(a.warmup + a.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = pb.reliability_net(net, grad=True, opts=o, stream=sp)
+        t1 = time.perf_counter()
+        if i >= a.warmup:
+            e2e_t.append(t1 - t0)
+    e2e_s = statistics.mean(e2e_t)
+
+    if ws > 1:
+        t = torch.tensor([ms_f, ms_r, e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_f, ms_r, e2e_s = t.tolist()
+
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+
+    cpu = None
+    if pool is not None:
+        rate, info = oracle_rate(a.workload, a.cpu_seconds, pool, cores)
+        pool.close()
+        cpu = {"value": rate, "unit": "states/s", "cores": cores, "kind": "oracle",
+               "sample": f"{info['divisions']} equal divisions x {info['division_states']} states "
+                         f"(R, N_k, T1/T0 gradient), {info['wall_s']:.1f} s wall on {cores} host "
+                         f"processes, extrapolated to states/s"}
+
+    ipc = INST_PER_STATE.get(a.workload)
+    peak = SM_COUNT * ISSUE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9  # G warp-inst/s
+    if ipc is not None:
+        achieved = ipc * states / (kern_f / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
+                "frac": achieved / peak,
+                "traffic": DRAM_BYTES_PER_LAUNCH.get(a.workload),
+                "kernel": "frontier_kernel<u32,grad>", "kernel_ms": kern_f}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s",
+                "frac": None, "traffic": None, "kernel": "frontier_kernel<u32,grad>",
+                "kernel_ms": kern_f}
+    value = ws * states / (ms_f / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_f, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+        "config": {"workload": a.workload, "n": net.n, "m": m, "states": states,
+                   "outputs": "R, N_k, dR/dp", "directed": bool(net.directed),
+                   "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roof,
+        "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r},
+        "fused_over_r_only_time": ms_f / ms_r,
+        "R": res_f.R, "pruned_states": res_f.stats[1], "walked_states": res_f.stats[0],
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * states / e2e_s, "unit": "states/s",
+                "h2d_bytes_per_step": int(r.stats[2]), "d2h_bytes_per_step": int(r.stats[3])},
+        "gpu_launches": 2 * a.steps,
+        "clocks": clocks,
+        "wall_s_timed": wall_f,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    fused.close()
+    plain.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target wall time of the cpu_baseline oracle sample")
+    ap.add_argument("--ref-seconds", type=float, default=6.0,
+                    help="target wall time of one --impl reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 0 or a.steps < 1:
+        ap.error("need --steps >= 1 and --warmup >= 0")
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

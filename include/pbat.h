@@ -1,0 +1,174 @@
+/*
+ * pbat.h -- C ABI of the GB300 PBAT engine: exact two-terminal reliability
+ * of a binary-state network by enumerating every arc-state vector.
+ *
+ * Problem (arXiv 2209.09711, Sec. 2 and Sec. 5.1 "Input/Output" of PBAT):
+ * a network G(V, E, D_b) with n nodes and m arcs, where arc a_k works with
+ * probability p_k independently of the others (Sec. 2.4 assumption 2).
+ * The reliability is
+ *
+ *     R = sum over arc-state vectors X in {0,1}^m with the sink reachable
+ *         from the source in G(X) of  prod_k (x_k ? p_k : 1 - p_k)   (Eq. 1)
+ *
+ * and the engine also returns the reliability-polynomial counts
+ * N_k = #{connected X with exactly k working arcs} and the gradient
+ * dR/dp_k.  Connectivity is the PLSA reachability test of Sec. 3.2.
+ *
+ * Conventions shared by every call:
+ *   - Node ids are 0-based, in [0, n_nodes).  The paper's source node 1 and
+ *     sink node n are simply `source` and `sink` here.
+ *   - Arc k joins tail[k] and head[k].  directed != 0: usable tail -> head
+ *     only; directed == 0: usable both ways.  Loops (tail == head) are
+ *     rejected (Sec. 2.4 assumption 3); parallel arcs are accepted -- the
+ *     sum in Eq. 1 is unchanged by them.
+ *   - Arc order is the paper's coordinate order: arc 0 is the first
+ *     coordinate x_1, the most significant bit of the state index
+ *     (Sec. 4.2, Eq. 2-3).  The engine may permute arcs internally; every
+ *     output is in input arc order.
+ *   - Limits: 2 <= n_nodes <= 64, 1 <= n_arcs <= 63.
+ *   - All pointers are HOST pointers unless a name says otherwise.  The
+ *     caller owns every array; the library copies what it needs and keeps no
+ *     pointer after the call returns.
+ *   - Every call returns PBAT_OK (0) or a negative PBAT_E* code.  On error no
+ *     output array is written, and pbat_last_error() (thread-local) gives a
+ *     one-line reason.  No C++ exception crosses this boundary.
+ *   - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     The calls are synchronous: they return after the results are on the
+ *     host.  Calls are re-entrant; concurrent calls from several host
+ *     threads are allowed.
+ */
+#ifndef PBAT_H
+#define PBAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PBAT_OK 0
+#define PBAT_EINVAL (-1)   /* malformed input: ids out of range, loop, source == sink, p not in [0,1] */
+#define PBAT_ERANGE (-2)   /* n_nodes > 64, n_arcs > 63, or a size past a stated maximum */
+#define PBAT_ECUDA (-3)    /* a CUDA runtime/driver call or a kernel failed */
+#define PBAT_ETIMEOUT (-4) /* opt->time_budget_s ran out on the device; results discarded */
+#define PBAT_ENOMEM (-5)   /* device or host allocation failed */
+#define PBAT_ENOTSUP (-6)  /* the requested algorithm cannot run this input */
+
+/* Connectivity kernels (the "a5" step of the hot path). */
+#define PBAT_ALGO_AUTO 0
+#define PBAT_ALGO_FRONTIER 1  /* one state per thread, bitmask frontier expansion (PLSA) */
+#define PBAT_ALGO_BITSLICE 2  /* 32 states per thread word, kernel specialised per graph */
+
+typedef struct pbat_options {
+  int struct_size;      /* sizeof(pbat_options); set by pbat_options_init */
+  int algo;             /* PBAT_ALGO_*; AUTO lets the autotuner choose */
+  int prefix_bits;      /* d: arcs fixed per work item (equal division, Sec. 4.3); -1 = auto */
+  int walk_bits;        /* L: arcs each thread walks in Gray-code order; -1 = auto */
+  int block_threads;    /* threads per CTA; -1 = auto */
+  int prune;            /* 1 (default): exact monotone prefix prune; 0: walk every state */
+  int autotune;         /* 1 (default): consult / fill the autotune cache */
+  int range_bits;       /* 0 (default) = whole space.  Otherwise only the states whose
+                           first range_bits coordinates, read as an integer, lie in
+                           [range_lo, range_hi) -- the divisions range_lo..range_hi-1 of
+                           Eq. 6 with chi = 2^range_bits.  Partial results of disjoint
+                           ranges add up to the full result (checkpoint / resume). */
+  uint64_t range_lo;
+  uint64_t range_hi;
+  double time_budget_s; /* > 0: the device stops after this many seconds and the call
+                           returns PBAT_ETIMEOUT; 0 = no limit */
+  uint64_t stats[8];    /* out, filled by the last call that took these options:
+                           [0] states enumerated by walking, [1] states resolved by the
+                           prune, [2] bytes copied host -> device, [3] bytes copied
+                           device -> host, [4] summed device time in ns of the
+                           enumeration kernel over the launches since the last read (CUDA
+                           events on the launch stream), [5] kernels launched, [6] work
+                           items per launch, [7] launches timed in [4] */
+} pbat_options;
+
+/* Fill *opt with the defaults above. */
+void pbat_options_init(pbat_options* opt);
+
+/*
+ * R and N_k of one network (Eq. 1; PBAT STEP 0-3 of Sec. 5.1).
+ *   p        [n_arcs] arc reliabilities, each in [0, 1]
+ *   opt      nullable (defaults)
+ *   R_out    out, 1 double: R (or the partial R of opt's range)
+ *   Nk_out   out, nullable, n_arcs + 1 uint64: N_0 .. N_m
+ */
+int pbat_reliability(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
+                     int directed, const double* p, int source, int sink,
+                     pbat_options* opt, void* cuda_stream, double* R_out, uint64_t* Nk_out);
+
+/*
+ * As pbat_reliability, plus the gradient dR/dp_k (Birnbaum importance of
+ * arc k) from one fused enumeration.  R is affine in every p_k, so
+ * dR/dp_k = R(p_k = 1) - R(p_k = 0); the engine differentiates Eq. 1 term
+ * by term in exact fixed-point sums.
+ *   dRdp_out out, n_arcs doubles (input arc order)
+ * With opt->range_bits > 0 the gradient is that of the partial R.
+ */
+int pbat_reliability_grad(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
+                          int directed, const double* p, int source, int sink,
+                          pbat_options* opt, void* cuda_stream, double* R_out, uint64_t* Nk_out,
+                          double* dRdp_out);
+
+/* One network of a batch. */
+typedef struct pbat_graph {
+  int n_nodes;
+  int n_arcs;
+  const int32_t* tail;
+  const int32_t* head;
+  int directed;
+  int source;
+  int sink;
+} pbat_graph;
+
+/*
+ * Many networks, each with n_pvec arc-reliability vectors, in one
+ * persistent launch (captured once in a CUDA graph and replayed).  Each
+ * state's connectivity is computed once and weighted by every p-vector.
+ *   p         per graph g: n_pvec x m_g doubles (vector-major), concatenated in
+ *             graph order
+ *   R_out     out, n_graphs x n_pvec doubles (graph-major)
+ *   Nk_out    out, nullable, sum over g of (m_g + 1) uint64, graph order
+ *   dRdp_out  out, nullable, same layout as p
+ * Limits: 1 <= n_graphs <= 4096, 1 <= n_pvec <= 64.
+ */
+int pbat_reliability_batched(int n_graphs, const pbat_graph* graphs, int n_pvec,
+                             const double* p, pbat_options* opt, void* cuda_stream,
+                             double* R_out, uint64_t* Nk_out, double* dRdp_out);
+
+/*
+ * Prepared enumerations.  pbat_plan_create validates the input, plans the
+ * equal division, builds the tables and uploads them to the device once;
+ * pbat_plan_execute then runs the whole enumeration (every kernel, no host
+ * work, no copies) on `cuda_stream` and returns without waiting;
+ * pbat_plan_read copies the results of the last execute back and waits.
+ * A plan owns its device scratch until pbat_plan_destroy; one plan must not
+ * be executed on two streams at once.
+ *   want_grad  0: R and N_k; 1: R, N_k and dR/dp (fused kernel)
+ *   plan_out   out: the new plan
+ */
+typedef struct pbat_plan_s* pbat_plan;
+int pbat_plan_create(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
+                     int directed, const double* p, int source, int sink, int want_grad,
+                     pbat_options* opt, void* cuda_stream, pbat_plan* plan_out);
+int pbat_plan_execute(pbat_plan plan, void* cuda_stream);
+int pbat_plan_read(pbat_plan plan, void* cuda_stream, double* R_out, uint64_t* Nk_out,
+                   double* dRdp_out);
+void pbat_plan_destroy(pbat_plan plan);
+/* Copy the plan's statistics (the pbat_options.stats[8] layout, as filled by
+ * the last pbat_plan_read) into stats_out[8]. */
+int pbat_plan_stats(pbat_plan plan, uint64_t* stats_out);
+
+/* Thread-local description of the last error in this thread ("" if none). */
+const char* pbat_last_error(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int pbat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBAT_H */

@@ -1,0 +1,632 @@
+// pbat_engine.cu -- host side of the PBAT engine behind the C ABI.
+//
+// Steps of one call (the PBAT driver of arXiv 2209.09711 Sec. 5.1, laid out
+// for one GPU):
+//   validate  -> reject what the problem statement excludes (Sec. 2.4)
+//   plan      -> choose which arcs are prefix / walk / lane arcs and how many
+//                of each (STEP 0-1: the equal division of Sec. 4.3)
+//   tables    -> fixed-point walk masses, lane masses, reciprocals
+//   launch    -> frontier kernel over all work items (STEP 2), then the
+//                fixed-order reduction of block partials (STEP 3)
+//   read back -> R, N_k and dR/dp in input arc order
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pbat.h"
+#include "pbat_engine.h"
+#include "pbat_internal.h"
+
+namespace pbat {
+
+size_t frontier_smem_bytes(int n, int m, int L, int nthr, bool grad, bool wide);
+const void* frontier_kernel_ptr(bool grad, bool wide);
+cudaError_t launch_frontier(bool grad, bool wide, int grid, int nthr, size_t smem,
+                            cudaStream_t st, const FrontierParams& P, const u128* wmid,
+                            const DevWork& W);
+cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int m);
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string t_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return code;
+}
+
+void clear_error() { t_last_error.clear(); }
+const char* last_error() { return t_last_error.c_str(); }
+
+#define PBAT_CUDA(call)                                                                   \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(PBAT_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+int validate_graph(const GraphIn& g) {
+  if (g.n > kMaxNodes) return fail(PBAT_ERANGE, "n_nodes=%d exceeds %d", g.n, kMaxNodes);
+  if (g.m > kMaxArcs) return fail(PBAT_ERANGE, "n_arcs=%d exceeds %d", g.m, kMaxArcs);
+  if (g.n < 2) return fail(PBAT_EINVAL, "n_nodes=%d: need at least 2 nodes", g.n);
+  if (g.m < 1) return fail(PBAT_EINVAL, "n_arcs=%d: need at least 1 arc", g.m);
+  if (!g.tail || !g.head) return fail(PBAT_EINVAL, "tail/head must not be NULL");
+  if (g.source < 0 || g.source >= g.n || g.sink < 0 || g.sink >= g.n)
+    return fail(PBAT_EINVAL, "source=%d sink=%d out of [0,%d)", g.source, g.sink, g.n);
+  if (g.source == g.sink) return fail(PBAT_EINVAL, "source == sink (%d)", g.source);
+  for (int k = 0; k < g.m; ++k) {
+    if (g.tail[k] < 0 || g.tail[k] >= g.n || g.head[k] < 0 || g.head[k] >= g.n)
+      return fail(PBAT_EINVAL, "arc %d (%d,%d) has a node id out of [0,%d)", k, g.tail[k],
+                  g.head[k], g.n);
+    if (g.tail[k] == g.head[k]) return fail(PBAT_EINVAL, "arc %d is a loop at node %d", k, g.tail[k]);
+  }
+  return PBAT_OK;
+}
+
+int validate_p(const double* p, int m) {
+  if (!p) return fail(PBAT_EINVAL, "p must not be NULL");
+  for (int k = 0; k < m; ++k)
+    if (!(p[k] >= 0.0 && p[k] <= 1.0))
+      return fail(PBAT_EINVAL, "p[%d]=%g is not in [0,1]", k, p[k]);
+  return PBAT_OK;
+}
+
+int validate_options(const pbat_options* o, int m) {
+  if (!o) return PBAT_OK;
+  if (o->struct_size != (int)sizeof(pbat_options))
+    return fail(PBAT_EINVAL, "pbat_options.struct_size=%d, expected %d (call pbat_options_init)",
+                o->struct_size, (int)sizeof(pbat_options));
+  if (o->algo < PBAT_ALGO_AUTO || o->algo > PBAT_ALGO_BITSLICE)
+    return fail(PBAT_EINVAL, "unknown algo %d", o->algo);
+  if (o->range_bits < 0 || o->range_bits > m)
+    return fail(PBAT_EINVAL, "range_bits=%d not in [0,%d]", o->range_bits, m);
+  if (o->range_bits > 0) {
+    const uint64_t lim = (uint64_t)1 << o->range_bits;
+    if (o->range_lo > o->range_hi || o->range_hi > lim)
+      return fail(PBAT_EINVAL, "range [%llu,%llu) not within [0,2^%d]",
+                  (unsigned long long)o->range_lo, (unsigned long long)o->range_hi, o->range_bits);
+  }
+  if (o->block_threads != -1 &&
+      (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32))
+    return fail(PBAT_EINVAL, "block_threads=%d must be -1 or a multiple of 32 in [32,256]",
+                o->block_threads);
+  if (!(o->time_budget_s >= 0.0)) return fail(PBAT_EINVAL, "time_budget_s must be >= 0");
+  return PBAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fixed point and double-double helpers (host)
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+static bool walk_ok(double p) {  // the gradient divides walk masses by p and 1 - p
+  return p >= 0x1p-20 && p <= 1.0 - 0x1p-20;
+}
+
+int make_plan(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
+              const DeviceInfo& dev, Plan& pl) {
+  const int m = g.m;
+  const int r = o.range_bits;
+  pl.grad = grad;
+  pl.range_bits = r;
+  pl.ell = std::min(kMaxLaneBits, m - r);
+  const int free_bits = m - r - pl.ell;
+  const int lmax = grad ? kMaxWalkBitsGrad : kMaxWalkBitsR;
+  // enough work items to keep every warp of the persistent grid busy
+  int want_items_log2 = 14;
+  if (o.walk_bits >= 0) {
+    pl.L = std::min(o.walk_bits, std::min(lmax, free_bits));
+  } else if (o.prefix_bits >= 0) {
+    const int d = std::max(o.prefix_bits, r);
+    pl.L = std::max(0, std::min(lmax, m - pl.ell - d));
+  } else {
+    const int extra_prefix = std::max(0, want_items_log2 - r);
+    pl.L = std::max(0, std::min(lmax, free_bits - extra_prefix));
+  }
+  pl.d = m - pl.ell - pl.L;
+  // Internal arc order: internal position k holds input arc m-1-k, so the
+  // state word equals the paper's state index (x_1 most significant, Eq. 2)
+  // and the first range_bits input arcs are the top prefix bits.
+  pl.perm.resize(m);
+  for (int k = 0; k < m; ++k) pl.perm[k] = m - 1 - k;
+  if (grad) {
+    // walk arcs need p strictly inside (0, 1); swap offenders with a lane or
+    // a free prefix arc
+    const int w0 = pl.ell, w1 = pl.ell + pl.L;
+    const int swap_hi = m - r;  // prefix positions [w1, m - r) are not range-fixed
+    for (int k = w0; k < w1; ++k) {
+      if (walk_ok(p[pl.perm[k]])) continue;
+      int found = -1;
+      for (int c = 0; c < swap_hi && found < 0; ++c) {
+        if (c >= w0 && c < w1) continue;
+        if (walk_ok(p[pl.perm[c]])) found = c;
+      }
+      if (found < 0) {
+        // shrink the walk: move this arc's slot to the prefix side
+        pl.L = k - w0;
+        pl.d = m - pl.ell - pl.L;
+        break;
+      }
+      std::swap(pl.perm[k], pl.perm[found]);
+    }
+  }
+  uint64_t lo = 0, hi = (uint64_t)1 << pl.d;
+  if (r > 0) {
+    lo = o.range_lo << (pl.d - r);
+    hi = o.range_hi << (pl.d - r);
+  }
+  if (pl.d >= 64) return fail(PBAT_ERANGE, "prefix of %d bits is too deep", pl.d);
+  pl.task_lo = lo;
+  pl.n_tasks = hi - lo;
+  pl.wide = g.n > 32;
+  pl.nthr = o.block_threads > 0 ? o.block_threads : 128;
+  pl.smem = frontier_smem_bytes(g.n, m, pl.L, pl.nthr, grad, pl.wide);
+  if (pl.smem > (size_t)dev.smem_optin)
+    return fail(PBAT_ERANGE, "shared memory %zu B exceeds %d B (lower walk_bits)", pl.smem,
+                dev.smem_optin);
+  pl.prune = o.prune ? 1 : 0;
+  return PBAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------
+
+void build_params(const GraphIn& g, const double* p, const Plan& pl, const pbat_options& o,
+                  FrontierParams& P, std::vector<u128>& wmid) {
+  memset(&P, 0, sizeof P);
+  const int m = g.m;
+  P.n = g.n;
+  P.m = m;
+  P.directed = g.directed ? 1 : 0;
+  P.source = g.source;
+  P.sink = g.sink;
+  P.lane_bits = pl.ell;
+  P.walk_bits = pl.L;
+  P.prefix_bits = pl.d;
+  P.prune = pl.prune;
+  P.task_lo = pl.task_lo;
+  P.n_tasks = pl.n_tasks;
+  P.budget_ns = o.time_budget_s > 0 ? (unsigned long long)(o.time_budget_s * 1e9) : 0ull;
+  P.free_mask = pl.ell + pl.L >= 64 ? ~0ull : ((1ull << (pl.ell + pl.L)) - 1ull);
+  for (int k = 0; k < m; ++k) {
+    const int a = pl.perm[k];
+    P.au[k] = (unsigned char)g.tail[a];
+    P.av[k] = (unsigned char)g.head[a];
+    P.p[k] = p[a];
+    P.q[k] = dd_one_minus(p[a]);
+    if (k >= pl.ell && k < pl.ell + pl.L) {
+      P.inv_p[k] = dd_recip(p[a]);
+      P.inv_q[k] = dd_recip_dd(P.q[k]);
+    }
+  }
+  for (int k = 0; k < m; ++k) {
+    unsigned long long gm = 0;
+    const int a = pl.perm[k];
+    for (int j = 0; j < m; ++j) {
+      const int b = pl.perm[j];
+      const bool same = g.directed ? (g.tail[a] == g.tail[b] && g.head[a] == g.head[b])
+                                   : ((g.tail[a] == g.tail[b] && g.head[a] == g.head[b]) ||
+                                      (g.tail[a] == g.head[b] && g.head[a] == g.tail[b]));
+      if (same) gm |= 1ull << j;
+    }
+    P.grp[k] = gm;
+  }
+  const int nl = 1 << pl.ell;
+  for (int j = 0; j < 32; ++j) {
+    if (j >= nl) {
+      P.lane_w[j] = dd{0.0, 0.0};
+      for (int i = 0; i < kMaxLaneBits; ++i) P.lane_w_ex[i][j] = dd{0.0, 0.0};
+      continue;
+    }
+    dd w = dd_make(1.0);
+    for (int i = 0; i < pl.ell; ++i) w = dd_mul(w, arc_w(p, pl.perm[i], (j >> i) & 1));
+    P.lane_w[j] = w;
+    for (int x = 0; x < pl.ell; ++x) {
+      dd we = dd_make(1.0);
+      for (int i = 0; i < pl.ell; ++i)
+        if (i != x) we = dd_mul(we, arc_w(p, pl.perm[i], (j >> i) & 1));
+      P.lane_w_ex[x][j] = we;
+    }
+  }
+  for (int j = 0; j < 64; ++j) P.binom[j] = binom_u64(pl.ell + pl.L, j);
+  const int nW = 1 << pl.L;
+  wmid.resize(nW);
+  for (int gi = 0; gi < nW; ++gi) {
+    dd w = dd_make(1.0);
+    for (int b = 0; b < pl.L; ++b) w = dd_mul(w, arc_w(p, pl.perm[pl.ell + b], (gi >> b) & 1));
+    wmid[gi] = to_fixed127(w);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// device info and scratch pool
+// ---------------------------------------------------------------------------
+static std::mutex g_mu;
+static std::vector<DeviceInfo> g_dev;
+
+int device_info(DeviceInfo& out) {
+  int d = 0;
+  PBAT_CUDA(cudaGetDevice(&d));
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& x : g_dev)
+    if (x.device == d) {
+      out = x;
+      return PBAT_OK;
+    }
+  DeviceInfo di;
+  di.device = d;
+  PBAT_CUDA(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, d));
+  PBAT_CUDA(cudaDeviceGetAttribute(&di.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d));
+  PBAT_CUDA(cudaDeviceGetAttribute(&di.cc_major, cudaDevAttrComputeCapabilityMajor, d));
+  PBAT_CUDA(cudaDeviceGetAttribute(&di.cc_minor, cudaDevAttrComputeCapabilityMinor, d));
+  g_dev.push_back(di);
+  out = di;
+  return PBAT_OK;
+}
+
+static std::vector<Scratch*> g_pool;
+
+int scratch_acquire(int device, size_t dbytes, size_t hbytes, Scratch** out) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto* s : g_pool) {
+      if (!s->busy && s->device == device && s->dbytes >= dbytes && s->hbytes >= hbytes) {
+        s->busy = true;
+        *out = s;
+        return PBAT_OK;
+      }
+    }
+  }
+  auto* s = new Scratch();
+  s->device = device;
+  s->dbytes = std::max<size_t>(dbytes, 1 << 20);
+  s->hbytes = std::max<size_t>(hbytes, 1 << 16);
+  if (cudaMalloc(&s->dmem, s->dbytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return fail(PBAT_ENOMEM, "cudaMalloc of %zu B failed", dbytes);
+  }
+  if (cudaMallocHost(&s->hmem, s->hbytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(s->dmem);
+    delete s;
+    return fail(PBAT_ENOMEM, "cudaMallocHost of %zu B failed", hbytes);
+  }
+  s->busy = true;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_pool.push_back(s);
+  *out = s;
+  return PBAT_OK;
+}
+
+void scratch_release(Scratch* s) {
+  if (!s) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  s->busy = false;
+}
+
+// ---------------------------------------------------------------------------
+// one planned enumeration (single network)
+// ---------------------------------------------------------------------------
+struct Job {
+  GraphIn g;
+  Plan pl;
+  FrontierParams P;
+  DeviceInfo dev;
+  Scratch* scr = nullptr;
+  int grid = 0;
+  DevWork W{};
+  u128* d_wmid = nullptr;
+  // host mirror in pinned memory
+  dd* h_acc = nullptr;
+  unsigned long long* h_n = nullptr;
+  unsigned int* h_status = nullptr;
+  unsigned long long* h_stats = nullptr;
+  void* wmid_host_staging = nullptr;
+  size_t wmid_bytes = 0;
+  // CUDA events around the enumeration kernel of every execute since the
+  // last read (so a caller can time many launches and read once)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+  size_t n_pending = 0;
+};
+
+static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, Job** out) {
+  pbat_options o;
+  pbat_options_init(&o);
+  if (opt) o = *opt;
+  int rc;
+  if ((rc = validate_graph(g))) return rc;
+  if ((rc = validate_p(p, g.m))) return rc;
+  if ((rc = validate_options(opt, g.m))) return rc;
+  if (o.algo == PBAT_ALGO_BITSLICE)
+    return fail(PBAT_ENOTSUP, "the bit-sliced kernel is not available in this build");
+  std::unique_ptr<Job> J(new Job());
+  J->g = g;
+  if ((rc = device_info(J->dev))) return rc;
+  if ((rc = make_plan(g, p, grad, o, J->dev, J->pl))) return rc;
+  std::vector<u128> wmid;
+  build_params(g, p, J->pl, o, J->P, wmid);
+
+  const void* kfn = frontier_kernel_ptr(grad, J->pl.wide);
+  PBAT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)J->pl.smem));
+  int per_sm = 0;
+  PBAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, J->pl.nthr, J->pl.smem));
+  if (per_sm < 1) return fail(PBAT_ERANGE, "frontier kernel cannot be resident (smem %zu B)", J->pl.smem);
+  const long long warps_per_block = J->pl.nthr / 32;
+  long long grid = (long long)per_sm * J->dev.sms;
+  // never more warps than work items
+  const long long need = ((long long)std::min<unsigned long long>(J->pl.n_tasks, 1ull << 40) +
+                          warps_per_block - 1) / warps_per_block;
+  grid = std::max(1LL, std::min(grid, need));
+  J->grid = (int)grid;
+  const int m = g.m;
+
+  // device scratch layout
+  size_t off = 0;
+  const size_t o_counter = off; off = up16(off + 8);
+  const size_t o_status = off; off = up16(off + 4);
+  const size_t o_stats = off; off = up16(off + 3 * 8);
+  const size_t o_part_acc = off; off = up16(off + (size_t)grid * (1 + m) * sizeof(dd));
+  const size_t o_part_n = off; off = up16(off + (size_t)grid * (m + 1) * 8);
+  const size_t o_out_acc = off; off = up16(off + (size_t)(1 + m) * sizeof(dd));
+  const size_t o_out_n = off; off = up16(off + (size_t)(m + 1) * 8);
+  const size_t o_wmid = off; off = up16(off + wmid.size() * sizeof(u128));
+  const size_t dbytes = off;
+  // host (pinned) layout: results + staging of the walk table
+  size_t hoff = 0;
+  const size_t h_acc = hoff; hoff = up16(hoff + (size_t)(1 + m) * sizeof(dd));
+  const size_t h_n = hoff; hoff = up16(hoff + (size_t)(m + 1) * 8);
+  const size_t h_status = hoff; hoff = up16(hoff + 4);
+  const size_t h_stats = hoff; hoff = up16(hoff + 3 * 8);
+  const size_t h_wmid = hoff; hoff = up16(hoff + wmid.size() * sizeof(u128));
+  const size_t hbytes = hoff;
+  if ((rc = scratch_acquire(J->dev.device, dbytes, hbytes, &J->scr))) return rc;
+  char* d = (char*)J->scr->dmem;
+  char* h = (char*)J->scr->hmem;
+  J->W.counter = (unsigned long long*)(d + o_counter);
+  J->W.status = (unsigned int*)(d + o_status);
+  J->W.stats = (unsigned long long*)(d + o_stats);
+  J->W.part_acc = (dd*)(d + o_part_acc);
+  J->W.part_n = (unsigned long long*)(d + o_part_n);
+  J->W.out_acc = (dd*)(d + o_out_acc);
+  J->W.out_n = (unsigned long long*)(d + o_out_n);
+  J->d_wmid = (u128*)(d + o_wmid);
+  J->h_acc = (dd*)(h + h_acc);
+  J->h_n = (unsigned long long*)(h + h_n);
+  J->h_status = (unsigned int*)(h + h_status);
+  J->h_stats = (unsigned long long*)(h + h_stats);
+  memcpy(h + h_wmid, wmid.data(), wmid.size() * sizeof(u128));
+  J->wmid_host_staging = h + h_wmid;
+  J->wmid_bytes = wmid.size() * sizeof(u128);
+  *out = J.release();
+  return PBAT_OK;
+}
+
+// Upload the walk table (host -> device, on the stream).
+int job_upload(Job* J, cudaStream_t st) {
+  PBAT_CUDA(cudaMemcpyAsync(J->d_wmid, J->wmid_host_staging, J->wmid_bytes,
+                            cudaMemcpyHostToDevice, st));
+  return PBAT_OK;
+}
+
+// Launch the enumeration and the reduction (asynchronous).
+int job_launch(Job* J, cudaStream_t st) {
+  PBAT_CUDA(cudaMemsetAsync(J->W.counter, 0, 64, st));  // counter, status, stats
+  const bool timed = J->n_pending < 65536;
+  if (timed && J->n_pending == J->evs.size()) {
+    cudaEvent_t a, b;
+    PBAT_CUDA(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return fail(PBAT_ECUDA, "cudaEventCreate failed");
+    }
+    J->evs.emplace_back(a, b);
+  }
+  if (timed) PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].first, st));
+  PBAT_CUDA(launch_frontier(J->pl.grad, J->pl.wide, J->grid, J->pl.nthr, J->pl.smem, st, J->P,
+                            J->d_wmid, J->W));
+  if (timed) {
+    PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].second, st));
+    ++J->n_pending;
+  }
+  PBAT_CUDA(launch_reduce(st, J->W, J->grid, J->g.m));
+  return PBAT_OK;
+}
+
+// Copy results to the host and wait; convert to input arc order.
+int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* dRdp_out,
+             pbat_options* opt) {
+  const int m = J->g.m;
+  PBAT_CUDA(cudaMemcpyAsync(J->h_acc, J->W.out_acc, (size_t)(1 + m) * sizeof(dd),
+                            cudaMemcpyDeviceToHost, st));
+  PBAT_CUDA(cudaMemcpyAsync(J->h_n, J->W.out_n, (size_t)(m + 1) * 8, cudaMemcpyDeviceToHost, st));
+  PBAT_CUDA(cudaMemcpyAsync(J->h_status, J->W.status, 4, cudaMemcpyDeviceToHost, st));
+  PBAT_CUDA(cudaMemcpyAsync(J->h_stats, J->W.stats, 24, cudaMemcpyDeviceToHost, st));
+  PBAT_CUDA(cudaStreamSynchronize(st));
+  if (*J->h_status & 1u)
+    return fail(PBAT_ETIMEOUT, "time budget of %.3f s ran out on the device",
+                J->P.budget_ns * 1e-9);
+  if (opt) {
+    const unsigned long long item = 1ull << (J->pl.ell + J->pl.L);
+    opt->stats[0] = J->h_stats[0] * item;
+    opt->stats[1] = (J->h_stats[1] + J->h_stats[2]) * item;
+    opt->stats[2] = J->wmid_bytes;
+    opt->stats[3] = (1 + m) * sizeof(dd) + (m + 1) * 8 + 4 + 24;
+    double ns = 0.0;
+    for (size_t i = 0; i < J->n_pending; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, J->evs[i].first, J->evs[i].second) == cudaSuccess)
+        ns += ms * 1e6;
+      else
+        cudaGetLastError();
+    }
+    opt->stats[4] = (unsigned long long)ns;
+    opt->stats[5] = 2 * J->n_pending;
+    opt->stats[6] = J->pl.n_tasks;
+    opt->stats[7] = J->n_pending;
+  }
+  J->n_pending = 0;
+  *R_out = J->h_acc[0].hi + J->h_acc[0].lo;
+  if (Nk_out)
+    for (int k = 0; k <= m; ++k) Nk_out[k] = J->h_n[k];
+  if (dRdp_out)
+    for (int k = 0; k < m; ++k) {
+      const dd v = J->h_acc[1 + k];
+      dRdp_out[J->pl.perm[k]] = v.hi + v.lo;
+    }
+  return PBAT_OK;
+}
+
+void job_destroy(Job* J) {
+  if (!J) return;
+  for (auto& e : J->evs) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  scratch_release(J->scr);
+  delete J;
+}
+
+int run_single(const GraphIn& g, const double* p, bool grad, pbat_options* opt, void* stream,
+               double* R_out, uint64_t* Nk_out, double* dRdp_out) {
+  clear_error();
+  if (!R_out) return fail(PBAT_EINVAL, "R_out must not be NULL");
+  if (grad && !dRdp_out) return fail(PBAT_EINVAL, "dRdp_out must not be NULL");
+  Job* J = nullptr;
+  int rc = job_create(g, p, grad, opt, &J);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!(rc = job_upload(J, st)) && !(rc = job_launch(J, st)))
+    rc = job_read(J, st, R_out, Nk_out, grad ? dRdp_out : nullptr, opt);
+  job_destroy(J);
+  return rc;
+}
+
+}  // namespace pbat
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void pbat_options_init(pbat_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->struct_size = (int)sizeof(pbat_options);
+  o->algo = PBAT_ALGO_AUTO;
+  o->prefix_bits = -1;
+  o->walk_bits = -1;
+  o->block_threads = -1;
+  o->prune = 1;
+  o->autotune = 1;
+}
+
+int pbat_reliability(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
+                     int directed, const double* p, int source, int sink, pbat_options* opt,
+                     void* cuda_stream, double* R_out, uint64_t* Nk_out) {
+  try {
+    pbat::GraphIn g{n_nodes, n_arcs, tail, head, directed, source, sink};
+    return pbat::run_single(g, p, false, opt, cuda_stream, R_out, Nk_out, nullptr);
+  } catch (...) {
+    return pbat::fail(PBAT_ENOMEM, "host exception");
+  }
+}
+
+int pbat_reliability_grad(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
+                          int directed, const double* p, int source, int sink, pbat_options* opt,
+                          void* cuda_stream, double* R_out, uint64_t* Nk_out, double* dRdp_out) {
+  try {
+    pbat::GraphIn g{n_nodes, n_arcs, tail, head, directed, source, sink};
+    return pbat::run_single(g, p, true, opt, cuda_stream, R_out, Nk_out, dRdp_out);
+  } catch (...) {
+    return pbat::fail(PBAT_ENOMEM, "host exception");
+  }
+}
+
+struct pbat_plan_s {
+  pbat::Job* job;
+  pbat_options opt;
+};
+
+int pbat_plan_create(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
+                     int directed, const double* p, int source, int sink, int want_grad,
+                     pbat_options* opt, void* cuda_stream, pbat_plan* plan_out) {
+  try {
+    pbat::clear_error();
+    if (!plan_out) return pbat::fail(PBAT_EINVAL, "plan_out must not be NULL");
+    pbat::GraphIn g{n_nodes, n_arcs, tail, head, directed, source, sink};
+    pbat::Job* J = nullptr;
+    int rc = pbat::job_create(g, p, want_grad != 0, opt, &J);
+    if (rc) return rc;
+    if ((rc = pbat::job_upload(J, (cudaStream_t)cuda_stream)) ||
+        (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess &&
+         (rc = pbat::fail(PBAT_ECUDA, "table upload failed")))) {
+      pbat::job_destroy(J);
+      return rc;
+    }
+    pbat_plan pl = new pbat_plan_s();
+    pl->job = J;
+    pbat_options_init(&pl->opt);
+    if (opt) pl->opt = *opt;
+    *plan_out = pl;
+    return PBAT_OK;
+  } catch (...) {
+    return pbat::fail(PBAT_ENOMEM, "host exception");
+  }
+}
+
+int pbat_plan_execute(pbat_plan plan, void* cuda_stream) {
+  pbat::clear_error();
+  if (!plan) return pbat::fail(PBAT_EINVAL, "plan must not be NULL");
+  return pbat::job_launch(plan->job, (cudaStream_t)cuda_stream);
+}
+
+int pbat_plan_read(pbat_plan plan, void* cuda_stream, double* R_out, uint64_t* Nk_out,
+                   double* dRdp_out) {
+  pbat::clear_error();
+  if (!plan || !R_out) return pbat::fail(PBAT_EINVAL, "plan and R_out must not be NULL");
+  return pbat::job_read(plan->job, (cudaStream_t)cuda_stream, R_out, Nk_out,
+                        plan->job->pl.grad ? dRdp_out : nullptr, &plan->opt);
+}
+
+int pbat_plan_stats(pbat_plan plan, uint64_t* stats_out) {
+  pbat::clear_error();
+  if (!plan || !stats_out) return pbat::fail(PBAT_EINVAL, "plan and stats_out must not be NULL");
+  for (int i = 0; i < 8; ++i) stats_out[i] = plan->opt.stats[i];
+  return PBAT_OK;
+}
+
+void pbat_plan_destroy(pbat_plan plan) {
+  if (!plan) return;
+  pbat::job_destroy(plan->job);
+  delete plan;
+}
+
+const char* pbat_last_error(void) { return pbat::last_error(); }
+
+int pbat_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+}  // extern "C"

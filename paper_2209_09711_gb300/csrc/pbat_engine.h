@@ -1,0 +1,119 @@
+// pbat_engine.h -- host-side types of the PBAT engine.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include <math.h>
+
+#include "pbat.h"
+#include "pbat_num.cuh"
+
+namespace pbat {
+
+struct GraphIn {
+  int n, m;
+  const int32_t* tail;
+  const int32_t* head;
+  int directed, source, sink;
+};
+
+struct DeviceInfo {
+  int device = -1;
+  int sms = 0;
+  int smem_optin = 0;
+  int cc_major = 0, cc_minor = 0;
+};
+
+// How one network's 2^m states are split (equal division, Sec. 4.3):
+//   ell lane arcs (one pattern per warp lane), L walk arcs (Gray walk per
+//   thread), d prefix arcs (one work item per prefix value).
+struct Plan {
+  bool grad = false;
+  bool wide = false;      // n > 32: 64-bit node masks
+  int ell = 0, L = 0, d = 0;
+  int range_bits = 0;
+  int prune = 1;
+  int nthr = 128;
+  size_t smem = 0;
+  unsigned long long task_lo = 0, n_tasks = 0;
+  std::vector<int> perm;  // internal arc position -> input arc index
+};
+
+// Device + pinned host scratch, pooled across calls (one user at a time).
+struct Scratch {
+  int device = -1;
+  bool busy = false;
+  void* dmem = nullptr;
+  size_t dbytes = 0;
+  void* hmem = nullptr;
+  size_t hbytes = 0;
+};
+int scratch_acquire(int device, size_t dbytes, size_t hbytes, Scratch** out);
+void scratch_release(Scratch* s);
+
+int run_single(const GraphIn& g, const double* p, bool grad, pbat_options* opt, void* stream,
+               double* R_out, uint64_t* Nk_out, double* dRdp_out);
+
+int fail(int code, const char* fmt, ...);
+void clear_error();
+const char* last_error();
+int validate_graph(const GraphIn& g);
+int validate_p(const double* p, int m);
+int validate_options(const pbat_options* o, int m);
+int device_info(DeviceInfo& out);
+
+// ---- host numeric helpers (fixed point, double-double) ----
+typedef unsigned __int128 uint128_host;
+
+// round(x * 2^e) for a finite double x >= 0 whose result is below 2^128
+inline uint128_host scaled_round_u(double x, int e) {
+  if (x <= 0.0) return 0;
+  int ex;
+  const double mant = frexp(x, &ex);  // x = mant * 2^ex, mant in [0.5, 1)
+  const uint64_t M = (uint64_t)ldexp(mant, 53);
+  const int sh = ex - 53 + e;
+  if (sh >= 0) return (uint128_host)M << sh;
+  if (-sh >= 64) return (-sh == 64 && M >= ((uint64_t)1 << 63)) ? 1 : 0;
+  const uint64_t half = (uint64_t)1 << (-sh - 1);
+  return (uint128_host)((M + half) >> (-sh));
+}
+
+// round((v.hi + v.lo) * 2^127) for v in [0, 1]
+inline u128 to_fixed127(dd v) {
+  uint128_host r = scaled_round_u(v.hi, 127);
+  if (v.lo > 0)
+    r += scaled_round_u(v.lo, 127);
+  else if (v.lo < 0)
+    r -= scaled_round_u(-v.lo, 127);
+  return u128{(uint64_t)r, (uint64_t)(r >> 64)};
+}
+
+inline dd dd_recip(double x) {
+  // Newton step on 1/x in double-double: y1 = y0 + y0 * (1 - x y0)
+  const double y0 = 1.0 / x;
+  const dd xy = two_prod(x, y0);
+  const dd e = dd_sub(dd_make(1.0), xy);
+  return dd_add(dd_make(y0), dd_mul_d(e, y0));
+}
+
+inline dd dd_recip_dd(dd x) {
+  const double y0 = 1.0 / x.hi;
+  const dd e = dd_sub(dd_make(1.0), dd_mul_d(x, y0));
+  return dd_add(dd_make(y0), dd_mul_d(e, y0));
+}
+
+inline uint64_t binom_u64(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  uint128_host r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (uint128_host)(n - k + i) / (uint128_host)i;
+  return (uint64_t)r;
+}
+
+
+inline dd arc_w(const double* p, int arc, int bit) {
+  return bit ? dd_make(p[arc]) : dd_one_minus(p[arc]);
+}
+
+}  // namespace pbat

@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+N_k must be bit-exact.  R must agree within 1e-12 relative.  dR/dp must
+agree within 1e-12 relative where the oracle's T1/T0 condition number is
+small, otherwise within 1e-12 * max(|g*|, 1e-4 * R) (the reading of the
+1e-12 target for gradients that are cancellations of two large sums).
+Full-size workloads the oracle cannot finish in seconds are checked on
+sampled equal divisions (Sec. 4.3) -- the same division on both sides --
+and through invariants that hold at any size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+R_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_09711_gb300 import build
+    build.build()
+    import paper_2209_09711_gb300 as mod
+    return mod
+
+
+def _grad_tol(gstar, t1, t0, R):
+    kappa = (t1 + t0) / max(abs(gstar), 1e-300)
+    if kappa * 2.0**-53 <= 1e-13:
+        return 1e-12 * abs(gstar) + 1e-300
+    return 1e-12 * max(abs(gstar), 1e-4 * abs(R)) + 1e-300
+
+
+def check(res, ref, grad=False, ctx=""):
+    assert res.Nk == ref.Nk, ctx
+    assert abs(res.R - ref.R) <= R_TOL * abs(ref.R) + 1e-300, (ctx, res.R, ref.R)
+    if grad:
+        gstar = ref.grad_t1t0
+        for i, (a, b) in enumerate(zip(res.grad, gstar)):
+            tol = _grad_tol(b, ref.T1[i], ref.T0[i], ref.R)
+            assert abs(a - b) <= tol, (ctx, i, a, b, tol)
+
+
+def run(pb, net, p=None, grad=False, **opt):
+    return pb.reliability_net(net, p=p, grad=grad, opts=pb.options(**opt))
+
+
+# ---------------------------------------------------------------------------
+# small cases, whole space
+# ---------------------------------------------------------------------------
+
+def test_small_random_workload(pb):
+    net = synth.workload_small_random()
+    ref = oracle.enumerate_states(net, grad=True)
+    for prune in (1, 0):
+        for walk in (-1, 0, 3, 6, 11):
+            check(run(pb, net, grad=True, prune=prune, walk_bits=walk), ref, True,
+                  f"prune={prune} walk={walk}")
+    check(run(pb, net), ref)
+
+
+def test_paper_worked_example_and_bridge(pb):
+    for directed in (True, False):
+        net = synth.figure1(directed)
+        res = run(pb, net, grad=True)
+        assert abs(res.R - 0.960175722) < 5e-10
+        assert res.Nk == [0, 0, 1, 6, 11, 6, 1]
+        check(res, oracle.enumerate_states(net, grad=True), True)
+    res = run(pb, synth.bridge([0.9] * 5))
+    assert abs(res.R - 0.97848) < 5e-11 and res.Nk == [0, 0, 2, 8, 5, 1]
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_random_graphs(pb, directed):
+    for seed in range(30):
+        rng = synth.SplitMix64(777 + seed)
+        m = 1 + rng.below(18)
+        n = 2 + rng.below(9)
+        net = synth.random_small(5000 + seed, n=n, m=m, directed=directed, p_lo=0.02, p_hi=0.98)
+        ref = oracle.enumerate_states(net, grad=True)
+        check(run(pb, net, grad=True), ref, True, f"seed={seed}")
+        check(run(pb, net, prune=0), ref, False, f"seed={seed} noprune")
+
+
+def test_edge_cases(pb):
+    # a single s-t arc
+    net = synth.Network(2, [0], [1], [0.3], 0, 1)
+    res = run(pb, net, grad=True)
+    assert res.Nk == [0, 1] and abs(res.R - 0.3) < 1e-16 and abs(res.grad[0] - 1.0) < 1e-15
+    # sink unreachable in every state
+    net = synth.Network(4, [0, 1], [1, 0], [0.6, 0.7], 0, 3)
+    res = run(pb, net, grad=True)
+    assert res.R == 0.0 and res.Nk == [0, 0, 0] and all(g == 0.0 for g in res.grad)
+    # deterministic arcs (p = 0 and p = 1), parallel arcs, directed
+    net = synth.Network(4, [0, 0, 1, 1, 2, 0, 1], [1, 2, 2, 3, 3, 1, 3],
+                        [1.0, 0.0, 0.5, 0.25, 1.0, 0.7, 0.0], 0, 3, True)
+    check(run(pb, net, grad=True), oracle.enumerate_states(net, grad=True), True, "p01")
+    # more than 32 nodes: 64-bit node masks
+    n = 40
+    tail = list(range(n - 1)) + [0, 5, 10, 20]
+    head = list(range(1, n)) + [10, 15, 30, 39]
+    p = [0.9 - 0.01 * (k % 7) for k in range(len(tail))]
+    net = synth.Network(n, tail, head, p, 0, n - 1)
+    if net.m <= 22:
+        check(run(pb, net, grad=True), oracle.enumerate_states(net, grad=True), True, "wide")
+    else:
+        r = run(pb, net, grad=True, range_bits=net.m - 18, range_lo=3, range_hi=4)
+        ref = oracle.enumerate_states(net, prefix_bits=net.m - 18, prefix_lo=3, prefix_hi=4,
+                                      grad=True)
+        check(r, ref, True, "wide-range")
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads: sampled divisions + invariants
+# ---------------------------------------------------------------------------
+
+def _sampled(pb, net, bits, picks, grad):
+    for d in picks:
+        r = run(pb, net, grad=grad, range_bits=bits, range_lo=d, range_hi=d + 1)
+        ref = oracle.enumerate_states(net, prefix_bits=bits, prefix_lo=d, prefix_hi=d + 1,
+                                      grad=grad)
+        check(r, ref, grad, f"{net.name} division {d}/{1 << bits}")
+
+
+def test_grid_3x6_full_and_sampled(pb):
+    net = synth.workload_grid_3x6()
+    m = net.m
+    _sampled(pb, net, 12, [0, 1370, 3000, 4095], True)
+    _sampled(pb, net, 9, [300], False)
+    full = run(pb, net, grad=True)
+    N = full.Nk
+    assert all(v == 0 for v in N[:7]) and N[7] == 21 and N[m] == 1 and N[m - 1] == m
+    assert N[m - 2] == math.comb(m, 2) - 2
+    assert all(N[k] <= math.comb(m, k) for k in range(m + 1))
+    # uniform p: R(p) = sum N_k p^k (1-p)^(m-k), sum_i dR/dp_i = dR/dp
+    p = 0.9
+    poly = sum(c * p**k * (1 - p) ** (m - k) for k, c in enumerate(N))
+    dpoly = sum(c * (k * p ** (k - 1) * (1 - p) ** (m - k) - (m - k) * p**k * (1 - p) ** (m - k - 1))
+                for k, c in enumerate(N))
+    assert abs(full.R - poly) <= 1e-13
+    assert abs(sum(full.grad) - dpoly) <= 1e-12
+    # p = 1/2 ties R to the integer counts exactly
+    half = run(pb, net, p=[0.5] * m)
+    assert half.R == sum(N) / 2.0**m and half.Nk == N
+    # every split of the work gives identical counts
+    for walk in (4, 8, 12):
+        for prune in (0, 1):
+            r = run(pb, net, walk_bits=walk, prune=prune)
+            assert r.Nk == N and abs(r.R - full.R) <= 1e-14
+
+
+def test_directed_34_sampled(pb):
+    net = synth.workload_directed_20_34()
+    _sampled(pb, net, 20, [0, 400000, (1 << 20) - 1], True)
+    _sampled(pb, net, 16, [40000], False)
+    full = run(pb, net, grad=True)
+    m = net.m
+    assert full.Nk[m] == 1 and all(full.Nk[k] <= math.comb(m, k) for k in range(m + 1))
+    # partial results over a partition of the divisions add up to the whole
+    parts = [run(pb, net, grad=True, range_bits=2, range_lo=i, range_hi=i + 1) for i in range(4)]
+    assert [sum(x) for x in zip(*[q.Nk for q in parts])] == full.Nk
+    assert abs(sum(q.R for q in parts) - full.R) <= 1e-13
+    g = np.sum([q.grad for q in parts], axis=0)
+    assert np.max(np.abs(g - full.grad)) <= 1e-13
+
+
+def test_random_40_sampled(pb):
+    net = synth.workload_random_24_40()
+    _sampled(pb, net, 26, [0, 20_000_000, (1 << 26) - 1], True)
+    _sampled(pb, net, 22, [1_234_567], False)
+
+
+# ---------------------------------------------------------------------------
+# batched
+# ---------------------------------------------------------------------------
+
+def test_batched_against_oracle(pb):
+    nets, pvecs = [], []
+    for i in range(6):
+        rng = synth.SplitMix64(31 + i)
+        m = 5 + rng.below(10)
+        net = synth.random_small(900 + i, n=3 + rng.below(6), m=m, directed=bool(i & 1))
+        nets.append(net)
+        pvecs.append([synth.uniform_p(rng, m, 0.05, 0.95) for _ in range(3)])
+    R, Nk, G = pb.reliability_batched(nets, pvecs, grad=True)
+    for g, net in enumerate(nets):
+        for k in range(3):
+            ref = oracle.enumerate_states(net, p=pvecs[g][k], grad=True)
+            assert Nk[g] == ref.Nk
+            assert abs(R[g][k] - ref.R) <= R_TOL * ref.R + 1e-300
+            for i in range(net.m):
+                assert abs(G[g][k][i] - ref.grad_t1t0[i]) <= _grad_tol(
+                    ref.grad_t1t0[i], ref.T1[i], ref.T0[i], ref.R)
+
+
+def test_batched_workload_matches_single(pb):
+    nets, pvecs = synth.workload_batched()
+    R, Nk, _ = pb.reliability_batched(nets, pvecs)
+    R2, Nk2, _ = pb.reliability_batched(nets, pvecs)  # replayed CUDA graph
+    assert np.array_equal(R, R2) and Nk == Nk2
+    small = sorted(range(len(nets)), key=lambda g: nets[g].m)[:3]
+    for g in small:
+        for k in (0, 7, 15):
+            r = pb.reliability_net(nets[g], p=pvecs[g][k])
+            assert r.Nk == Nk[g]
+            assert abs(r.R - R[g][k]) <= 1e-13 * r.R
+
+
+# ---------------------------------------------------------------------------
+# failure path and autograd
+# ---------------------------------------------------------------------------
+
+def test_time_budget_returns_etimeout_and_context_survives(pb):
+    net = synth.workload_random_24_40()
+    with pytest.raises(pb.PbatError) as e:
+        run(pb, net, time_budget_s=0.002, prune=0)
+    assert "PBAT_ETIMEOUT" in str(e.value)
+    res = run(pb, synth.bridge([0.9] * 5))
+    assert abs(res.R - 0.97848) < 5e-11
+
+
+def test_autograd_function(pb):
+    import torch
+    net = synth.workload_small_random()
+    p = torch.tensor(net.p, dtype=torch.float64, device="cuda", requires_grad=True)
+    R = pb.PBATReliability.apply(p, net)
+    R.backward()
+    ref = oracle.enumerate_states(net, grad=True)
+    assert abs(R.item() - ref.R) <= R_TOL * ref.R
+    gref = ref.grad_t1t0
+    for i in range(net.m):
+        assert abs(p.grad[i].item() - gref[i]) <= _grad_tol(gref[i], ref.T1[i], ref.T0[i], ref.R)
+    # R is affine in each p_i: central differences are exact up to rounding
+    q = torch.tensor(net.p[:], dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda x: pb.PBATReliability.apply(x, net), (q,),
+                                    eps=1e-4, atol=1e-9, rtol=1e-7)
