@@ -161,6 +161,33 @@ void pbat_plan_destroy(pbat_plan plan);
  * the last pbat_plan_read) into stats_out[8]. */
 int pbat_plan_stats(pbat_plan plan, uint64_t* stats_out);
 
+/*
+ * pbat_reliability_noalloc -- R and N_k exactly as pbat_reliability computes
+ * them, for callers that cannot allocate device memory: code whose device
+ * memory belongs to a framework's caching allocator or is capped per
+ * process, and latency-critical paths that must not stall on an
+ * allocation.  The paper has no counterpart; this is an engineering entry
+ * point of this library.
+ *
+ * It calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating
+ * routine.  Its scratch is one static 512 KiB device array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Limits that follow from that size: opt->walk_bits <= 12 (a larger
+ * value returns PBAT_ERANGE), and the persistent grid is capped at the
+ * number of per-block partials that fit.  The gradient is not offered here.
+ *   arguments, layout and ownership: as pbat_reliability (host arrays in and
+ *   out; opt nullable, algo must be AUTO or FRONTIER; opt->stats untouched)
+ * The first call on each device looks up the array's device address (once
+ * per device, with that device current); make that first call before any
+ * stream capture.  Every call shares the one array: calls whose work
+ * overlaps on the GPU (concurrent host threads, or several streams) race
+ * and give wrong results, so serialise them.
+ */
+int pbat_reliability_noalloc(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
+                             int directed, const double* p, int source, int sink,
+                             const pbat_options* opt, void* cuda_stream, double* R_out,
+                             uint64_t* Nk_out);
+
 /* Thread-local description of the last error in this thread ("" if none). */
 const char* pbat_last_error(void);
 

@@ -80,7 +80,8 @@ _lib = None
 EXPORTED = [
     "pbat_options_init", "pbat_reliability", "pbat_reliability_grad",
     "pbat_reliability_batched", "pbat_plan_create", "pbat_plan_execute", "pbat_plan_read",
-    "pbat_plan_destroy", "pbat_plan_stats", "pbat_last_error", "pbat_version",
+    "pbat_plan_destroy", "pbat_plan_stats", "pbat_reliability_noalloc", "pbat_last_error",
+    "pbat_version",
 ]
 
 
@@ -118,6 +119,8 @@ def load(path: Optional[str] = None):
         lib.pbat_plan_stats.restype = I
         lib.pbat_plan_destroy.argtypes = [V]
         lib.pbat_plan_destroy.restype = None
+        lib.pbat_reliability_noalloc.argtypes = [I, I, PI32, PI32, I, PD, I, I, PO, V, PD, PU]
+        lib.pbat_reliability_noalloc.restype = I
         lib.pbat_last_error.argtypes = []
         lib.pbat_last_error.restype = ctypes.c_char_p
         lib.pbat_version.argtypes = []
