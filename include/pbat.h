@@ -40,6 +40,7 @@
 #ifndef PBAT_H
 #define PBAT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -187,6 +188,19 @@ int pbat_reliability_noalloc(int n_nodes, int n_arcs, const int32_t* tail, const
                              int directed, const double* p, int source, int sink,
                              const pbat_options* opt, void* cuda_stream, double* R_out,
                              uint64_t* Nk_out);
+
+/*
+ * Diagnostic, no GPU needed: the CUDA C++ source the engine generates and
+ * compiles (NVRTC) for the bit-sliced kernel of this network and options --
+ * the per-graph connectivity program of the PLSA test (Sec. 3.2) as
+ * straight-line Boolean elimination on 32-state words, inside the kernel
+ * template.  The first line lists the internal arc order.  Writes at most
+ * cap bytes (NUL-terminated) to buf (nullable) and returns the full length,
+ * or a negative PBAT_E* code.
+ */
+int pbat_kernel_source(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
+                       int directed, int source, int sink, const pbat_options* opt, char* buf,
+                       size_t cap);
 
 /* Thread-local description of the last error in this thread ("" if none). */
 const char* pbat_last_error(void);

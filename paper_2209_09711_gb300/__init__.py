@@ -80,8 +80,8 @@ _lib = None
 EXPORTED = [
     "pbat_options_init", "pbat_reliability", "pbat_reliability_grad",
     "pbat_reliability_batched", "pbat_plan_create", "pbat_plan_execute", "pbat_plan_read",
-    "pbat_plan_destroy", "pbat_plan_stats", "pbat_reliability_noalloc", "pbat_last_error",
-    "pbat_version",
+    "pbat_plan_destroy", "pbat_plan_stats", "pbat_reliability_noalloc", "pbat_kernel_source",
+    "pbat_last_error", "pbat_version",
 ]
 
 
@@ -121,6 +121,9 @@ def load(path: Optional[str] = None):
         lib.pbat_plan_destroy.restype = None
         lib.pbat_reliability_noalloc.argtypes = [I, I, PI32, PI32, I, PD, I, I, PO, V, PD, PU]
         lib.pbat_reliability_noalloc.restype = I
+        lib.pbat_kernel_source.argtypes = [I, I, PI32, PI32, I, I, I, PO, ctypes.c_char_p,
+                                           ctypes.c_size_t]
+        lib.pbat_kernel_source.restype = I
         lib.pbat_last_error.argtypes = []
         lib.pbat_last_error.restype = ctypes.c_char_p
         lib.pbat_version.argtypes = []
@@ -280,6 +283,22 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def kernel_source(net, opts: Optional[Options] = None) -> str:
+    """The generated CUDA source of the bit-sliced kernel for a network."""
+    lib = load()
+    t, tp = _i32(net.tail)
+    h, hp = _i32(net.head)
+    o = opts if opts is not None else options()
+    n = lib.pbat_kernel_source(net.n, len(t), tp, hp, int(net.directed), net.source, net.sink,
+                               ctypes.byref(o), None, 0)
+    if n < 0:
+        _check(n)
+    buf = ctypes.create_string_buffer(n + 1)
+    lib.pbat_kernel_source(net.n, len(t), tp, hp, int(net.directed), net.source, net.sink,
+                           ctypes.byref(o), buf, n + 1)
+    return buf.value.decode()
 
 
 def version() -> int:

@@ -1,0 +1,503 @@
+// pbat_bitslice.cu -- planner, code generator and launcher of the
+// bit-sliced enumeration kernel.
+//
+// Connectivity as Boolean elimination.  For a fixed assignment of the
+// non-lane arcs, each node pair (u, v) carries a 32-bit word E[u][v]: bit j
+// set iff the pair is joined by a working arc in lane state j.  Eliminating
+// a node k (neither source nor sink) replaces every path i -> k -> j by the
+// shortcut E[i][j] |= E[i][k] & E[k][j] -- Gaussian elimination over the
+// Boolean semiring, i.e. Floyd-Warshall restricted to the graph's sparsity.
+// After every other node is gone, E[s][t] holds, for all 32 lane states at
+// once, whether the sink is reachable from the source: the PLSA answer of
+// Sec. 3.2, thirty-two states per 32-bit operation.  Loops the paper
+// excludes never arise (i != j), and for directed graphs edges into the
+// source or out of the sink are dropped (no s-t path uses them).
+//
+// The elimination program is specialised per graph and compiled with NVRTC,
+// so every word lives in a register.  Nodes that touch no walk arc are
+// eliminated first: those operations do not depend on the Gray walk and run
+// once per work item (bs_inv); only the small "core" left around the source,
+// the sink and the walk arcs is eliminated per word (bs_var).
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "pbat.h"
+#include "pbat_bs_template.h"
+#include "pbat_engine.h"
+#include "pbat_internal.h"
+
+namespace pbat {
+
+// Host mirror of BsParams in the kernel source (same field order and types).
+struct BsParamsHost {
+  unsigned long long task_lo, n_tasks, budget_ns;
+  int prune, pad;
+  double p[64];
+  dd q[64];
+  dd thr_w[32];
+  unsigned long long binom[64];
+};
+
+// ---------------------------------------------------------------------------
+// elimination program builder
+// ---------------------------------------------------------------------------
+class Elim {
+ public:
+  Elim(int n, bool directed, int s, int t) : n_(n), dir_(directed), s_(s), t_(t), E_(n * n) {}
+
+  bool has(int i, int j) const { return !at(i, j).empty(); }
+  const std::string& at(int i, int j) const {
+    if (!dir_ && i > j) std::swap(i, j);
+    return E_[i * n_ + j];
+  }
+  // E[i][j] |= expr
+  void or_in(int i, int j, const std::string& expr) {
+    if (i == j) return;
+    if (dir_ && (j == s_ || i == t_)) return;  // no s-t path enters s or leaves t
+    std::string& e = ref(i, j);
+    const std::string v = "v" + std::to_string(nvar_++);
+    if (e.empty())
+      code_ += "  const u32 " + v + " = " + expr + ";\n";
+    else
+      code_ += "  const u32 " + v + " = " + e + " | " + expr + ";\n";
+    e = v;
+  }
+  void set(int i, int j, const std::string& v) { ref(i, j) = v; }
+  int degree(int k) const {
+    int d = 0;
+    for (int i = 0; i < n_; ++i)
+      if (i != k && (has(i, k) || (dir_ && has(k, i)))) ++d;
+    return d;
+  }
+  // cost of eliminating k now (number of shortcut operations)
+  int cost(int k) const {
+    int in = 0, out = 0;
+    for (int i = 0; i < n_; ++i) {
+      if (i == k) continue;
+      if (has(i, k)) ++in;
+      if (dir_ && has(k, i)) ++out;
+    }
+    return dir_ ? in * out : in * (in - 1) / 2;
+  }
+  void eliminate(int k) {
+    std::vector<int> in, out;
+    for (int i = 0; i < n_; ++i) {
+      if (i == k) continue;
+      if (has(i, k)) in.push_back(i);
+      if (dir_ && has(k, i)) out.push_back(i);
+    }
+    if (!dir_) out = in;
+    for (int i : in)
+      for (int j : out) {
+        if (i == j || (!dir_ && i > j)) continue;
+        or_in(i, j, "(" + at(i, k) + " & " + at(k, j) + ")");
+        ++ops_;
+      }
+    for (int i = 0; i < n_; ++i) {
+      if (i == k) continue;
+      ref(i, k).clear();
+      ref(k, i).clear();
+    }
+  }
+  // min-cost elimination of the given nodes (greedy, recomputed each step)
+  void eliminate_all(std::vector<int> nodes) {
+    while (!nodes.empty()) {
+      size_t best = 0;
+      int bc = cost(nodes[0]);
+      for (size_t x = 1; x < nodes.size(); ++x) {
+        const int c = cost(nodes[x]);
+        if (c < bc) bc = c, best = x;
+      }
+      eliminate(nodes[best]);
+      nodes.erase(nodes.begin() + best);
+    }
+  }
+  std::vector<std::pair<int, int>> edges() const {
+    std::vector<std::pair<int, int>> r;
+    for (int i = 0; i < n_; ++i)
+      for (int j = 0; j < n_; ++j) {
+        if (!dir_ && j <= i) continue;
+        if (i != j && has(i, j)) r.emplace_back(i, j);
+      }
+    return r;
+  }
+  std::string& code() { return code_; }
+  int ops() const { return ops_; }
+
+ private:
+  std::string& ref(int i, int j) {
+    if (!dir_ && i > j) std::swap(i, j);
+    return E_[i * n_ + j];
+  }
+  int n_;
+  bool dir_;
+  int s_, t_;
+  std::vector<std::string> E_;
+  std::string code_;
+  int nvar_ = 0, ops_ = 0;
+};
+
+// ---------------------------------------------------------------------------
+// plan: which arcs are lane / thread / walk / prefix arcs
+// ---------------------------------------------------------------------------
+struct BsPlan {
+  int ell = 0, tb = 0, L = 0, d = 0, r = 0;
+  std::vector<int> perm;  // internal position -> input arc
+  std::string gen;        // generated bs_inv / bs_var
+  int ncore = 0, ops_inv = 0, ops_var = 0;
+};
+
+static std::vector<int> bfs_dist(const GraphIn& g, int src) {
+  std::vector<std::vector<int>> adj(g.n);
+  for (int k = 0; k < g.m; ++k) {
+    adj[g.tail[k]].push_back(g.head[k]);
+    adj[g.head[k]].push_back(g.tail[k]);
+  }
+  std::vector<int> d(g.n, 1 << 20);
+  std::queue<int> q;
+  d[src] = 0;
+  q.push(src);
+  while (!q.empty()) {
+    const int u = q.front();
+    q.pop();
+    for (int v : adj[u])
+      if (d[v] > d[u] + 1) {
+        d[v] = d[u] + 1;
+        q.push(v);
+      }
+  }
+  return d;
+}
+
+// Generate bs_inv / bs_var for a given role assignment; returns bs_var's op count.
+static void bs_generate(const GraphIn& g, BsPlan& bp) {
+  const int m = g.m, top = bp.ell + bp.tb + bp.L, w0 = bp.ell + bp.tb;
+  std::vector<bool> core(g.n, false);
+  core[g.source] = core[g.sink] = true;
+  for (int k = w0; k < top; ++k) {
+    const int a = bp.perm[k];
+    core[g.tail[a]] = core[g.head[a]] = true;
+  }
+  // phase A: every arc but the walk arcs, then every non-core node
+  Elim A(g.n, g.directed != 0, g.source, g.sink);
+  for (int k = 0; k < m; ++k) {
+    if (k >= w0 && k < top) continue;
+    const int a = bp.perm[k];
+    const std::string w = "a[" + std::to_string(k) + "]";
+    A.or_in(g.tail[a], g.head[a], w);
+    if (!g.directed) continue;
+  }
+  std::vector<int> outer;
+  for (int v = 0; v < g.n; ++v)
+    if (!core[v]) outer.push_back(v);
+  A.eliminate_all(outer);
+  const auto ce = A.edges();
+  std::string inv = "__device__ __forceinline__ void bs_inv(const u32* a, u32* e) {\n" + A.code();
+  // phase B: the core edges plus the walk arcs, then the core nodes
+  Elim B(g.n, g.directed != 0, g.source, g.sink);
+  for (size_t x = 0; x < ce.size(); ++x) {
+    inv += "  e[" + std::to_string(x) + "] = " + A.at(ce[x].first, ce[x].second) + ";\n";
+    B.set(ce[x].first, ce[x].second, "e[" + std::to_string(x) + "]");
+  }
+  inv += "}\n";
+  for (int k = w0; k < top; ++k) {
+    const int a = bp.perm[k];
+    B.or_in(g.tail[a], g.head[a], "w[" + std::to_string(k - w0) + "]");
+  }
+  std::vector<int> inner;
+  for (int v = 0; v < g.n; ++v)
+    if (core[v] && v != g.source && v != g.sink) inner.push_back(v);
+  B.eliminate_all(inner);
+  std::string var = "__device__ __forceinline__ u32 bs_var(const u32* e, const u32* w) {\n" + B.code();
+  var += "  return " + (B.has(g.source, g.sink) ? B.at(g.source, g.sink) : std::string("0u")) + ";\n}\n";
+  bp.gen = inv + var;
+  bp.ncore = (int)ce.size();
+  bp.ops_inv = A.ops();
+  bp.ops_var = B.ops() + bp.L;
+}
+
+int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp) {
+  const int m = g.m, r = o.range_bits;
+  bp.r = r;
+  bp.ell = std::min(kMaxLaneBits, m - r);
+  bp.tb = std::min(5, m - r - bp.ell);
+  const int free_bits = m - r - bp.ell - bp.tb;
+  const int lmax = 10;
+  if (o.walk_bits >= 0) {
+    bp.L = std::min(std::min(o.walk_bits, lmax), free_bits);
+  } else if (o.prefix_bits >= 0) {
+    bp.L = std::max(0, std::min(lmax, m - bp.ell - bp.tb - std::max(o.prefix_bits, r)));
+  } else {
+    // enough work items (one per warp at a time) to fill the GPU several times
+    bp.L = std::max(0, std::min(lmax, free_bits - std::max(0, 14 - r)));
+  }
+  bp.d = m - bp.ell - bp.tb - bp.L;
+  (void)nthr;
+  // ---- roles.  range arcs are the top prefix bits in input order.
+  std::vector<int> cand;
+  for (int a = r; a < m; ++a) cand.push_back(a);
+  // walk arcs: a compact cluster grown from {source, sink}, so the per-word
+  // core stays small
+  std::vector<bool> incore(g.n, false), used(m, false);
+  incore[g.source] = incore[g.sink] = true;
+  std::vector<int> walk;
+  for (int it = 0; it < bp.L; ++it) {
+    int best = -1, bscore = 1 << 30;
+    for (int a : cand) {
+      if (used[a]) continue;
+      const int add = (!incore[g.tail[a]]) + (!incore[g.head[a]]);
+      if (add < bscore) bscore = add, best = a;
+    }
+    used[best] = true;
+    walk.push_back(best);
+    incore[g.tail[best]] = incore[g.head[best]] = true;
+  }
+  // prefix arcs: the arcs nearest to the source or the sink (they decide the
+  // prune), among the rest
+  const std::vector<int> ds = bfs_dist(g, g.source), dt = bfs_dist(g, g.sink);
+  std::vector<int> rest;
+  for (int a : cand)
+    if (!used[a]) rest.push_back(a);
+  std::stable_sort(rest.begin(), rest.end(), [&](int x, int y) {
+    const int dx = std::min(std::min(ds[g.tail[x]], ds[g.head[x]]), std::min(dt[g.tail[x]], dt[g.head[x]]));
+    const int dy = std::min(std::min(ds[g.tail[y]], ds[g.head[y]]), std::min(dt[g.tail[y]], dt[g.head[y]]));
+    return dx < dy;
+  });
+  const int npre_free = bp.d - r;
+  bp.perm.assign(m, -1);
+  // prefix positions [top, m - r): nearest arcs; range arcs at [m - r, m)
+  const int top = bp.ell + bp.tb + bp.L;
+  for (int j = 0; j < npre_free; ++j) bp.perm[top + j] = rest[j];
+  for (int i = 0; i < r; ++i) bp.perm[m - 1 - i] = i;
+  for (int b = 0; b < bp.L; ++b) bp.perm[bp.ell + bp.tb + b] = walk[b];
+  int x = npre_free;
+  for (int k = 0; k < bp.ell + bp.tb; ++k) bp.perm[k] = rest[x++];
+  bs_generate(g, bp);
+  return PBAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// NVRTC compile cache
+// ---------------------------------------------------------------------------
+struct JitEntry {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kernel = nullptr;
+  int regs = 0;
+};
+static std::mutex g_jit_mu;
+static std::map<std::string, JitEntry> g_jit;
+
+static int jit_compile(const std::string& src, const DeviceInfo& dev, JitEntry* out) {
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  auto it = g_jit.find(src);
+  if (it != g_jit.end()) {
+    *out = it->second;
+    return PBAT_OK;
+  }
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "pbat_bitslice_gen.cu", 0, nullptr, nullptr) !=
+      NVRTC_SUCCESS)
+    return fail(PBAT_ECUDA, "nvrtcCreateProgram failed");
+  const std::string arch = "-arch=sm_" + std::to_string(dev.cc_major * 10 + dev.cc_minor) + "a";
+  const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo"};
+  const nvrtcResult rc = nvrtcCompileProgram(prog, 3, opts);
+  if (rc != NVRTC_SUCCESS) {
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) nvrtcGetProgramLog(prog, &log[0]);
+    nvrtcDestroyProgram(&prog);
+    if (log.size() > 400) log.resize(400);
+    return fail(PBAT_ECUDA, "NVRTC compile of the bit-sliced kernel failed: %s %s",
+                nvrtcGetErrorString(rc), log.c_str());
+  }
+  size_t cs = 0;
+  nvrtcGetCUBINSize(prog, &cs);
+  std::vector<char> cubin(cs);
+  nvrtcGetCUBIN(prog, cubin.data());
+  nvrtcDestroyProgram(&prog);
+  JitEntry e;
+  cudaError_t ce = cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (ce != cudaSuccess) return fail(PBAT_ECUDA, "cudaLibraryLoadData: %s", cudaGetErrorString(ce));
+  ce = cudaLibraryGetKernel(&e.kernel, e.lib, "bs_kernel");
+  if (ce != cudaSuccess) return fail(PBAT_ECUDA, "cudaLibraryGetKernel: %s", cudaGetErrorString(ce));
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, (const void*)e.kernel) == cudaSuccess) e.regs = fa.numRegs;
+  else cudaGetLastError();
+  g_jit.emplace(src, e);
+  *out = e;
+  return PBAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tables and launch
+// ---------------------------------------------------------------------------
+struct BsLaunch {
+  BsPlan plan;
+  BsParamsHost P;
+  std::vector<unsigned long long> lane_tab;  // [4][256][3]
+  std::vector<unsigned long long> wmid;      // [2^L]
+  JitEntry jit;
+  int nthr = 128;
+  size_t smem = 0;
+  int per_sm = 1;
+};
+
+static unsigned long long fixed_u64(dd v, int scale) {
+  // round((hi + lo) * 2^scale) for 0 <= v, result < 2^64
+  uint128_host r = scaled_round_u(v.hi, scale);
+  if (v.lo > 0)
+    r += scaled_round_u(v.lo, scale);
+  else if (v.lo < 0)
+    r -= scaled_round_u(-v.lo, scale);
+  return (unsigned long long)r;
+}
+
+static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
+  char defs[512];
+  const unsigned lane_mask = bp.ell >= 5 ? 0xffffffffu : ((1u << (1 << bp.ell)) - 1u);
+  snprintf(defs, sizeof defs,
+           "#define BS_M %d\n#define BS_ELL %d\n#define BS_TB %d\n#define BS_L %d\n#define BS_D %d\n"
+           "#define BS_NTHR %d\n#define BS_WALK0 %d\n#define BS_TOP %d\n#define BS_NCORE %d\n"
+           "#define BS_LANE_MASK 0x%08xu\n",
+           g.m, bp.ell, bp.tb, bp.L, bp.d, nthr, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, bp.ncore,
+           lane_mask);
+  const std::string tmpl = kBsTemplate;
+  const size_t cut = tmpl.find("//@@GENERATED@@");
+  return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tmpl.substr(cut);
+}
+
+// Generated source for a network (no device needed); see pbat_kernel_source.
+int bs_source_for(const GraphIn& g, const pbat_options& o, std::string& out) {
+  BsPlan bp;
+  const int nthr = o.block_threads > 0 ? o.block_threads : 128;
+  int rc = bs_make_plan(g, o, nthr, bp);
+  if (rc) return rc;
+  char perm[64 * 4 + 64] = "// internal arc -> input arc:";
+  for (int k = 0; k < g.m; ++k) snprintf(perm + strlen(perm), 8, " %d", bp.perm[k]);
+  out = std::string(perm) + "\n" + bs_source(g, bp, nthr);
+  return PBAT_OK;
+}
+
+int bs_prepare(const GraphIn& g, const double* p, const pbat_options& o, const DeviceInfo& dev,
+               BsLaunch& bl) {
+  bl.nthr = o.block_threads > 0 ? o.block_threads : 128;
+  int rc = bs_make_plan(g, o, bl.nthr, bl.plan);
+  if (rc) return rc;
+  const BsPlan& bp = bl.plan;
+  const int m = g.m, top = bp.ell + bp.tb + bp.L;
+  const std::string src = bs_source(g, bp, bl.nthr);
+  if ((rc = jit_compile(src, dev, &bl.jit))) return rc;
+  // parameters
+  BsParamsHost& P = bl.P;
+  memset(&P, 0, sizeof P);
+  P.prune = o.prune ? 1 : 0;
+  P.budget_ns = o.time_budget_s > 0 ? (unsigned long long)(o.time_budget_s * 1e9) : 0ull;
+  for (int k = 0; k < m; ++k) {
+    P.p[k] = p[bp.perm[k]];
+    P.q[k] = dd_one_minus(p[bp.perm[k]]);
+  }
+  for (int j = 0; j < 32; ++j) {
+    if (j >= (1 << bp.tb)) continue;
+    dd w = dd_make(1.0);
+    for (int i = 0; i < bp.tb; ++i) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + i], (j >> i) & 1));
+    P.thr_w[j] = w;
+  }
+  for (int j = 0; j < 64; ++j) P.binom[j] = binom_u64(top, j);
+  unsigned long long lo = 0, hi = 1ull << bp.d;
+  if (bp.r > 0) {
+    lo = o.range_lo << (bp.d - bp.r);
+    hi = o.range_hi << (bp.d - bp.r);
+  }
+  P.task_lo = lo;
+  P.n_tasks = hi - lo;
+  // lane tables: byte position b, value v -> lane mass (scale 2^62) and
+  // packed counts by lane popcount class (21-bit fields; classes 0-2, 3-5)
+  bl.lane_tab.assign(4 * 256 * 3, 0ull);
+  dd lw[32];
+  for (int j = 0; j < 32; ++j) {
+    lw[j] = dd{0.0, 0.0};
+    if (j >= (1 << bp.ell)) continue;
+    dd w = dd_make(1.0);
+    for (int i = 0; i < bp.ell; ++i) w = dd_mul(w, arc_w(p, bp.perm[i], (j >> i) & 1));
+    lw[j] = w;
+  }
+  for (int b = 0; b < 4; ++b)
+    for (int v = 0; v < 256; ++v) {
+      dd s = dd{0.0, 0.0};
+      unsigned long long n0 = 0, n1 = 0;
+      for (int k = 0; k < 8; ++k) {
+        if (!((v >> k) & 1)) continue;
+        const int j = 8 * b + k;
+        if (j >= (1 << bp.ell)) continue;
+        s = dd_add(s, lw[j]);
+        const int cl = __builtin_popcount((unsigned)j);
+        if (cl < 3)
+          n0 += 1ull << (21 * cl);
+        else
+          n1 += 1ull << (21 * (cl - 3));
+      }
+      unsigned long long* e = &bl.lane_tab[(b * 256 + v) * 3];
+      e[0] = fixed_u64(s, 62);
+      e[1] = n0;
+      e[2] = n1;
+    }
+  bl.wmid.resize((size_t)1 << bp.L);
+  for (int gi = 0; gi < (1 << bp.L); ++gi) {
+    dd w = dd_make(1.0);
+    for (int b = 0; b < bp.L; ++b) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + bp.tb + b], (gi >> b) & 1));
+    bl.wmid[gi] = fixed_u64(w, 63);
+  }
+  bl.smem = (size_t)(4 * 256 * 3 + (1 << bp.L) + (bp.L + 1) * 2 * bl.nthr) * 8 +
+            (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
+  if (bl.smem > (size_t)dev.smem_optin)
+    return fail(PBAT_ERANGE, "bit-sliced kernel needs %zu B of shared memory", bl.smem);
+  cudaError_t e = cudaFuncSetAttribute((const void*)bl.jit.kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bl.smem);
+  if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)bl.jit.kernel, bl.nthr,
+                                                    bl.smem);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  bl.per_sm = per_sm;
+  return PBAT_OK;
+}
+
+cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st,
+                      const unsigned long long* d_lane, const unsigned long long* d_wmid,
+                      const DevWork& W) {
+  const BsParamsHost& P = bl.P;
+  void* args[] = {(void*)&P, (void*)&d_lane, (void*)&d_wmid, (void*)&W};
+  return cudaLaunchKernel((const void*)bl.jit.kernel, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
+}
+
+// accessors used by the engine
+const std::vector<int>& bs_perm(const BsLaunch& bl) { return bl.plan.perm; }
+unsigned long long bs_items(const BsLaunch& bl) { return bl.P.n_tasks; }
+unsigned long long bs_item_states(const BsLaunch& bl) {
+  return 1ull << (bl.plan.ell + bl.plan.tb + bl.plan.L);
+}
+int bs_per_sm(const BsLaunch& bl) { return bl.per_sm; }
+int bs_nthr(const BsLaunch& bl) { return bl.nthr; }
+const std::vector<unsigned long long>& bs_lane_tab(const BsLaunch& bl) { return bl.lane_tab; }
+const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl) { return bl.wmid; }
+BsLaunch* bs_new() { return new BsLaunch(); }
+void bs_delete(BsLaunch* b) { delete b; }
+void bs_describe(const BsLaunch& bl, int* out6) {
+  out6[0] = bl.plan.ell; out6[1] = bl.plan.tb; out6[2] = bl.plan.L; out6[3] = bl.plan.d;
+  out6[4] = bl.plan.ops_inv; out6[5] = bl.plan.ops_var;
+}
+
+}  // namespace pbat

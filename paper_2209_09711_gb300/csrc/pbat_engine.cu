@@ -34,6 +34,24 @@ cudaError_t launch_frontier(bool grad, bool wide, int grid, int nthr, size_t sme
                             const DevWork& W);
 cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int m);
 
+struct BsLaunch;
+BsLaunch* bs_new();
+void bs_delete(BsLaunch* b);
+int bs_prepare(const GraphIn& g, const double* p, const pbat_options& o, const DeviceInfo& dev,
+               BsLaunch& bl);
+cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st,
+                      const unsigned long long* d_lane, const unsigned long long* d_wmid,
+                      const DevWork& W);
+const std::vector<int>& bs_perm(const BsLaunch& bl);
+unsigned long long bs_items(const BsLaunch& bl);
+unsigned long long bs_item_states(const BsLaunch& bl);
+int bs_per_sm(const BsLaunch& bl);
+int bs_nthr(const BsLaunch& bl);
+const std::vector<unsigned long long>& bs_lane_tab(const BsLaunch& bl);
+const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl);
+void bs_describe(const BsLaunch& bl, int* out6);
+int bs_source_for(const GraphIn& g, const pbat_options& o, std::string& out);
+
 // ---------------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------------
@@ -348,9 +366,43 @@ struct Job {
   // last read (so a caller can time many launches and read once)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
   size_t n_pending = 0;
+  // bit-sliced kernel (R and N_k); null for the frontier kernel
+  BsLaunch* bs = nullptr;
+  unsigned long long* d_lane = nullptr;
+  unsigned long long* d_wmid64 = nullptr;
+  double abs_err_bound = 0.0;  // of R, relative to the enumerated probability mass
+  double mass = 1.0;           // probability mass of the enumerated states
+  std::vector<int> perm;       // internal arc position -> input arc
+  unsigned long long item_states = 0, n_items = 0;
+  int grid_nthr = 128;
+  // the inputs, kept to re-run the exact frontier kernel when R is too small
+  // for the bit-sliced kernel's fixed-point error bound
+  std::vector<int32_t> tail_copy, head_copy;
+  std::vector<double> p_copy;
+  pbat_options opt_copy;
 };
 
 static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Probability mass of the states an enumeration covers: 1 for the whole
+// space, else the mass of the prefixes [range_lo, range_hi) of the first
+// range_bits input arcs (a digit-by-digit sum, O(range_bits)).
+double range_mass(int m, const double* p, const pbat_options& o) {
+  (void)m;
+  if (o.range_bits <= 0) return 1.0;
+  const int r = o.range_bits;
+  auto below = [&](unsigned long long x) {  // mass of prefixes < x (x <= 2^r)
+    if (x >= (1ull << r)) return 1.0L;
+    long double acc = 0.0L, run = 1.0L;
+    for (int i = 0; i < r; ++i) {  // input arc i is bit r-1-i of the prefix
+      const int bit = (int)((x >> (r - 1 - i)) & 1ull);
+      if (bit) acc += run * (1.0L - (long double)p[i]);
+      run *= bit ? (long double)p[i] : 1.0L - (long double)p[i];
+    }
+    return acc;
+  };
+  return (double)(below(o.range_hi) - below(o.range_lo));
+}
 
 int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, Job** out) {
   pbat_options o;
@@ -360,25 +412,55 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   if ((rc = validate_graph(g))) return rc;
   if ((rc = validate_p(p, g.m))) return rc;
   if ((rc = validate_options(opt, g.m))) return rc;
-  if (o.algo == PBAT_ALGO_BITSLICE)
-    return fail(PBAT_ENOTSUP, "the bit-sliced kernel is not available in this build");
+  const bool use_bs = o.algo == PBAT_ALGO_BITSLICE || (o.algo == PBAT_ALGO_AUTO && !grad);
+  if (use_bs && grad)
+    return fail(PBAT_ENOTSUP, "the bit-sliced kernel computes R and N_k only");
   std::unique_ptr<Job> J(new Job());
   J->g = g;
+  J->tail_copy.assign(g.tail, g.tail + g.m);
+  J->head_copy.assign(g.head, g.head + g.m);
+  J->g.tail = J->tail_copy.data();
+  J->g.head = J->head_copy.data();
+  J->p_copy.assign(p, p + g.m);
+  J->opt_copy = o;
+  J->mass = range_mass(g.m, p, o);
   if ((rc = device_info(J->dev))) return rc;
-  if ((rc = make_plan(g, p, grad, o, J->dev, J->pl))) return rc;
   std::vector<u128> wmid;
-  build_params(g, p, J->pl, o, J->P, wmid);
-
-  const void* kfn = frontier_kernel_ptr(grad, J->pl.wide);
-  PBAT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)J->pl.smem));
-  int per_sm = 0;
-  PBAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, J->pl.nthr, J->pl.smem));
-  if (per_sm < 1) return fail(PBAT_ERANGE, "frontier kernel cannot be resident (smem %zu B)", J->pl.smem);
-  const long long warps_per_block = J->pl.nthr / 32;
+  int per_sm = 0, nthr = 128;
+  unsigned long long n_items = 0;
+  if (use_bs) {
+    J->bs = bs_new();
+    if ((rc = bs_prepare(g, p, o, J->dev, *J->bs))) return rc;
+    J->perm = bs_perm(*J->bs);
+    per_sm = bs_per_sm(*J->bs);
+    nthr = bs_nthr(*J->bs);
+    n_items = bs_items(*J->bs);
+    J->item_states = bs_item_states(*J->bs);
+    int d6[6];
+    bs_describe(*J->bs, d6);
+    J->abs_err_bound = ldexp(1.0, -61) + ldexp(1.0, d6[2] - 64);
+    J->pl.grad = false;
+  } else {
+    if ((rc = make_plan(g, p, grad, o, J->dev, J->pl))) return rc;
+    build_params(g, p, J->pl, o, J->P, wmid);
+    J->perm = J->pl.perm;
+    const void* kfn = frontier_kernel_ptr(grad, J->pl.wide);
+    PBAT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)J->pl.smem));
+    PBAT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, J->pl.nthr, J->pl.smem));
+    if (per_sm < 1)
+      return fail(PBAT_ERANGE, "frontier kernel cannot be resident (smem %zu B)", J->pl.smem);
+    nthr = J->pl.nthr;
+    n_items = J->pl.n_tasks;
+    J->item_states = 1ull << (J->pl.ell + J->pl.L);
+    J->abs_err_bound = ldexp(1.0, -100);
+  }
+  J->n_items = n_items;
+  J->grid_nthr = nthr;
+  const long long warps_per_block = nthr / 32;
   long long grid = (long long)per_sm * J->dev.sms;
   // never more warps than work items
-  const long long need = ((long long)std::min<unsigned long long>(J->pl.n_tasks, 1ull << 40) +
+  const long long need = ((long long)std::min<unsigned long long>(n_items, 1ull << 40) +
                           warps_per_block - 1) / warps_per_block;
   grid = std::max(1LL, std::min(grid, need));
   J->grid = (int)grid;
@@ -394,6 +476,11 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t o_out_acc = off; off = up16(off + (size_t)(1 + m) * sizeof(dd));
   const size_t o_out_n = off; off = up16(off + (size_t)(m + 1) * 8);
   const size_t o_wmid = off; off = up16(off + wmid.size() * sizeof(u128));
+  size_t o_lane = 0, o_wmid64 = 0;
+  if (J->bs) {
+    o_lane = off; off = up16(off + bs_lane_tab(*J->bs).size() * 8);
+    o_wmid64 = off; off = up16(off + bs_wmid(*J->bs).size() * 8);
+  }
   const size_t dbytes = off;
   // host (pinned) layout: results + staging of the walk table
   size_t hoff = 0;
@@ -402,6 +489,11 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t h_status = hoff; hoff = up16(hoff + 4);
   const size_t h_stats = hoff; hoff = up16(hoff + 3 * 8);
   const size_t h_wmid = hoff; hoff = up16(hoff + wmid.size() * sizeof(u128));
+  size_t h_lane = 0, h_wmid64 = 0;
+  if (J->bs) {
+    h_lane = hoff; hoff = up16(hoff + bs_lane_tab(*J->bs).size() * 8);
+    h_wmid64 = hoff; hoff = up16(hoff + bs_wmid(*J->bs).size() * 8);
+  }
   const size_t hbytes = hoff;
   if ((rc = scratch_acquire(J->dev.device, dbytes, hbytes, &J->scr))) return rc;
   char* d = (char*)J->scr->dmem;
@@ -421,6 +513,18 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   memcpy(h + h_wmid, wmid.data(), wmid.size() * sizeof(u128));
   J->wmid_host_staging = h + h_wmid;
   J->wmid_bytes = wmid.size() * sizeof(u128);
+  if (J->bs) {
+    // one contiguous upload: lane tables then the walk table
+    const auto& lt = bs_lane_tab(*J->bs);
+    const auto& wm = bs_wmid(*J->bs);
+    memcpy(h + h_lane, lt.data(), lt.size() * 8);
+    memcpy(h + h_wmid64, wm.data(), wm.size() * 8);
+    J->d_lane = (unsigned long long*)(d + o_lane);
+    J->d_wmid64 = (unsigned long long*)(d + o_wmid64);
+    J->wmid_host_staging = h + h_lane;
+    J->wmid_bytes = (o_wmid64 - o_lane) + wm.size() * 8;
+    J->d_wmid = (u128*)(d + o_lane);  // upload destination
+  }
   *out = J.release();
   return PBAT_OK;
 }
@@ -446,8 +550,11 @@ int job_launch(Job* J, cudaStream_t st) {
     J->evs.emplace_back(a, b);
   }
   if (timed) PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].first, st));
-  PBAT_CUDA(launch_frontier(J->pl.grad, J->pl.wide, J->grid, J->pl.nthr, J->pl.smem, st, J->P,
-                            J->d_wmid, J->W));
+  if (J->bs)
+    PBAT_CUDA(bs_launch(*J->bs, J->grid, st, J->d_lane, J->d_wmid64, J->W));
+  else
+    PBAT_CUDA(launch_frontier(J->pl.grad, J->pl.wide, J->grid, J->pl.nthr, J->pl.smem, st, J->P,
+                              J->d_wmid, J->W));
   if (timed) {
     PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].second, st));
     ++J->n_pending;
@@ -455,6 +562,8 @@ int job_launch(Job* J, cudaStream_t st) {
   PBAT_CUDA(launch_reduce(st, J->W, J->grid, J->g.m));
   return PBAT_OK;
 }
+
+void job_destroy(Job* J);
 
 // Copy results to the host and wait; convert to input arc order.
 int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* dRdp_out,
@@ -468,9 +577,9 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
   PBAT_CUDA(cudaStreamSynchronize(st));
   if (*J->h_status & 1u)
     return fail(PBAT_ETIMEOUT, "time budget of %.3f s ran out on the device",
-                J->P.budget_ns * 1e-9);
+                J->opt_copy.time_budget_s);
   if (opt) {
-    const unsigned long long item = 1ull << (J->pl.ell + J->pl.L);
+    const unsigned long long item = J->item_states;
     opt->stats[0] = J->h_stats[0] * item;
     opt->stats[1] = (J->h_stats[1] + J->h_stats[2]) * item;
     opt->stats[2] = J->wmid_bytes;
@@ -485,23 +594,37 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
     }
     opt->stats[4] = (unsigned long long)ns;
     opt->stats[5] = 2 * J->n_pending;
-    opt->stats[6] = J->pl.n_tasks;
+    opt->stats[6] = J->n_items;
     opt->stats[7] = J->n_pending;
   }
   J->n_pending = 0;
-  *R_out = J->h_acc[0].hi + J->h_acc[0].lo;
+  const double R = J->h_acc[0].hi + J->h_acc[0].lo;
+  if (J->bs && J->opt_copy.algo == PBAT_ALGO_AUTO && R < 1e12 * J->abs_err_bound * J->mass) {
+    // the fixed-point bound of the bit-sliced kernel would not guarantee
+    // 1e-12 relative accuracy for so small an R: run the frontier kernel
+    pbat_options o = J->opt_copy;
+    o.algo = PBAT_ALGO_FRONTIER;
+    Job* F = nullptr;
+    int rc = job_create(J->g, J->p_copy.data(), false, &o, &F);
+    if (!rc && !(rc = job_upload(F, st)) && !(rc = job_launch(F, st)))
+      rc = job_read(F, st, R_out, Nk_out, nullptr, opt);
+    job_destroy(F);
+    return rc;
+  }
+  *R_out = R;
   if (Nk_out)
     for (int k = 0; k <= m; ++k) Nk_out[k] = J->h_n[k];
   if (dRdp_out)
     for (int k = 0; k < m; ++k) {
       const dd v = J->h_acc[1 + k];
-      dRdp_out[J->pl.perm[k]] = v.hi + v.lo;
+      dRdp_out[J->perm[k]] = v.hi + v.lo;
     }
   return PBAT_OK;
 }
 
 void job_destroy(Job* J) {
   if (!J) return;
+  if (J->bs) bs_delete(J->bs);
   for (auto& e : J->evs) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
@@ -561,6 +684,30 @@ int pbat_reliability_grad(int n_nodes, int n_arcs, const int32_t* tail, const in
   try {
     pbat::GraphIn g{n_nodes, n_arcs, tail, head, directed, source, sink};
     return pbat::run_single(g, p, true, opt, cuda_stream, R_out, Nk_out, dRdp_out);
+  } catch (...) {
+    return pbat::fail(PBAT_ENOMEM, "host exception");
+  }
+}
+
+int pbat_kernel_source(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
+                       int directed, int source, int sink, const pbat_options* opt, char* buf,
+                       size_t cap) {
+  try {
+    pbat::clear_error();
+    pbat::GraphIn g{n_nodes, n_arcs, tail, head, directed, source, sink};
+    int rc;
+    if ((rc = pbat::validate_graph(g)) || (rc = pbat::validate_options(opt, n_arcs))) return rc;
+    pbat_options o;
+    pbat_options_init(&o);
+    if (opt) o = *opt;
+    std::string src;
+    if ((rc = pbat::bs_source_for(g, o, src))) return rc;
+    if (buf && cap) {
+      const size_t n = std::min(cap - 1, src.size());
+      memcpy(buf, src.data(), n);
+      buf[n] = '\0';
+    }
+    return (int)std::min<size_t>(src.size(), 0x7fffffff);
   } catch (...) {
     return pbat::fail(PBAT_ENOMEM, "host exception");
   }

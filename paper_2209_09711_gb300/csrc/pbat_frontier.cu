@@ -294,17 +294,35 @@ __global__ void __launch_bounds__(256) frontier_kernel(const __grid_constant__ F
   }
 }
 
-// Fixed-order sum of the per-block partials (PBAT STEP 3).
-__global__ void reduce_kernel(DevWork W, int nblocks, int m) {
-  for (int i = threadIdx.x; i <= m; i += blockDim.x) {
-    dd s = dd{0.0, 0.0};
-    unsigned long long c = 0ull;
-    for (int b = 0; b < nblocks; ++b) {
-      s = dd_add(s, W.part_acc[(size_t)b * (1 + m) + i]);
-      c += W.part_n[(size_t)b * (m + 1) + i];
+// Fixed-order sum of the per-block partials (PBAT STEP 3).  One CTA per
+// output value; thread t sums blocks t, t + 256, ... in order, then a fixed
+// shared-memory tree combines the 256 partial sums, so the result does not
+// depend on scheduling.
+constexpr int kReduceThreads = 256;
+
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevWork W, int nblocks, int m) {
+  __shared__ dd s_acc[kReduceThreads];
+  __shared__ unsigned long long s_n[kReduceThreads];
+  const int i = blockIdx.x, t = threadIdx.x;
+  dd s = dd{0.0, 0.0};
+  unsigned long long c = 0ull;
+  for (int b = t; b < nblocks; b += kReduceThreads) {
+    s = dd_add(s, W.part_acc[(size_t)b * (1 + m) + i]);
+    c += W.part_n[(size_t)b * (m + 1) + i];
+  }
+  s_acc[t] = s;
+  s_n[t] = c;
+  __syncthreads();
+  for (int h = kReduceThreads / 2; h > 0; h >>= 1) {
+    if (t < h) {
+      s_acc[t] = dd_add(s_acc[t], s_acc[t + h]);
+      s_n[t] += s_n[t + h];
     }
-    W.out_acc[i] = s;
-    W.out_n[i] = c;
+    __syncthreads();
+  }
+  if (t == 0) {
+    W.out_acc[i] = s_acc[0];
+    W.out_n[i] = s_n[0];
   }
 }
 
@@ -345,7 +363,7 @@ cudaError_t launch_frontier(bool grad, bool wide, int grid, int nthr, size_t sme
 }
 
 cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int m) {
-  reduce_kernel<<<1, 64, 0, st>>>(W, nblocks, m);
+  reduce_kernel<<<m + 1, kReduceThreads, 0, st>>>(W, nblocks, m);
   return cudaGetLastError();
 }
 

@@ -64,7 +64,22 @@ def test_small_random_workload(pb):
         for walk in (-1, 0, 3, 6, 11):
             check(run(pb, net, grad=True, prune=prune, walk_bits=walk), ref, True,
                   f"prune={prune} walk={walk}")
+            for algo in (pb.ALGO_FRONTIER, pb.ALGO_BITSLICE):
+                check(run(pb, net, prune=prune, walk_bits=walk, algo=algo), ref, False,
+                      f"algo={algo} prune={prune} walk={walk}")
     check(run(pb, net), ref)
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_bitslice_random_graphs(pb, directed):
+    for seed in range(25):
+        rng = synth.SplitMix64(9100 + seed)
+        m = 1 + rng.below(20)
+        n = 2 + rng.below(12)
+        net = synth.random_small(7000 + seed, n=n, m=m, directed=directed, p_lo=0.05, p_hi=0.95)
+        ref = oracle.enumerate_states(net)
+        for walk in (-1, 2):
+            check(run(pb, net, algo=pb.ALGO_BITSLICE, walk_bits=walk), ref, False, f"seed={seed}")
 
 
 def test_paper_worked_example_and_bridge(pb):
@@ -150,11 +165,12 @@ def test_grid_3x6_full_and_sampled(pb):
     # p = 1/2 ties R to the integer counts exactly
     half = run(pb, net, p=[0.5] * m)
     assert half.R == sum(N) / 2.0**m and half.Nk == N
-    # every split of the work gives identical counts
+    # every split of the work and both connectivity kernels give identical counts
     for walk in (4, 8, 12):
         for prune in (0, 1):
-            r = run(pb, net, walk_bits=walk, prune=prune)
-            assert r.Nk == N and abs(r.R - full.R) <= 1e-14
+            for algo in (pb.ALGO_FRONTIER, pb.ALGO_BITSLICE):
+                r = run(pb, net, walk_bits=walk, prune=prune, algo=algo)
+                assert r.Nk == N and abs(r.R - full.R) <= 1e-14, (walk, prune, algo)
 
 
 def test_directed_34_sampled(pb):
