@@ -45,9 +45,10 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "grid-3x6"
 
-# Warp instructions executed per state by the fused enumeration kernel on
-# each workload, from ncu (inst_executed of the launch / 2^m); the per-unit
-# figure of the issue-rate roofline.  Source: profiles/frontier_fused_grid3x6.md
+# Warp instructions executed per state by the fused enumeration kernel
+# (bs_kernel_grad) on each workload, from ncu (smsp__inst_executed.sum of
+# one launch / 2^m): the per-unit figure of the issue-rate roofline.
+# Source: profiles/bs_kernel_grad_grid3x6.md
 INST_PER_STATE = {}
 # DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # same capture; None until measured for the current kernel.
@@ -248,8 +249,14 @@ def run_ours(a):
     fused = pb.Plan(net, grad=True, stream=sp)
     ms_f, kern_f, wall_f, res_f = time_plan(fused, a.steps, a.warmup)
     clocks = sampler.stop()
-    plain = pb.Plan(net, grad=False, stream=sp)
-    ms_r, kern_r, _, res_r = time_plan(plain, a.steps, a.warmup)
+    ronly = pb.Plan(net, grad=False, stream=sp)
+    ms_r, kern_r, _, res_r = time_plan(ronly, a.steps, a.warmup)
+    # the plain GPU BAT: one state per thread, per-state PLSA frontier expansion
+    plain = pb.Plan(net, grad=False, opts=pb.options(algo=pb.ALGO_FRONTIER), stream=sp)
+    ms_p, kern_p, _, res_p = time_plan(plain, max(3, a.steps // 10), min(a.warmup, 3))
+    plain_g = pb.Plan(net, grad=True, opts=pb.options(algo=pb.ALGO_FRONTIER), stream=sp)
+    ms_pg, kern_pg, _, res_pg = time_plan(plain_g, max(3, a.steps // 10), min(a.warmup, 3))
+    assert res_r.Nk == res_f.Nk == res_p.Nk == res_pg.Nk, "kernels disagree on N_k"
 
     # e2e: the public call with host buffers, copies included
     e2e_t = []
@@ -264,9 +271,9 @@ def run_ours(a):
     e2e_s = statistics.mean(e2e_t)
 
     if ws > 1:
-        t = torch.tensor([ms_f, ms_r, e2e_s], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms_f, ms_r, e2e_s, ms_p, ms_pg], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_f, ms_r, e2e_s = t.tolist()
+        ms_f, ms_r, e2e_s, ms_p, ms_pg = t.tolist()
 
     if rank != 0:
         torch.distributed.destroy_process_group()
@@ -288,11 +295,10 @@ def run_ours(a):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
                 "frac": achieved / peak,
                 "traffic": DRAM_BYTES_PER_LAUNCH.get(a.workload),
-                "kernel": "frontier_kernel<u32,grad>", "kernel_ms": kern_f}
+                "kernel": "bs_kernel_grad", "kernel_ms": kern_f}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": None, "traffic": None, "kernel": "frontier_kernel<u32,grad>",
-                "kernel_ms": kern_f}
+                "frac": None, "traffic": None, "kernel": "bs_kernel_grad", "kernel_ms": kern_f}
     value = ws * states / (ms_f / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": ws, "steps": a.steps,
@@ -303,8 +309,13 @@ def run_ours(a):
                    "l2": "flushed between steps (256 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": roof,
-        "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r},
+        "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r,
+                   "kernel": "bs_kernel"},
+        "plain_gpu_bat": {"value": ws * states / (ms_p / 1e3), "ms_per_step": ms_p,
+                          "kernel": "frontier_kernel (one state per thread, PLSA frontier)",
+                          "fused_value": ws * states / (ms_pg / 1e3), "fused_ms_per_step": ms_pg},
         "fused_over_r_only_time": ms_f / ms_r,
+        "speedup_over_plain_gpu_bat": {"R": ms_p / ms_r, "R+grad": ms_pg / ms_f},
         "R": res_f.R, "pruned_states": res_f.stats[1], "walked_states": res_f.stats[0],
         "cpu_baseline": cpu,
         "e2e": {"value": ws * states / e2e_s, "unit": "states/s",
@@ -316,8 +327,8 @@ def run_ours(a):
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
-    fused.close()
-    plain.close()
+    for pl in (fused, ronly, plain, plain_g):
+        pl.close()
     return 0
 
 

@@ -150,6 +150,7 @@ class Elim {
 // plan: which arcs are lane / thread / walk / prefix arcs
 // ---------------------------------------------------------------------------
 struct BsPlan {
+  bool grad = false;
   int ell = 0, tb = 0, L = 0, d = 0, r = 0;
   std::vector<int> perm;  // internal position -> input arc
   std::string gen;        // generated bs_inv / bs_var
@@ -225,9 +226,16 @@ static void bs_generate(const GraphIn& g, BsPlan& bp) {
   bp.ops_var = B.ops() + bp.L;
 }
 
-int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp) {
+// The fused kernel divides walk masses by p and 1 - p (p-dependent roles).
+static bool bs_walk_ok(const double* p, int a) {
+  return !p || (p[a] >= 0x1p-20 && p[a] <= 1.0 - 0x1p-20);
+}
+
+int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
+                 const double* p_for_grad) {
   const int m = g.m, r = o.range_bits;
   bp.r = r;
+  bp.grad = p_for_grad != nullptr;
   bp.ell = std::min(kMaxLaneBits, m - r);
   bp.tb = std::min(5, m - r - bp.ell);
   const int free_bits = m - r - bp.ell - bp.tb;
@@ -237,8 +245,10 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp) 
   } else if (o.prefix_bits >= 0) {
     bp.L = std::max(0, std::min(lmax, m - bp.ell - bp.tb - std::max(o.prefix_bits, r)));
   } else {
-    // enough work items (one per warp at a time) to fill the GPU several times
-    bp.L = std::max(0, std::min(lmax, free_bits - std::max(0, 14 - r)));
+    // about 2^11 work items: measured best on GB300 for 27..40 arcs (larger
+    // items amortise the per-item epilogue, which is heavier in the fused
+    // kernel, so that one walks two arcs more)
+    bp.L = std::max(0, std::min(lmax, free_bits - std::max(0, 11 - r) + (p_for_grad ? 2 : 0)));
   }
   bp.d = m - bp.ell - bp.tb - bp.L;
   (void)nthr;
@@ -253,9 +263,14 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp) 
   for (int it = 0; it < bp.L; ++it) {
     int best = -1, bscore = 1 << 30;
     for (int a : cand) {
-      if (used[a]) continue;
+      if (used[a] || !bs_walk_ok(p_for_grad, a)) continue;
       const int add = (!incore[g.tail[a]]) + (!incore[g.head[a]]);
       if (add < bscore) bscore = add, best = a;
+    }
+    if (best < 0) {  // not enough eligible walk arcs: shorter walk, deeper prefix
+      bp.L = it;
+      bp.d = m - bp.ell - bp.tb - bp.L;
+      break;
     }
     used[best] = true;
     walk.push_back(best);
@@ -296,7 +311,8 @@ struct JitEntry {
 static std::mutex g_jit_mu;
 static std::map<std::string, JitEntry> g_jit;
 
-static int jit_compile(const std::string& src, const DeviceInfo& dev, JitEntry* out) {
+static int jit_compile(const std::string& src, const DeviceInfo& dev, const char* kname,
+                       JitEntry* out) {
   std::lock_guard<std::mutex> lk(g_jit_mu);
   auto it = g_jit.find(src);
   if (it != g_jit.end()) {
@@ -328,7 +344,7 @@ static int jit_compile(const std::string& src, const DeviceInfo& dev, JitEntry* 
   JitEntry e;
   cudaError_t ce = cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (ce != cudaSuccess) return fail(PBAT_ECUDA, "cudaLibraryLoadData: %s", cudaGetErrorString(ce));
-  ce = cudaLibraryGetKernel(&e.kernel, e.lib, "bs_kernel");
+  ce = cudaLibraryGetKernel(&e.kernel, e.lib, kname);
   if (ce != cudaSuccess) return fail(PBAT_ECUDA, "cudaLibraryGetKernel: %s", cudaGetErrorString(ce));
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, (const void*)e.kernel) == cudaSuccess) e.regs = fa.numRegs;
@@ -341,9 +357,18 @@ static int jit_compile(const std::string& src, const DeviceInfo& dev, JitEntry* 
 // ---------------------------------------------------------------------------
 // tables and launch
 // ---------------------------------------------------------------------------
+struct BsGradParamsHost {
+  dd thr_w_ex[5][32];
+  dd lane_w_ex[5][32];
+  dd inv_p[64], inv_q[64];
+};
+
 struct BsLaunch {
   BsPlan plan;
   BsParamsHost P;
+  BsGradParamsHost Q;
+  std::vector<unsigned long long> thr_tab;   // [4][256] (fused kernel)
+  std::vector<unsigned long long> wmid128;   // [2^L][2] (fused kernel)
   std::vector<unsigned long long> lane_tab;  // [4][256][3]
   std::vector<unsigned long long> wmid;      // [2^L]
   JitEntry jit;
@@ -368,9 +393,9 @@ static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
   snprintf(defs, sizeof defs,
            "#define BS_M %d\n#define BS_ELL %d\n#define BS_TB %d\n#define BS_L %d\n#define BS_D %d\n"
            "#define BS_NTHR %d\n#define BS_WALK0 %d\n#define BS_TOP %d\n#define BS_NCORE %d\n"
-           "#define BS_LANE_MASK 0x%08xu\n",
+           "#define BS_LANE_MASK 0x%08xu\n#define BS_GRAD %d\n",
            g.m, bp.ell, bp.tb, bp.L, bp.d, nthr, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, bp.ncore,
-           lane_mask);
+           lane_mask, bp.grad ? 1 : 0);
   const std::string tmpl = kBsTemplate;
   const size_t cut = tmpl.find("//@@GENERATED@@");
   return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tmpl.substr(cut);
@@ -380,7 +405,7 @@ static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
 int bs_source_for(const GraphIn& g, const pbat_options& o, std::string& out) {
   BsPlan bp;
   const int nthr = o.block_threads > 0 ? o.block_threads : 128;
-  int rc = bs_make_plan(g, o, nthr, bp);
+  int rc = bs_make_plan(g, o, nthr, bp, nullptr);
   if (rc) return rc;
   char perm[64 * 4 + 64] = "// internal arc -> input arc:";
   for (int k = 0; k < g.m; ++k) snprintf(perm + strlen(perm), 8, " %d", bp.perm[k]);
@@ -388,15 +413,15 @@ int bs_source_for(const GraphIn& g, const pbat_options& o, std::string& out) {
   return PBAT_OK;
 }
 
-int bs_prepare(const GraphIn& g, const double* p, const pbat_options& o, const DeviceInfo& dev,
-               BsLaunch& bl) {
+int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
+               const DeviceInfo& dev, BsLaunch& bl) {
   bl.nthr = o.block_threads > 0 ? o.block_threads : 128;
-  int rc = bs_make_plan(g, o, bl.nthr, bl.plan);
+  int rc = bs_make_plan(g, o, bl.nthr, bl.plan, grad ? p : nullptr);
   if (rc) return rc;
   const BsPlan& bp = bl.plan;
   const int m = g.m, top = bp.ell + bp.tb + bp.L;
   const std::string src = bs_source(g, bp, bl.nthr);
-  if ((rc = jit_compile(src, dev, &bl.jit))) return rc;
+  if ((rc = jit_compile(src, dev, grad ? "bs_kernel_grad" : "bs_kernel", &bl.jit))) return rc;
   // parameters
   BsParamsHost& P = bl.P;
   memset(&P, 0, sizeof P);
@@ -457,8 +482,55 @@ int bs_prepare(const GraphIn& g, const double* p, const pbat_options& o, const D
     for (int b = 0; b < bp.L; ++b) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + bp.tb + b], (gi >> b) & 1));
     bl.wmid[gi] = fixed_u64(w, 63);
   }
-  bl.smem = (size_t)(4 * 256 * 3 + (1 << bp.L) + (bp.L + 1) * 2 * bl.nthr) * 8 +
-            (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
+  if (grad) {
+    // fused kernel: thread-pattern masses, 128-bit walk masses, excluded-arc
+    // masses, reciprocals of the walk arcs' p and 1 - p
+    memset(&bl.Q, 0, sizeof bl.Q);
+    dd tw[32];
+    for (int t = 0; t < 32; ++t) tw[t] = P.thr_w[t];
+    bl.thr_tab.assign(4 * 256, 0ull);
+    for (int b = 0; b < 4; ++b)
+      for (int v = 0; v < 256; ++v) {
+        dd s = dd{0.0, 0.0};
+        for (int k = 0; k < 8; ++k)
+          if ((v >> k) & 1) s = dd_add(s, tw[8 * b + k]);
+        bl.thr_tab[b * 256 + v] = fixed_u64(s, 62);
+      }
+    bl.wmid128.resize((size_t)2 << bp.L);
+    for (int gi = 0; gi < (1 << bp.L); ++gi) {
+      dd w = dd_make(1.0);
+      for (int b = 0; b < bp.L; ++b) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + bp.tb + b], (gi >> b) & 1));
+      const u128 f = to_fixed127(w);
+      bl.wmid128[2 * gi] = f.lo;
+      bl.wmid128[2 * gi + 1] = f.hi;
+    }
+    for (int x = 0; x < bp.tb; ++x)
+      for (int t = 0; t < (1 << bp.tb); ++t) {
+        dd w = dd_make(1.0);
+        for (int i = 0; i < bp.tb; ++i)
+          if (i != x) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + i], (t >> i) & 1));
+        bl.Q.thr_w_ex[x][t] = w;
+      }
+    for (int x = 0; x < bp.ell; ++x)
+      for (int j = 0; j < (1 << bp.ell); ++j) {
+        dd w = dd_make(1.0);
+        for (int i = 0; i < bp.ell; ++i)
+          if (i != x) w = dd_mul(w, arc_w(p, bp.perm[i], (j >> i) & 1));
+        bl.Q.lane_w_ex[x][j] = w;
+      }
+    for (int b = 0; b < bp.L; ++b) {
+      const int k = bp.ell + bp.tb + b;
+      const double pk = p[bp.perm[k]];
+      bl.Q.inv_p[k] = dd_recip(pk);
+      bl.Q.inv_q[k] = dd_recip_dd(dd_one_minus(pk));
+    }
+    bl.smem = (size_t)(4 * 256 * 3 + 4 * 256 + 2 * (1 << bp.L) + (bp.L + 1) * 2 * bl.nthr) * 8 +
+              (size_t)std::max(bp.L, 1) * bl.nthr * 16 +
+              (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
+  } else {
+    bl.smem = (size_t)(4 * 256 * 3 + (1 << bp.L) + (bp.L + 1) * 2 * bl.nthr) * 8 +
+              (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
+  }
   if (bl.smem > (size_t)dev.smem_optin)
     return fail(PBAT_ERANGE, "bit-sliced kernel needs %zu B of shared memory", bl.smem);
   cudaError_t e = cudaFuncSetAttribute((const void*)bl.jit.kernel,
@@ -475,10 +547,17 @@ int bs_prepare(const GraphIn& g, const double* p, const pbat_options& o, const D
   return PBAT_OK;
 }
 
-cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st,
-                      const unsigned long long* d_lane, const unsigned long long* d_wmid,
+// d_tabs: the tables in upload order (lane, then walk for R only; lane,
+// thread, 128-bit walk for the fused kernel), each at the given offsets
+cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsigned long long* d_lane,
+                      const unsigned long long* d_thr, const unsigned long long* d_wmid,
                       const DevWork& W) {
   const BsParamsHost& P = bl.P;
+  if (bl.plan.grad) {
+    const BsGradParamsHost& Q = bl.Q;
+    void* args[] = {(void*)&P, (void*)&Q, (void*)&d_lane, (void*)&d_thr, (void*)&d_wmid, (void*)&W};
+    return cudaLaunchKernel((const void*)bl.jit.kernel, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
+  }
   void* args[] = {(void*)&P, (void*)&d_lane, (void*)&d_wmid, (void*)&W};
   return cudaLaunchKernel((const void*)bl.jit.kernel, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
 }
@@ -492,7 +571,11 @@ unsigned long long bs_item_states(const BsLaunch& bl) {
 int bs_per_sm(const BsLaunch& bl) { return bl.per_sm; }
 int bs_nthr(const BsLaunch& bl) { return bl.nthr; }
 const std::vector<unsigned long long>& bs_lane_tab(const BsLaunch& bl) { return bl.lane_tab; }
-const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl) { return bl.wmid; }
+const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl) {
+  return bl.plan.grad ? bl.wmid128 : bl.wmid;
+}
+const std::vector<unsigned long long>& bs_thr_tab(const BsLaunch& bl) { return bl.thr_tab; }
+bool bs_grad(const BsLaunch& bl) { return bl.plan.grad; }
 BsLaunch* bs_new() { return new BsLaunch(); }
 void bs_delete(BsLaunch* b) { delete b; }
 void bs_describe(const BsLaunch& bl, int* out6) {

@@ -13,6 +13,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -37,11 +39,13 @@ cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int m)
 struct BsLaunch;
 BsLaunch* bs_new();
 void bs_delete(BsLaunch* b);
-int bs_prepare(const GraphIn& g, const double* p, const pbat_options& o, const DeviceInfo& dev,
-               BsLaunch& bl);
-cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st,
-                      const unsigned long long* d_lane, const unsigned long long* d_wmid,
+int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
+               const DeviceInfo& dev, BsLaunch& bl);
+cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsigned long long* d_lane,
+                      const unsigned long long* d_thr, const unsigned long long* d_wmid,
                       const DevWork& W);
+const std::vector<unsigned long long>& bs_thr_tab(const BsLaunch& bl);
+bool bs_grad(const BsLaunch& bl);
 const std::vector<int>& bs_perm(const BsLaunch& bl);
 unsigned long long bs_items(const BsLaunch& bl);
 unsigned long long bs_item_states(const BsLaunch& bl);
@@ -369,6 +373,7 @@ struct Job {
   // bit-sliced kernel (R and N_k); null for the frontier kernel
   BsLaunch* bs = nullptr;
   unsigned long long* d_lane = nullptr;
+  unsigned long long* d_thr = nullptr;
   unsigned long long* d_wmid64 = nullptr;
   double abs_err_bound = 0.0;  // of R, relative to the enumerated probability mass
   double mass = 1.0;           // probability mass of the enumerated states
@@ -404,6 +409,138 @@ double range_mass(int m, const double* p, const pbat_options& o) {
   return (double)(below(o.range_hi) - below(o.range_lo));
 }
 
+int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, Job** out);
+int job_upload(Job* J, cudaStream_t st);
+int job_launch(Job* J, cudaStream_t st);
+void job_destroy(Job* J);
+
+// ---------------------------------------------------------------------------
+// autotuner: walk length L and block shape of the bit-sliced kernel
+// ---------------------------------------------------------------------------
+// Candidates around the planner's default are timed on the real problem
+// (CUDA events around the kernel, best of two launches) and the fastest is
+// kept per network structure, mode and range -- in memory, and in the file
+// named by PBAT_AUTOTUNE_CACHE if that is set ("key walk_bits block_threads"
+// lines).  Only problems of at least 2^26 states are tuned: below that a
+// launch is too short for the choice to matter.
+static std::mutex g_tune_mu;
+static std::map<std::string, std::pair<int, int>> g_tune;
+static bool g_tune_loaded = false;
+
+static std::string tune_key(const GraphIn& g, bool grad, const pbat_options& o, int device) {
+  char head[160];
+  snprintf(head, sizeof head, "d%d:g%d:n%d:m%d:dir%d:s%d:t%d:r%d:%llx:%llx:pr%d:", device,
+           grad ? 1 : 0, g.n, g.m, g.directed ? 1 : 0, g.source, g.sink, o.range_bits,
+           (unsigned long long)o.range_lo, (unsigned long long)o.range_hi, o.prune);
+  std::string k = head;
+  for (int i = 0; i < g.m; ++i) {
+    char e[24];
+    snprintf(e, sizeof e, "%d-%d,", g.tail[i], g.head[i]);
+    k += e;
+  }
+  return k;
+}
+
+static void tune_load_file() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("PBAT_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[4096];
+  int L, nt;
+  while (fscanf(f, "%4095s %d %d", key, &L, &nt) == 3) g_tune[key] = {L, nt};
+  fclose(f);
+}
+
+static void tune_store_file(const std::string& key, int L, int nt) {
+  const char* path = getenv("PBAT_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d\n", key.c_str(), L, nt);
+  fclose(f);
+}
+
+static double log2_states(const GraphIn& g, const pbat_options& o) {
+  double s = g.m;
+  if (o.range_bits > 0) {
+    const double frac = (double)(o.range_hi - o.range_lo) / ldexp(1.0, o.range_bits);
+    s += frac > 0 ? log2(frac) : -1e9;
+  }
+  return s;
+}
+
+// Fill o.walk_bits / o.block_threads with the tuned choice when tuning applies.
+static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& o,
+                    const DeviceInfo& dev) {
+  if (!o.autotune || o.walk_bits >= 0 || o.block_threads > 0 || o.prefix_bits >= 0) return PBAT_OK;
+  if (o.algo == PBAT_ALGO_FRONTIER || log2_states(g, o) < 26.0) return PBAT_OK;
+  const std::string key = tune_key(g, grad, o, dev.device);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_file();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      o.walk_bits = it->second.first;
+      o.block_threads = it->second.second;
+      return PBAT_OK;
+    }
+  }
+  const int lmax = std::min(10, std::max(0, g.m - o.range_bits - 10));
+  std::vector<int> Ls;
+  for (int L = std::max(0, lmax - 6); L <= lmax; L += 2) Ls.push_back(L);
+  if (Ls.empty() || Ls.back() != lmax) Ls.push_back(lmax);
+  cudaStream_t st;
+  PBAT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  double best_ms = 1e300;
+  int best_L = -1, best_nt = 128;
+  for (int L : Ls)
+    for (int nt : {128, 256}) {
+      pbat_options t = o;
+      t.autotune = 0;
+      t.walk_bits = L;
+      t.block_threads = nt;
+      t.time_budget_s = 0;
+      Job* J = nullptr;
+      if (job_create(g, p, grad, &t, &J) != PBAT_OK) {
+        clear_error();
+        continue;
+      }
+      double ms = 1e300;
+      bool ok = !job_upload(J, st);
+      for (int rep = 0; ok && rep < 2; ++rep) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+        ok = !job_launch(J, st);
+        cudaEventRecord(b, st);
+        ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+        float f = 0.f;
+        if (ok && cudaEventElapsedTime(&f, a, b) == cudaSuccess && rep > 0) ms = f;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+      }
+      job_destroy(J);
+      if (!ok) {
+        cudaGetLastError();
+        clear_error();
+        continue;
+      }
+      if (ms < best_ms) best_ms = ms, best_L = L, best_nt = nt;
+    }
+  cudaStreamDestroy(st);
+  if (best_L < 0) return PBAT_OK;  // keep the planner's defaults
+  o.walk_bits = best_L;
+  o.block_threads = best_nt;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = {best_L, best_nt};
+  tune_store_file(key, best_L, best_nt);
+  return PBAT_OK;
+}
+
 int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, Job** out) {
   pbat_options o;
   pbat_options_init(&o);
@@ -412,9 +549,12 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   if ((rc = validate_graph(g))) return rc;
   if ((rc = validate_p(p, g.m))) return rc;
   if ((rc = validate_options(opt, g.m))) return rc;
-  const bool use_bs = o.algo == PBAT_ALGO_BITSLICE || (o.algo == PBAT_ALGO_AUTO && !grad);
-  if (use_bs && grad)
-    return fail(PBAT_ENOTSUP, "the bit-sliced kernel computes R and N_k only");
+  {
+    DeviceInfo dv;
+    if ((rc = device_info(dv))) return rc;
+    if ((rc = autotune(g, p, grad, o, dv))) return rc;
+  }
+  const bool use_bs = o.algo == PBAT_ALGO_BITSLICE || o.algo == PBAT_ALGO_AUTO;
   std::unique_ptr<Job> J(new Job());
   J->g = g;
   J->tail_copy.assign(g.tail, g.tail + g.m);
@@ -430,7 +570,7 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   unsigned long long n_items = 0;
   if (use_bs) {
     J->bs = bs_new();
-    if ((rc = bs_prepare(g, p, o, J->dev, *J->bs))) return rc;
+    if ((rc = bs_prepare(g, p, grad, o, J->dev, *J->bs))) return rc;
     J->perm = bs_perm(*J->bs);
     per_sm = bs_per_sm(*J->bs);
     nthr = bs_nthr(*J->bs);
@@ -438,8 +578,8 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
     J->item_states = bs_item_states(*J->bs);
     int d6[6];
     bs_describe(*J->bs, d6);
-    J->abs_err_bound = ldexp(1.0, -61) + ldexp(1.0, d6[2] - 64);
-    J->pl.grad = false;
+    J->abs_err_bound = grad ? ldexp(1.0, -60) : ldexp(1.0, -61) + ldexp(1.0, d6[2] - 64);
+    J->pl.grad = grad;
   } else {
     if ((rc = make_plan(g, p, grad, o, J->dev, J->pl))) return rc;
     build_params(g, p, J->pl, o, J->P, wmid);
@@ -476,9 +616,10 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t o_out_acc = off; off = up16(off + (size_t)(1 + m) * sizeof(dd));
   const size_t o_out_n = off; off = up16(off + (size_t)(m + 1) * 8);
   const size_t o_wmid = off; off = up16(off + wmid.size() * sizeof(u128));
-  size_t o_lane = 0, o_wmid64 = 0;
+  size_t o_lane = 0, o_thr = 0, o_wmid64 = 0;
   if (J->bs) {
     o_lane = off; off = up16(off + bs_lane_tab(*J->bs).size() * 8);
+    o_thr = off; off = up16(off + bs_thr_tab(*J->bs).size() * 8);
     o_wmid64 = off; off = up16(off + bs_wmid(*J->bs).size() * 8);
   }
   const size_t dbytes = off;
@@ -489,9 +630,10 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t h_status = hoff; hoff = up16(hoff + 4);
   const size_t h_stats = hoff; hoff = up16(hoff + 3 * 8);
   const size_t h_wmid = hoff; hoff = up16(hoff + wmid.size() * sizeof(u128));
-  size_t h_lane = 0, h_wmid64 = 0;
+  size_t h_lane = 0, h_thr = 0, h_wmid64 = 0;
   if (J->bs) {
     h_lane = hoff; hoff = up16(hoff + bs_lane_tab(*J->bs).size() * 8);
+    h_thr = hoff; hoff = up16(hoff + bs_thr_tab(*J->bs).size() * 8);
     h_wmid64 = hoff; hoff = up16(hoff + bs_wmid(*J->bs).size() * 8);
   }
   const size_t hbytes = hoff;
@@ -516,10 +658,13 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   if (J->bs) {
     // one contiguous upload: lane tables then the walk table
     const auto& lt = bs_lane_tab(*J->bs);
+    const auto& tt = bs_thr_tab(*J->bs);
     const auto& wm = bs_wmid(*J->bs);
     memcpy(h + h_lane, lt.data(), lt.size() * 8);
+    if (!tt.empty()) memcpy(h + h_thr, tt.data(), tt.size() * 8);
     memcpy(h + h_wmid64, wm.data(), wm.size() * 8);
     J->d_lane = (unsigned long long*)(d + o_lane);
+    J->d_thr = (unsigned long long*)(d + o_thr);
     J->d_wmid64 = (unsigned long long*)(d + o_wmid64);
     J->wmid_host_staging = h + h_lane;
     J->wmid_bytes = (o_wmid64 - o_lane) + wm.size() * 8;
@@ -551,7 +696,7 @@ int job_launch(Job* J, cudaStream_t st) {
   }
   if (timed) PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].first, st));
   if (J->bs)
-    PBAT_CUDA(bs_launch(*J->bs, J->grid, st, J->d_lane, J->d_wmid64, J->W));
+    PBAT_CUDA(bs_launch(*J->bs, J->grid, st, J->d_lane, J->d_thr, J->d_wmid64, J->W));
   else
     PBAT_CUDA(launch_frontier(J->pl.grad, J->pl.wide, J->grid, J->pl.nthr, J->pl.smem, st, J->P,
                               J->d_wmid, J->W));
@@ -605,9 +750,9 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
     pbat_options o = J->opt_copy;
     o.algo = PBAT_ALGO_FRONTIER;
     Job* F = nullptr;
-    int rc = job_create(J->g, J->p_copy.data(), false, &o, &F);
+    int rc = job_create(J->g, J->p_copy.data(), J->pl.grad, &o, &F);
     if (!rc && !(rc = job_upload(F, st)) && !(rc = job_launch(F, st)))
-      rc = job_read(F, st, R_out, Nk_out, nullptr, opt);
+      rc = job_read(F, st, R_out, Nk_out, J->pl.grad ? dRdp_out : nullptr, opt);
     job_destroy(F);
     return rc;
   }

@@ -62,9 +62,9 @@ def test_small_random_workload(pb):
     ref = oracle.enumerate_states(net, grad=True)
     for prune in (1, 0):
         for walk in (-1, 0, 3, 6, 11):
-            check(run(pb, net, grad=True, prune=prune, walk_bits=walk), ref, True,
-                  f"prune={prune} walk={walk}")
             for algo in (pb.ALGO_FRONTIER, pb.ALGO_BITSLICE):
+                check(run(pb, net, grad=True, prune=prune, walk_bits=walk, algo=algo), ref, True,
+                      f"grad algo={algo} prune={prune} walk={walk}")
                 check(run(pb, net, prune=prune, walk_bits=walk, algo=algo), ref, False,
                       f"algo={algo} prune={prune} walk={walk}")
     check(run(pb, net), ref)
@@ -78,8 +78,11 @@ def test_bitslice_random_graphs(pb, directed):
         n = 2 + rng.below(12)
         net = synth.random_small(7000 + seed, n=n, m=m, directed=directed, p_lo=0.05, p_hi=0.95)
         ref = oracle.enumerate_states(net)
+        gref = oracle.enumerate_states(net, grad=True)
         for walk in (-1, 2):
             check(run(pb, net, algo=pb.ALGO_BITSLICE, walk_bits=walk), ref, False, f"seed={seed}")
+            check(run(pb, net, grad=True, algo=pb.ALGO_BITSLICE, walk_bits=walk), gref, True,
+                  f"seed={seed} grad")
 
 
 def test_paper_worked_example_and_bridge(pb):
@@ -102,6 +105,7 @@ def test_random_graphs(pb, directed):
         net = synth.random_small(5000 + seed, n=n, m=m, directed=directed, p_lo=0.02, p_hi=0.98)
         ref = oracle.enumerate_states(net, grad=True)
         check(run(pb, net, grad=True), ref, True, f"seed={seed}")
+        check(run(pb, net, grad=True, algo=pb.ALGO_FRONTIER), ref, True, f"seed={seed} frontier")
         check(run(pb, net, prune=0), ref, False, f"seed={seed} noprune")
 
 
@@ -162,6 +166,9 @@ def test_grid_3x6_full_and_sampled(pb):
                 for k, c in enumerate(N))
     assert abs(full.R - poly) <= 1e-13
     assert abs(sum(full.grad) - dpoly) <= 1e-12
+    fr = run(pb, net, grad=True, algo=pb.ALGO_FRONTIER)
+    assert fr.Nk == N and abs(fr.R - full.R) <= 1e-14
+    assert np.max(np.abs(np.asarray(fr.grad) - np.asarray(full.grad))) <= 1e-15
     # p = 1/2 ties R to the integer counts exactly
     half = run(pb, net, p=[0.5] * m)
     assert half.R == sum(N) / 2.0**m and half.Nk == N
