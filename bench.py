@@ -86,8 +86,10 @@ def oracle_rate(name: str, target_s: float, pool, cores: int, grad: bool = True)
     m = net.m
     sub = min(m, 12)                 # states per division: 2^sub
     bits = m - sub
-    t1 = _oracle_division((name, bits, 0, grad))
-    per = max(t1, 1e-4)
+    # calibrate with one division per process, all processes busy at once
+    t0 = time.perf_counter()
+    pool.map(_oracle_division, [(name, bits, (i * 7919) % (1 << bits), grad) for i in range(cores)])
+    per = max(time.perf_counter() - t0, 1e-4)
     n_div = max(cores, int(target_s * cores / per))
     n_div = min(n_div, 1 << bits)
     step = max(1, (1 << bits) // n_div)
@@ -332,6 +334,25 @@ def run_ours(a):
     return 0
 
 
+def run_probe(a):
+    """One untimed launch of one kernel: the program ncu captures."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2209_09711_gb300 import build
+    build.build()
+    import paper_2209_09711_gb300 as pb
+    net = WORKLOADS[a.workload]()
+    algo = pb.ALGO_FRONTIER if a.probe.startswith("plain") else pb.ALGO_AUTO
+    grad = a.probe.endswith("fused")
+    plan = pb.Plan(net, grad=grad, opts=pb.options(algo=algo))
+    plan.execute(0)
+    r = plan.read(0)
+    print(json.dumps({"probe": a.probe, "workload": a.workload, "R": r.R,
+                      "kernel_ms": r.stats[4] / 1e6, "items": r.stats[6]}))
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,7 +365,11 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=6.0,
                     help="target wall time of one --impl reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", choices=["fused", "r-only", "plain-r-only", "plain-fused"],
+                    help="run one untimed launch of that kernel (for profiler captures)")
     a = ap.parse_args()
+    if a.probe:
+        return run_probe(a)
     if a.warmup < 0 or a.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
     if a.impl == "reference":

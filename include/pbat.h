@@ -194,13 +194,16 @@ int pbat_reliability_noalloc(int n_nodes, int n_arcs, const int32_t* tail, const
  * compiles (NVRTC) for the bit-sliced kernel of this network and options --
  * the per-graph connectivity program of the PLSA test (Sec. 3.2) as
  * straight-line Boolean elimination on 32-state words, inside the kernel
- * template.  The first line lists the internal arc order.  Writes at most
- * cap bytes (NUL-terminated) to buf (nullable) and returns the full length,
- * or a negative PBAT_E* code.
+ * template.  The first line lists the internal arc order.
+ *   p          nullable; with want_grad the plan depends on p (walk arcs need
+ *              p in [2^-20, 1 - 2^-20]); NULL treats every arc as eligible
+ *   want_grad  0: the R + N_k kernel's plan; 1: the fused kernel's plan
+ * Writes at most cap bytes (NUL-terminated) to buf (nullable) and returns the
+ * full length, or a negative PBAT_E* code.
  */
 int pbat_kernel_source(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
-                       int directed, int source, int sink, const pbat_options* opt, char* buf,
-                       size_t cap);
+                       int directed, const double* p, int source, int sink, int want_grad,
+                       const pbat_options* opt, char* buf, size_t cap);
 
 /* Thread-local description of the last error in this thread ("" if none). */
 const char* pbat_last_error(void);

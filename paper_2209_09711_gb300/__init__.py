@@ -121,7 +121,7 @@ def load(path: Optional[str] = None):
         lib.pbat_plan_destroy.restype = None
         lib.pbat_reliability_noalloc.argtypes = [I, I, PI32, PI32, I, PD, I, I, PO, V, PD, PU]
         lib.pbat_reliability_noalloc.restype = I
-        lib.pbat_kernel_source.argtypes = [I, I, PI32, PI32, I, I, I, PO, ctypes.c_char_p,
+        lib.pbat_kernel_source.argtypes = [I, I, PI32, PI32, I, PD, I, I, I, PO, ctypes.c_char_p,
                                            ctypes.c_size_t]
         lib.pbat_kernel_source.restype = I
         lib.pbat_last_error.argtypes = []
@@ -285,19 +285,20 @@ class Plan:
             pass
 
 
-def kernel_source(net, opts: Optional[Options] = None) -> str:
+def kernel_source(net, opts: Optional[Options] = None, grad: bool = False, p=None) -> str:
     """The generated CUDA source of the bit-sliced kernel for a network."""
     lib = load()
     t, tp = _i32(net.tail)
     h, hp = _i32(net.head)
+    pv, pp = _f64(net.p if p is None else p)
     o = opts if opts is not None else options()
-    n = lib.pbat_kernel_source(net.n, len(t), tp, hp, int(net.directed), net.source, net.sink,
-                               ctypes.byref(o), None, 0)
+    n = lib.pbat_kernel_source(net.n, len(t), tp, hp, int(net.directed), pp, net.source, net.sink,
+                               int(grad), ctypes.byref(o), None, 0)
     if n < 0:
         _check(n)
     buf = ctypes.create_string_buffer(n + 1)
-    lib.pbat_kernel_source(net.n, len(t), tp, hp, int(net.directed), net.source, net.sink,
-                           ctypes.byref(o), buf, n + 1)
+    lib.pbat_kernel_source(net.n, len(t), tp, hp, int(net.directed), pp, net.source, net.sink,
+                           int(grad), ctypes.byref(o), buf, n + 1)
     return buf.value.decode()
 
 

@@ -537,6 +537,10 @@ static double limbs_value(const unsigned long long* limbs) {
   return s.hi + s.lo;
 }
 
+int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
+                   cudaStream_t st, double* R_out, uint64_t* Nk_out, const std::string& key,
+                   const DeviceInfo& dev);
+
 int run_batched(int G, const pbat_graph* graphs, int K, const double* p, pbat_options* opt,
                 void* stream, double* R_out, uint64_t* Nk_out, double* dRdp_out) {
   clear_error();
@@ -557,13 +561,44 @@ int run_batched(int G, const pbat_graph* graphs, int K, const double* p, pbat_op
   }
   if ((rc = validate_options(opt, 0))) return rc;
   if (o.range_bits != 0) return fail(PBAT_EINVAL, "range_bits is not supported for batches");
-  if (o.algo == PBAT_ALGO_BITSLICE)
-    return fail(PBAT_ENOTSUP, "the bit-sliced kernel is not available for batches in this build");
   DeviceInfo dev;
   if ((rc = device_info(dev))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
 
   const std::string key = batch_key(dev.device, G, graphs, K, o);
+  if (o.algo != PBAT_ALGO_FRONTIER) {
+    // bit-sliced batched kernel for R and N_k; the gradient, if asked for,
+    // comes from one fused enumeration per (network, p-vector) below
+    std::vector<double> Rb((size_t)G * K);
+    std::vector<uint64_t> Nb;
+    int nk_total = 0;
+    for (int i = 0; i < G; ++i) nk_total += graphs[i].n_arcs + 1;
+    Nb.resize(nk_total);
+    rc = run_batched_bs(G, graphs, K, p, o, st, Rb.data(), Nb.data(), key, dev);
+    if (rc == PBAT_OK) {
+      if (dRdp_out) {
+        size_t poff = 0;
+        for (int i = 0; i < G; ++i) {
+          GraphIn g{graphs[i].n_nodes, graphs[i].n_arcs, graphs[i].tail, graphs[i].head,
+                    graphs[i].directed, graphs[i].source, graphs[i].sink};
+          for (int k = 0; k < K; ++k) {
+            double Rk;
+            pbat_options oo = o;
+            rc = run_single(g, p + poff + (size_t)k * g.m, true, &oo, stream, &Rk, nullptr,
+                            dRdp_out + poff + (size_t)k * g.m);
+            if (rc) return rc;
+          }
+          poff += (size_t)K * g.m;
+        }
+      }
+      memcpy(R_out, Rb.data(), sizeof(double) * Rb.size());
+      if (Nk_out) memcpy(Nk_out, Nb.data(), sizeof(uint64_t) * Nb.size());
+      if (opt) opt->stats[5] = (unsigned long long)((K + 15) / 16);
+      return PBAT_OK;
+    }
+    if (rc != PBAT_ENOTSUP || o.algo == PBAT_ALGO_BITSLICE) return rc;
+    clear_error();
+  }
   BatchEntry* E = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_bmu);

@@ -40,10 +40,10 @@ namespace pbat {
 // Host mirror of BsParams in the kernel source (same field order and types).
 struct BsParamsHost {
   unsigned long long task_lo, n_tasks, budget_ns;
-  int prune, pad;
-  double p[64];
-  dd q[64];
-  dd thr_w[32];
+  int prune, nlev;
+  int lev_bits[6];
+  int lev_off[6];
+  unsigned long long thw[32];
   unsigned long long binom[64];
 };
 
@@ -250,6 +250,7 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
     // kernel, so that one walks two arcs more)
     bp.L = std::max(0, std::min(lmax, free_bits - std::max(0, 11 - r) + (p_for_grad ? 2 : 0)));
   }
+  bp.L = std::max(0, std::min(bp.L, free_bits));  // never into the range arcs
   bp.d = m - bp.ell - bp.tb - bp.L;
   (void)nthr;
   // ---- roles.  range arcs are the top prefix bits in input order.
@@ -288,6 +289,8 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
     return dx < dy;
   });
   const int npre_free = bp.d - r;
+  if (npre_free < 0 || npre_free + bp.ell + bp.tb != (int)rest.size())
+    return fail(PBAT_EINVAL, "internal: bit-sliced plan does not fit (m=%d r=%d L=%d)", m, r, bp.L);
   bp.perm.assign(m, -1);
   // prefix positions [top, m - r): nearest arcs; range arcs at [m - r, m)
   const int top = bp.ell + bp.tb + bp.L;
@@ -296,6 +299,19 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
   for (int b = 0; b < bp.L; ++b) bp.perm[bp.ell + bp.tb + b] = walk[b];
   int x = npre_free;
   for (int k = 0; k < bp.ell + bp.tb; ++k) bp.perm[k] = rest[x++];
+  // invariants the kernel relies on: a permutation, range arcs on top, and
+  // every role within its limits
+  std::vector<int> seen(m, 0);
+  bool ok = bp.L >= 0 && bp.L <= 10 && bp.ell <= 5 && bp.tb <= 5 && bp.d >= r &&
+            bp.ell + bp.tb + bp.L + bp.d == m && npre_free >= 0 && x == (int)rest.size();
+  for (int k = 0; ok && k < m; ++k) {
+    ok = bp.perm[k] >= 0 && bp.perm[k] < m && !seen[bp.perm[k]];
+    if (ok) seen[bp.perm[k]] = 1;
+  }
+  for (int i = 0; ok && i < r; ++i) ok = bp.perm[m - 1 - i] == i;
+  if (!ok)
+    return fail(PBAT_EINVAL, "internal: inconsistent bit-sliced plan (m=%d r=%d L=%d d=%d)", m, r,
+                bp.L, bp.d);
   bs_generate(g, bp);
   return PBAT_OK;
 }
@@ -358,8 +374,8 @@ static int jit_compile(const std::string& src, const DeviceInfo& dev, const char
 // tables and launch
 // ---------------------------------------------------------------------------
 struct BsGradParamsHost {
-  dd thr_w_ex[5][32];
-  dd lane_w_ex[5][32];
+  unsigned long long thw_ex[5][32];
+  unsigned long long lw_ex[5][32];
   dd inv_p[64], inv_q[64];
 };
 
@@ -369,6 +385,8 @@ struct BsLaunch {
   BsGradParamsHost Q;
   std::vector<unsigned long long> thr_tab;   // [4][256] (fused kernel)
   std::vector<unsigned long long> wmid128;   // [2^L][2] (fused kernel)
+  std::vector<dd> ptab;                      // prefix masses per level
+  std::vector<dd> ptab_ex;                   // [prefix arc][2^11]: its level without it
   std::vector<unsigned long long> lane_tab;  // [4][256][3]
   std::vector<unsigned long long> wmid;      // [2^L]
   JitEntry jit;
@@ -402,10 +420,16 @@ static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
 }
 
 // Generated source for a network (no device needed); see pbat_kernel_source.
-int bs_source_for(const GraphIn& g, const pbat_options& o, std::string& out) {
+int bs_source_for(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
+                  std::string& out) {
   BsPlan bp;
   const int nthr = o.block_threads > 0 ? o.block_threads : 128;
-  int rc = bs_make_plan(g, o, nthr, bp, nullptr);
+  std::vector<double> half;
+  if (grad && !p) {
+    half.assign(g.m, 0.5);
+    p = half.data();
+  }
+  int rc = bs_make_plan(g, o, nthr, bp, grad ? p : nullptr);
   if (rc) return rc;
   char perm[64 * 4 + 64] = "// internal arc -> input arc:";
   for (int k = 0; k < g.m; ++k) snprintf(perm + strlen(perm), 8, " %d", bp.perm[k]);
@@ -427,15 +451,14 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   memset(&P, 0, sizeof P);
   P.prune = o.prune ? 1 : 0;
   P.budget_ns = o.time_budget_s > 0 ? (unsigned long long)(o.time_budget_s * 1e9) : 0ull;
-  for (int k = 0; k < m; ++k) {
-    P.p[k] = p[bp.perm[k]];
-    P.q[k] = dd_one_minus(p[bp.perm[k]]);
-  }
+  dd tw[32];
   for (int j = 0; j < 32; ++j) {
+    tw[j] = dd{0.0, 0.0};
     if (j >= (1 << bp.tb)) continue;
     dd w = dd_make(1.0);
     for (int i = 0; i < bp.tb; ++i) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + i], (j >> i) & 1));
-    P.thr_w[j] = w;
+    tw[j] = w;
+    P.thw[j] = fixed_u64(w, 63);
   }
   for (int j = 0; j < 64; ++j) P.binom[j] = binom_u64(top, j);
   unsigned long long lo = 0, hi = 1ull << bp.d;
@@ -445,6 +468,31 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   }
   P.task_lo = lo;
   P.n_tasks = hi - lo;
+  // prefix masses: the d prefix arcs in levels of at most 11 bits; each
+  // entry is the exact double-double product over one level's arcs
+  P.nlev = (bp.d + 10) / 11;
+  bl.ptab.clear();
+  bl.ptab_ex.assign(grad ? (size_t)bp.d << 11 : 0, dd{0.0, 0.0});
+  for (int l = 0, sh = 0; l < P.nlev; ++l) {
+    const int bits = bp.d / P.nlev + (l < bp.d % P.nlev ? 1 : 0);
+    P.lev_bits[l] = bits;
+    P.lev_off[l] = (int)bl.ptab.size();
+    for (int v = 0; v < (1 << bits); ++v) {
+      dd w = dd_make(1.0);
+      for (int x = 0; x < bits; ++x) w = dd_mul(w, arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
+      bl.ptab.push_back(w);
+    }
+    if (grad)
+      for (int jj = 0; jj < bits; ++jj)
+        for (int v = 0; v < (1 << bits); ++v) {
+          dd w = dd_make(1.0);
+          for (int x = 0; x < bits; ++x)
+            if (x != jj) w = dd_mul(w, arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
+          bl.ptab_ex[((size_t)(sh + jj) << 11) + v] = w;
+        }
+    sh += bits;
+  }
+  if (bl.ptab.empty()) bl.ptab.push_back(dd_make(1.0));
   // lane tables: byte position b, value v -> lane mass (scale 2^62) and
   // packed counts by lane popcount class (21-bit fields; classes 0-2, 3-5)
   bl.lane_tab.assign(4 * 256 * 3, 0ull);
@@ -476,18 +524,20 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
       e[1] = n0;
       e[2] = n1;
     }
-  bl.wmid.resize((size_t)1 << bp.L);
-  for (int gi = 0; gi < (1 << bp.L); ++gi) {
-    dd w = dd_make(1.0);
-    for (int b = 0; b < bp.L; ++b) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + bp.tb + b], (gi >> b) & 1));
-    bl.wmid[gi] = fixed_u64(w, 63);
-  }
-  if (grad) {
-    // fused kernel: thread-pattern masses, 128-bit walk masses, excluded-arc
-    // masses, reciprocals of the walk arcs' p and 1 - p
+  const int L_in = std::min(bp.L, 2), L_out = bp.L - L_in;
+  if (!grad) {
+    bl.wmid.resize((size_t)1 << bp.L);
+    for (int gi = 0; gi < (1 << bp.L); ++gi) {
+      dd w = dd_make(1.0);
+      for (int b = 0; b < bp.L; ++b) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + bp.tb + b], (gi >> b) & 1));
+      bl.wmid[gi] = fixed_u64(w, 63);
+    }
+    bl.smem = (size_t)(4 * 256 * 3 + (1 << bp.L) + (bp.L + 1) * 2 * bl.nthr) * 8 +
+              (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
+  } else {
+    // fused kernel: thread-pattern masses, 128-bit walk masses, fixed-point
+    // excluded-arc masses, reciprocals of the walk arcs' p and 1 - p
     memset(&bl.Q, 0, sizeof bl.Q);
-    dd tw[32];
-    for (int t = 0; t < 32; ++t) tw[t] = P.thr_w[t];
     bl.thr_tab.assign(4 * 256, 0ull);
     for (int b = 0; b < 4; ++b)
       for (int v = 0; v < 256; ++v) {
@@ -509,14 +559,14 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
         dd w = dd_make(1.0);
         for (int i = 0; i < bp.tb; ++i)
           if (i != x) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + i], (t >> i) & 1));
-        bl.Q.thr_w_ex[x][t] = w;
+        bl.Q.thw_ex[x][t] = fixed_u64(w, 63);
       }
     for (int x = 0; x < bp.ell; ++x)
       for (int j = 0; j < (1 << bp.ell); ++j) {
         dd w = dd_make(1.0);
         for (int i = 0; i < bp.ell; ++i)
           if (i != x) w = dd_mul(w, arc_w(p, bp.perm[i], (j >> i) & 1));
-        bl.Q.lane_w_ex[x][j] = w;
+        bl.Q.lw_ex[x][j] = fixed_u64(w, 63);
       }
     for (int b = 0; b < bp.L; ++b) {
       const int k = bp.ell + bp.tb + b;
@@ -525,10 +575,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
       bl.Q.inv_q[k] = dd_recip_dd(dd_one_minus(pk));
     }
     bl.smem = (size_t)(4 * 256 * 3 + 4 * 256 + 2 * (1 << bp.L) + (bp.L + 1) * 2 * bl.nthr) * 8 +
-              (size_t)std::max(bp.L, 1) * bl.nthr * 16 +
-              (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
-  } else {
-    bl.smem = (size_t)(4 * 256 * 3 + (1 << bp.L) + (bp.L + 1) * 2 * bl.nthr) * 8 +
+              (size_t)std::max(L_out, 1) * bl.nthr * 16 + (size_t)(bl.nthr / 32) * 64 * 16 +
               (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
   }
   if (bl.smem > (size_t)dev.smem_optin)
@@ -547,18 +594,18 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   return PBAT_OK;
 }
 
-// d_tabs: the tables in upload order (lane, then walk for R only; lane,
-// thread, 128-bit walk for the fused kernel), each at the given offsets
+// Launch with the device copies of the tables (see bs_tables for the order).
 cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsigned long long* d_lane,
                       const unsigned long long* d_thr, const unsigned long long* d_wmid,
-                      const DevWork& W) {
+                      const dd* d_ptab, const dd* d_ptab_ex, const DevWork& W) {
   const BsParamsHost& P = bl.P;
   if (bl.plan.grad) {
     const BsGradParamsHost& Q = bl.Q;
-    void* args[] = {(void*)&P, (void*)&Q, (void*)&d_lane, (void*)&d_thr, (void*)&d_wmid, (void*)&W};
+    void* args[] = {(void*)&P, (void*)&Q, (void*)&d_lane, (void*)&d_thr, (void*)&d_wmid,
+                    (void*)&d_ptab, (void*)&d_ptab_ex, (void*)&W};
     return cudaLaunchKernel((const void*)bl.jit.kernel, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
   }
-  void* args[] = {(void*)&P, (void*)&d_lane, (void*)&d_wmid, (void*)&W};
+  void* args[] = {(void*)&P, (void*)&d_lane, (void*)&d_wmid, (void*)&d_ptab, (void*)&W};
   return cudaLaunchKernel((const void*)bl.jit.kernel, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
 }
 
@@ -575,12 +622,383 @@ const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl) {
   return bl.plan.grad ? bl.wmid128 : bl.wmid;
 }
 const std::vector<unsigned long long>& bs_thr_tab(const BsLaunch& bl) { return bl.thr_tab; }
+const std::vector<dd>& bs_ptab(const BsLaunch& bl) { return bl.ptab; }
+const std::vector<dd>& bs_ptab_ex(const BsLaunch& bl) { return bl.ptab_ex; }
 bool bs_grad(const BsLaunch& bl) { return bl.plan.grad; }
 BsLaunch* bs_new() { return new BsLaunch(); }
 void bs_delete(BsLaunch* b) { delete b; }
 void bs_describe(const BsLaunch& bl, int* out6) {
   out6[0] = bl.plan.ell; out6[1] = bl.plan.tb; out6[2] = bl.plan.L; out6[3] = bl.plan.d;
   out6[4] = bl.plan.ops_inv; out6[5] = bl.plan.ops_var;
+}
+
+}  // namespace pbat
+
+// ---------------------------------------------------------------------------
+// Batched bit-sliced enumeration: one module, one persistent kernel.
+// ---------------------------------------------------------------------------
+namespace pbat {
+
+struct BGraphHost {
+  unsigned long long task_begin, n_tasks;
+  int gidx, m, nlev, prune;
+  int lev_bits[6], lev_off[6];
+  int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, pad;
+  unsigned long long binom[64];
+};
+
+constexpr int kBsbThreads = 128;
+constexpr int kBsbChunk = 16;
+constexpr int kBsbLimbs = 5;
+constexpr int kBsbScale = 158;
+constexpr int kBsbMaxGraphs = 256;
+
+struct BsBatch {
+  std::string key;
+  bool busy = false;
+  int device = -1, G = 0, K = 0, grid = 0, lmax = 0;
+  size_t smem = 0;
+  JitEntry jit;
+  std::vector<BsPlan> plans;        // input order
+  std::vector<int> order;           // launch order -> input index
+  std::vector<BGraphHost> bg;       // launch order
+  unsigned long long total = 0;
+  int nk_total = 0;
+  size_t n_lt = 0, n_nt = 0, n_wm = 0, n_pt = 0, n_thw = 0;
+  Scratch* scr = nullptr;
+  size_t o_graphs, o_lt, o_nt, o_wm, o_pt, o_thw, o_upload_end, o_limbs, o_nk, o_counter, o_status, o_end;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static std::mutex g_bsb_mu;
+static std::vector<BsBatch*> g_bsb;
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int bsb_build(BsBatch& E, int G, const pbat_graph* graphs, int K, const pbat_options& o,
+                     const DeviceInfo& dev) {
+  E.G = G;
+  E.K = K;
+  E.device = dev.device;
+  E.plans.resize(G);
+  std::vector<unsigned long long> items(G);
+  for (int i = 0; i < G; ++i) {
+    GraphIn g{graphs[i].n_nodes, graphs[i].n_arcs, graphs[i].tail, graphs[i].head,
+              graphs[i].directed, graphs[i].source, graphs[i].sink};
+    pbat_options oo;
+    pbat_options_init(&oo);
+    oo.walk_bits = o.walk_bits;
+    int rc = bs_make_plan(g, oo, kBsbThreads, E.plans[i], nullptr);
+    if (rc) return rc;
+    items[i] = 1ull << E.plans[i].d;
+    E.lmax = std::max(E.lmax, E.plans[i].L);
+  }
+  E.order.resize(G);
+  for (int i = 0; i < G; ++i) E.order[i] = i;
+  std::stable_sort(E.order.begin(), E.order.end(), [&](int a, int b) { return items[a] > items[b]; });
+  // source: prelude, one struct per network (launch order), item template, kernel
+  const std::string tmpl = kBsTemplate;
+  std::string src = "#define BSB_NTHR " + std::to_string(kBsbThreads) + "\n" +
+                    tmpl.substr(0, tmpl.find("//@@GENERATED@@"));
+  for (int r = 0; r < G; ++r) {
+    const BsPlan& bp = E.plans[E.order[r]];
+    std::string gen = bp.gen;
+    auto rep = [&](const std::string& a, const std::string& b) {
+      const size_t at = gen.find(a);
+      if (at != std::string::npos) gen.replace(at, a.size(), b);
+    };
+    rep("__device__ __forceinline__ void bs_inv(", "static __device__ __forceinline__ void inv(");
+    rep("__device__ __forceinline__ u32 bs_var(", "static __device__ __forceinline__ u32 var(");
+    const int m = graphs[E.order[r]].n_arcs;
+    const unsigned lane_mask = bp.ell >= 5 ? 0xffffffffu : ((1u << (1 << bp.ell)) - 1u);
+    char head[400];
+    snprintf(head, sizeof head,
+             "struct G%d {\n  static constexpr int M = %d, ELL = %d, TB = %d, L = %d, D = %d, NCORE = %d,"
+             " WALK0 = %d, TOP = %d;\n  static constexpr u32 LANE_MASK = 0x%08xu;\n",
+             r, m, bp.ell, bp.tb, bp.L, bp.d, bp.ncore, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, lane_mask);
+    src += head + gen + "};\n";
+  }
+  const int kc_max = std::min(K, kBsbChunk);
+  std::string kern = "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR)\n"
+      "bs_batch(const BGraph* __restrict__ graphs, int G, int K, int k0, int kc, u64 total,\n"
+      "         const u64* __restrict__ lt, const u64* __restrict__ nt, const u64* __restrict__ wm,\n"
+      "         const dd* __restrict__ pt, const u64* __restrict__ thw, u64* limbs, u64* nk,\n"
+      "         u64* counter, u32* status, u64 budget_ns) {\n"
+      "  extern __shared__ __align__(16) u64 s_bins[];\n"
+      "  const int lane = threadIdx.x & 31;\n"
+      "  u64* bins = s_bins + threadIdx.x;\n"
+      "  const u64 t0 = bs_timer();\n"
+      "  for (;;) {\n"
+      "    u64 task = 0;\n"
+      "    if (lane == 0) {\n"
+      "      task = atomicAdd(counter, 1ull);\n"
+      "      if (budget_ns && bs_timer() - t0 > budget_ns) { atomicOr(status, 1u); task = ~0ull; }\n"
+      "    }\n"
+      "    task = __shfl_sync(0xffffffffu, task, 0);\n"
+      "    if (task >= total) break;\n"
+      "    int lo = 0, hi = G - 1;\n"
+      "    while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (graphs[mid].task_begin <= task) lo = mid; else hi = mid - 1; }\n"
+      "    const BGraph& B = graphs[lo];\n"
+      "    const u64 prefix = task - B.task_begin;\n"
+      "    switch (lo) {\n";
+  for (int r = 0; r < G; ++r)
+    kern += "      case " + std::to_string(r) + ": bsb_item<G" + std::to_string(r) + ", " +
+            std::to_string(kc_max) + ">(B, prefix, lane, K, k0, kc, lt, nt, wm, pt, thw, limbs, nk, bins); break;\n";
+  kern += "    }\n    __syncwarp();\n  }\n}\n";
+  std::string bt = kBsBatchTemplate;
+  const size_t cut = bt.find("//@@BATCH_KERNEL@@");
+  src += bt.substr(0, cut) + kern;
+  int rc = jit_compile(src, dev, "bs_batch", &E.jit);
+  if (rc) return rc;
+  // descriptors and table layout (launch order)
+  E.bg.resize(G);
+  unsigned long long begin = 0;
+  size_t lt = 0, nt = 0, wm = 0, pt = 0, th = 0;
+  int nk_off = 0;
+  std::vector<int> nk_offs(G);
+  for (int i = 0; i < G; ++i) {
+    nk_offs[i] = nk_off;
+    nk_off += graphs[i].n_arcs + 1;
+  }
+  E.nk_total = nk_off;
+  for (int r = 0; r < G; ++r) {
+    const int i = E.order[r];
+    const BsPlan& bp = E.plans[i];
+    BGraphHost& b = E.bg[r];
+    memset(&b, 0, sizeof b);
+    b.task_begin = begin;
+    b.n_tasks = items[i];
+    begin += items[i];
+    b.gidx = i;
+    b.m = graphs[i].n_arcs;
+    b.prune = o.prune ? 1 : 0;
+    b.nlev = (bp.d + 10) / 11;
+    int off = 0;
+    for (int l = 0; l < b.nlev; ++l) {
+      b.lev_bits[l] = bp.d / b.nlev + (l < bp.d % b.nlev ? 1 : 0);
+      b.lev_off[l] = off;
+      off += 1 << b.lev_bits[l];
+    }
+    b.pt_size = std::max(off, 1);
+    for (int j = 0; j < 64; ++j) b.binom[j] = binom_u64(bp.ell + bp.tb + bp.L, j);
+    b.lt_off = (int)lt; lt += (size_t)1024 * K;
+    b.nt_off = (int)nt; nt += 1024 * 2;
+    b.wm_off = (int)wm; wm += ((size_t)1 << bp.L) * K;
+    b.pt_off = (int)pt; pt += (size_t)b.pt_size * K;
+    b.thw_off = (int)th; th += (size_t)32 * K;
+    b.nk_off = nk_offs[i];
+  }
+  E.total = begin;
+  E.n_lt = lt; E.n_nt = nt; E.n_wm = wm; E.n_pt = pt; E.n_thw = th;
+  size_t off = 0;
+  E.o_graphs = off; off = a256(off + sizeof(BGraphHost) * G);
+  E.o_lt = off; off = a256(off + 8 * lt);
+  E.o_nt = off; off = a256(off + 8 * nt);
+  E.o_wm = off; off = a256(off + 8 * wm);
+  E.o_pt = off; off = a256(off + sizeof(dd) * pt);
+  E.o_thw = off; off = a256(off + 8 * th);
+  E.o_upload_end = off;
+  E.o_limbs = off; off = a256(off + 8 * (size_t)kBsbLimbs * G * K);
+  E.o_nk = off; off = a256(off + 8 * (size_t)E.nk_total);
+  E.o_counter = off; off = a256(off + 8);
+  E.o_status = off; off = a256(off + 4);
+  E.o_end = off;
+  if ((rc = scratch_acquire(dev.device, E.o_end, E.o_end, &E.scr))) return rc;
+  memcpy((char*)E.scr->hmem + E.o_graphs, E.bg.data(), sizeof(BGraphHost) * G);
+  E.smem = (size_t)(E.lmax + 1) * 2 * kBsbThreads * 8;
+  cudaError_t e = cudaFuncSetAttribute((const void*)E.jit.kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E.smem);
+  if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)E.jit.kernel, kBsbThreads,
+                                                    E.smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const long long need = (long long)((E.total + kBsbThreads / 32 - 1) / (kBsbThreads / 32));
+  E.grid = (int)std::max(1LL, std::min((long long)per_sm * dev.sms, need));
+  return PBAT_OK;
+}
+
+static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
+  char* h = (char*)E.scr->hmem;
+  unsigned long long* lt = (unsigned long long*)(h + E.o_lt);
+  unsigned long long* nt = (unsigned long long*)(h + E.o_nt);
+  unsigned long long* wm = (unsigned long long*)(h + E.o_wm);
+  dd* pt = (dd*)(h + E.o_pt);
+  unsigned long long* th = (unsigned long long*)(h + E.o_thw);
+  const int K = E.K;
+  std::vector<size_t> poff(E.G);
+  size_t acc = 0;
+  for (int i = 0; i < E.G; ++i) {
+    poff[i] = acc;
+    acc += (size_t)K * graphs[i].n_arcs;
+  }
+  for (int r = 0; r < E.G; ++r) {
+    const BGraphHost& b = E.bg[r];
+    const int i = b.gidx, m = b.m;
+    const BsPlan& bp = E.plans[i];
+    const int top = bp.ell + bp.tb + bp.L;
+    for (int v = 0; v < 1024; ++v) {  // packed N counts by lane class (same for every p-vector)
+      const int by = v >> 8, val = v & 255;
+      unsigned long long n0 = 0, n1 = 0;
+      for (int k = 0; k < 8; ++k) {
+        const int j = 8 * by + k;
+        if (!((val >> k) & 1) || j >= (1 << bp.ell)) continue;
+        const int cl = __builtin_popcount((unsigned)j);
+        if (cl < 3) n0 += 1ull << (21 * cl); else n1 += 1ull << (21 * (cl - 3));
+      }
+      nt[b.nt_off + 2 * v] = n0;
+      nt[b.nt_off + 2 * v + 1] = n1;
+    }
+    for (int k = 0; k < K; ++k) {
+      const double* pv = p + poff[i] + (size_t)k * m;
+      dd lw[32];
+      for (int j = 0; j < 32; ++j) {
+        lw[j] = dd{0.0, 0.0};
+        if (j >= (1 << bp.ell)) continue;
+        dd w = dd_make(1.0);
+        for (int a = 0; a < bp.ell; ++a) w = dd_mul(w, arc_w(pv, bp.perm[a], (j >> a) & 1));
+        lw[j] = w;
+      }
+      for (int v = 0; v < 1024; ++v) {
+        const int by = v >> 8, val = v & 255;
+        dd s = dd{0.0, 0.0};
+        for (int x = 0; x < 8; ++x)
+          if ((val >> x) & 1) s = dd_add(s, lw[8 * by + x]);
+        lt[b.lt_off + (size_t)v * K + k] = fixed_u64(s, 62);
+      }
+      for (int gi = 0; gi < (1 << bp.L); ++gi) {
+        dd w = dd_make(1.0);
+        for (int a = 0; a < bp.L; ++a) w = dd_mul(w, arc_w(pv, bp.perm[bp.ell + bp.tb + a], (gi >> a) & 1));
+        wm[b.wm_off + (size_t)gi * K + k] = fixed_u64(w, 63);
+      }
+      for (int t = 0; t < 32; ++t) {
+        unsigned long long f = 0;
+        if (t < (1 << bp.tb)) {
+          dd w = dd_make(1.0);
+          for (int a = 0; a < bp.tb; ++a) w = dd_mul(w, arc_w(pv, bp.perm[bp.ell + a], (t >> a) & 1));
+          f = fixed_u64(w, 63);
+        }
+        th[b.thw_off + (size_t)t * K + k] = f;
+      }
+      dd* ptk = pt + b.pt_off + (size_t)k * b.pt_size;
+      if (b.nlev == 0) ptk[0] = dd_make(1.0);
+      for (int l = 0, sh = 0; l < b.nlev; ++l) {
+        for (int v = 0; v < (1 << b.lev_bits[l]); ++v) {
+          dd w = dd_make(1.0);
+          for (int x = 0; x < b.lev_bits[l]; ++x) w = dd_mul(w, arc_w(pv, bp.perm[top + sh + x], (v >> x) & 1));
+          ptk[b.lev_off[l] + v] = w;
+        }
+        sh += b.lev_bits[l];
+      }
+    }
+  }
+}
+
+static int bsb_enqueue(BsBatch& E, cudaStream_t st, unsigned long long budget_ns) {
+  char* d = (char*)E.scr->dmem;
+  cudaError_t e = cudaMemsetAsync(d + E.o_limbs, 0, E.o_end - E.o_limbs, st);
+  if (e != cudaSuccess) return fail(PBAT_ECUDA, "memset: %s", cudaGetErrorString(e));
+  const void* graphs = d + E.o_graphs;
+  const void *lt = d + E.o_lt, *nt = d + E.o_nt, *wm = d + E.o_wm, *pt = d + E.o_pt, *thw = d + E.o_thw;
+  void *limbs = d + E.o_limbs, *nk = d + E.o_nk, *counter = d + E.o_counter, *status = d + E.o_status;
+  for (int k0 = 0; k0 < E.K; k0 += kBsbChunk) {
+    if (k0 > 0 && (e = cudaMemsetAsync(counter, 0, 8, st)) != cudaSuccess)
+      return fail(PBAT_ECUDA, "memset: %s", cudaGetErrorString(e));
+    int G = E.G, K = E.K, kk0 = k0, kc = std::min(kBsbChunk, E.K - k0);
+    unsigned long long total = E.total, bud = budget_ns;
+    void* args[] = {(void*)&graphs, &G, &K, &kk0, &kc, &total, (void*)&lt, (void*)&nt, (void*)&wm,
+                    (void*)&pt, (void*)&thw, &limbs, &nk, &counter, &status, &bud};
+    e = cudaLaunchKernel((const void*)E.jit.kernel, dim3(E.grid), dim3(kBsbThreads), args, E.smem, st);
+    if (e != cudaSuccess) return fail(PBAT_ECUDA, "batched launch: %s", cudaGetErrorString(e));
+  }
+  return PBAT_OK;
+}
+
+static double bsb_limbs_value(const unsigned long long* limbs) {
+  long long carry = 0;
+  uint32_t chunk[kBsbLimbs + 2];
+  for (int i = 0; i < kBsbLimbs; ++i) {
+    const __int128 v = (__int128)(long long)limbs[i] + carry;
+    chunk[i] = (uint32_t)(v & 0xffffffff);
+    carry = (long long)(v >> 32);
+  }
+  chunk[kBsbLimbs] = (uint32_t)(carry & 0xffffffff);
+  chunk[kBsbLimbs + 1] = (uint32_t)((carry >> 32) & 0xffffffff);
+  dd s = dd{0.0, 0.0};
+  for (int i = kBsbLimbs + 1; i >= 0; --i) s = dd_add(s, dd_make(ldexp((double)chunk[i], 32 * i - kBsbScale)));
+  return s.hi + s.lo;
+}
+
+// R (and N_k) of a batch with the bit-sliced batched kernel; returns
+// PBAT_ENOTSUP when the batch is outside its limits (the caller then uses the
+// frontier kernel).
+int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
+                   cudaStream_t st, double* R_out, uint64_t* Nk_out, const std::string& key,
+                   const DeviceInfo& dev) {
+  if (G > kBsbMaxGraphs) return PBAT_ENOTSUP;
+  BsBatch* E = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_bsb_mu);
+    for (auto* e : g_bsb)
+      if (!e->busy && e->key == key) { e->busy = true; E = e; break; }
+  }
+  if (!E) {
+    std::unique_ptr<BsBatch> ne(new BsBatch());
+    ne->key = key;
+    ne->busy = true;
+    int rc = bsb_build(*ne, G, graphs, K, o, dev);
+    if (rc) {
+      if (ne->scr) scratch_release(ne->scr);
+      return rc;
+    }
+    E = ne.release();
+    std::lock_guard<std::mutex> lk(g_bsb_mu);
+    g_bsb.push_back(E);
+  }
+  auto done = [&](int code) {
+    std::lock_guard<std::mutex> lk(g_bsb_mu);
+    E->busy = false;
+    return code;
+  };
+  const unsigned long long budget = o.time_budget_s > 0 ? (unsigned long long)(o.time_budget_s * 1e9) : 0ull;
+  bsb_tables(*E, graphs, p);
+  char* d = (char*)E->scr->dmem;
+  char* h = (char*)E->scr->hmem;
+  if (cudaMemcpyAsync(d, h, E->o_upload_end, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return done(fail(PBAT_ECUDA, "upload failed: %s", cudaGetErrorString(cudaGetLastError())));
+  if (!E->exec) {
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+      return done(fail(PBAT_ECUDA, "stream create failed"));
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const int erc = ok ? bsb_enqueue(*E, cs, budget) : PBAT_ECUDA;
+    ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && ok && erc == PBAT_OK;
+    if (ok) ok = cudaGraphInstantiate(&E->exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (!ok) {
+      E->exec = nullptr;
+      return done(fail(PBAT_ECUDA, "CUDA graph capture of the batched launch failed: %s",
+                       cudaGetErrorString(cudaGetLastError())));
+    }
+  }
+  if (cudaGraphLaunch(E->exec, st) != cudaSuccess)
+    return done(fail(PBAT_ECUDA, "graph launch failed: %s", cudaGetErrorString(cudaGetLastError())));
+  if (cudaMemcpyAsync(h + E->o_limbs, d + E->o_limbs, E->o_end - E->o_limbs, cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return done(fail(PBAT_ECUDA, "batched run failed: %s", cudaGetErrorString(cudaGetLastError())));
+  if (*(unsigned int*)(h + E->o_status) & 1u) return done(fail(PBAT_ETIMEOUT, "time budget ran out on the device"));
+  const unsigned long long* limbs = (const unsigned long long*)(h + E->o_limbs);
+  const unsigned long long* nk = (const unsigned long long*)(h + E->o_nk);
+  for (int i = 0; i < G; ++i)
+    for (int k = 0; k < K; ++k)
+      R_out[(size_t)i * K + k] = bsb_limbs_value(limbs + ((size_t)i * K + k) * kBsbLimbs);
+  if (Nk_out) memcpy(Nk_out, nk, sizeof(uint64_t) * E->nk_total);
+  return done(PBAT_OK);
 }
 
 }  // namespace pbat

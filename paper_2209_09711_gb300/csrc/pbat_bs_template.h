@@ -1,22 +1,24 @@
-// pbat_bs_template.h -- CUDA source of the bit-sliced enumeration kernel.
+// pbat_bs_template.h -- CUDA source of the bit-sliced enumeration kernels.
 //
 // The engine prepends a block of #defines and the graph-specific
 // connectivity functions (bs_inv / bs_var, written by the planner in
 // pbat_bitslice.cu) and compiles the result with NVRTC for sm_103a.
 //
-// State layout of one thread's 32-bit word: bit j of the word is the state
-// whose BS_ELL lane arcs follow the bits of j.  The BS_TB thread arcs follow
-// the bits of the warp lane id, the BS_L walk arcs are walked in reflected
-// Gray order, and the BS_D prefix arcs are fixed per work item (one item per
-// warp, from an atomic ticket: the equal division of Sec. 4.3).
+// State layout: bit j of a thread's 32-bit word is the state whose BS_ELL
+// lane arcs follow the bits of j; the BS_TB thread arcs follow the bits of
+// the warp lane id; the BS_L walk arcs follow the walk index g; the BS_D
+// prefix arcs are fixed per work item (one item per warp, from an atomic
+// ticket: the equal division of Sec. 4.3).  The walk visits g in reflected
+// Gray order over its upper BS_L - BS_IN bits and, for each such step, all
+// 2^BS_IN settings of its lowest bits in an unrolled block whose walk words
+// are compile-time constants that fold through the connectivity program.
 //
-// Per word the connectivity of all 32 states is one evaluation of the
-// straight-line program: c = bs_var(inv, walk words), bit j of c set iff the
-// sink is reachable from the source in state j (PLSA reachability, Sec.
-// 3.2).  R (Eq. 1) accumulates exactly: the lane mass of the connected bits
-// comes from four byte tables (u64, scale 2^62), times the walk mass of g
-// (u64, scale 2^63), into a 128-bit integer per thread; the prefix and
-// thread-arc masses are applied once per item in double-double.
+// Per word the connectivity of its 32 states is c = bs_var(inv, walk words):
+// bit j set iff the sink is reachable from the source in state j (the PLSA
+// answer of Sec. 3.2).  R (Eq. 1) accumulates exactly: the lane mass of the
+// connected bits comes from four byte tables (u64, scale 2^62), times the
+// walk mass of g, into a 128-bit integer T per thread (scale 2^125); the
+// thread-arc and prefix masses are applied once per item.
 #pragma once
 
 namespace pbat {
@@ -24,6 +26,9 @@ namespace pbat {
 static const char* kBsTemplate = R"PBAT(
 typedef unsigned int u32;
 typedef unsigned long long u64;
+
+#define BS_IN (BS_L >= 2 ? 2 : BS_L)
+#define BS_OUT (BS_L - BS_IN)
 
 struct dd { double hi, lo; };
 __device__ __forceinline__ dd two_sum(double a, double b) {
@@ -39,11 +44,9 @@ __device__ __forceinline__ dd dd_add(dd a, dd b) {
   dd s = two_sum(a.hi, b.hi); dd t = two_sum(a.lo, b.lo);
   s.lo += t.hi; s = fast_two_sum(s.hi, s.lo); s.lo += t.lo; return fast_two_sum(s.hi, s.lo);
 }
+__device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
 __device__ __forceinline__ dd dd_mul(dd a, dd b) {
   dd p = two_prod(a.hi, b.hi); p.lo += a.hi * b.lo + a.lo * b.hi; return fast_two_sum(p.hi, p.lo);
-}
-__device__ __forceinline__ dd dd_mul_d(dd a, double b) {
-  dd p = two_prod(a.hi, b); p.lo += a.lo * b; return fast_two_sum(p.hi, p.lo);
 }
 __device__ __forceinline__ dd dd_ldexp(dd a, int e) { return dd{ldexp(a.hi, e), ldexp(a.lo, e)}; }
 
@@ -51,19 +54,48 @@ struct u128 { u64 lo, hi; };
 __device__ __forceinline__ void u128_add(u128& a, u64 blo, u64 bhi) {
   asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(blo), "l"(bhi));
 }
+__device__ __forceinline__ u128 u128_sub(u128 a, u128 b) {
+  u128 r;
+  asm("sub.cc.u64 %0, %2, %4;\n\tsubc.u64 %1, %3, %5;" : "=l"(r.lo), "=l"(r.hi) : "l"(a.lo), "l"(a.hi), "l"(b.lo), "l"(b.hi));
+  return r;
+}
 __device__ __forceinline__ dd u128_to_dd(u128 v) {
   double h = __ull2double_rd(v.hi);
   u64 hr = v.hi - (u64)h;
   dd r = two_sum(ldexp(h, 64), ldexp((double)hr, 64));
   return dd_add(r, two_sum(ldexp((double)(v.lo >> 32), 32), (double)(v.lo & 0xffffffffull)));
 }
+// (a * b) >> 64 for a 64-bit a and a 128-bit b (the lowest 64 bits dropped)
+__device__ __forceinline__ u128 mul64x128_shr64(u64 a, u64 blo, u64 bhi) {
+  const u64 h0 = __umul64hi(a, blo);
+  const u64 l1 = a * bhi;
+  const u64 h1 = __umul64hi(a, bhi);
+  u128 r;
+  asm("add.cc.u64 %0, %2, %3;\n\taddc.u64 %1, %4, 0;" : "=l"(r.lo), "=l"(r.hi) : "l"(l1), "l"(h0), "l"(h1));
+  return r;
+}
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int m) {
+  u128 r;
+  r.lo = __shfl_xor_sync(0xffffffffu, v.lo, m);
+  r.hi = __shfl_xor_sync(0xffffffffu, v.hi, m);
+  return r;
+}
+// exact sum over the warp (every lane gets it)
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const u128 w = shfl_xor_u128(v, o);
+    u128_add(v, w.lo, w.hi);
+  }
+  return v;
+}
 
 struct BsParams {
   u64 task_lo, n_tasks, budget_ns;
-  int prune, pad;
-  double p[64];
-  dd q[64];
-  dd thr_w[32];
+  int prune, nlev;       // prefix-mass table levels
+  int lev_bits[6];       // prefix bits per level (low level first)
+  int lev_off[6];        // first entry of each level in the prefix table
+  u64 thw[32];           // thread-pattern masses, fixed point 2^63
   u64 binom[64];
 };
 struct BsWork {
@@ -75,25 +107,17 @@ __device__ __forceinline__ u64 bs_timer() {
   u64 t; asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t)); return t;
 }
 
-__device__ __forceinline__ dd bs_warp_sum(dd v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    dd w; w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o); w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-    v = dd_add(v, w);
-  }
-  return v;
-}
-
-__device__ __forceinline__ dd bs_prefix_mass(const BsParams& P, u64 prefix) {
+// Mass of the prefix arcs of `prefix`: product over table levels.
+__device__ __forceinline__ dd bs_prefix_mass(const BsParams& P, const dd* __restrict__ ptab, u64 prefix) {
   dd w = dd{1.0, 0.0};
-#pragma unroll 1
-  for (int j = 0; j < BS_D; ++j) {
-    const int k = BS_TOP + j;
-    w = ((prefix >> j) & 1ull) ? dd_mul_d(w, P.p[k]) : dd_mul(w, P.q[k]);
+  int sh = 0;
+  for (int l = 0; l < P.nlev; ++l) {
+    const u64 v = (prefix >> sh) & ((1ull << P.lev_bits[l]) - 1ull);
+    w = l ? dd_mul(w, ptab[P.lev_off[l] + v]) : ptab[P.lev_off[l] + v];
+    sh += P.lev_bits[l];
   }
   return w;
 }
-
 //@@GENERATED@@
 // connectivity of one uniform state (every word 0 or ~0): the prune test
 __device__ __forceinline__ u32 bs_uniform(const u32* a) {
@@ -105,15 +129,61 @@ __device__ __forceinline__ u32 bs_uniform(const u32* a) {
   return bs_var(e, w);
 }
 
+__device__ __forceinline__ void bs_init_arcs(u32* a, int lane) {
+#pragma unroll
+  for (int i = 0; i < BS_ELL; ++i)
+    a[i] = i == 0 ? 0xAAAAAAAAu : i == 1 ? 0xCCCCCCCCu : i == 2 ? 0xF0F0F0F0u : i == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+#pragma unroll
+  for (int i = 0; i < BS_TB; ++i) a[BS_ELL + i] = 0u - (u32)((lane >> i) & 1);
+#pragma unroll
+  for (int b = 0; b < BS_L; ++b) a[BS_WALK0 + b] = 0u;
+}
+
+// 0: walk the item, 1: every state disconnected, 2: every state connected
+__device__ __forceinline__ int bs_prune(const u32* a) {
+  u32 u[BS_M];
+#pragma unroll
+  for (int k = 0; k < BS_M; ++k) u[k] = k < BS_TOP ? ~0u : a[k];
+  if (bs_uniform(u) == 0u) return 1;
+#pragma unroll
+  for (int k = 0; k < BS_M; ++k) u[k] = k < BS_TOP ? 0u : a[k];
+  return bs_uniform(u) != 0u ? 2 : 0;
+}
+
+__device__ __forceinline__ void bs_flush_bins(u64* bins, u64* s_nbins, int base) {
+#pragma unroll 1
+  for (int r = 0; r <= BS_L; ++r) {
+    const u64 n0 = bins[(2 * r) * BS_NTHR], n1 = bins[(2 * r + 1) * BS_NTHR];
+#pragma unroll
+    for (int cl = 0; cl < 3; ++cl) {
+      const u64 c0 = (n0 >> (21 * cl)) & 0x1fffffull, c1 = (n1 >> (21 * cl)) & 0x1fffffull;
+      if (c0) atomicAdd(&s_nbins[base + r + cl], c0);
+      if (c1) atomicAdd(&s_nbins[base + r + 3 + cl], c1);
+    }
+  }
+}
+
+// per-block partials for the fixed-order reduction
+__device__ __forceinline__ void bs_write_partials(const BsWork& W, const dd* s_wacc, const u64* s_nbins) {
+  for (int i = threadIdx.x; i <= BS_M; i += BS_NTHR) {
+    dd s = dd{0.0, 0.0};
+    for (int w = 0; w < BS_NTHR / 32; ++w) s = dd_add(s, s_wacc[w * (1 + BS_M) + i]);
+    W.part_acc[(size_t)blockIdx.x * (1 + BS_M) + i] = s;
+    W.part_n[(size_t)blockIdx.x * (BS_M + 1) + i] = s_nbins[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// R + N_k
+// ---------------------------------------------------------------------------
 extern "C" __global__ void __launch_bounds__(BS_NTHR)
 bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
-          const u64* __restrict__ wmid_tab, BsWork W) {
+          const u64* __restrict__ wmid_tab, const dd* __restrict__ ptab, BsWork W) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // lane tables: [4 bytes][256 values][3]: R (scale 2^62), N classes 0-2, N classes 3-5
-  u64* s_lt = (u64*)smem;
-  u64* s_wmid = s_lt + 4 * 256 * 3;
-  u64* s_bins = s_wmid + (1 << BS_L);             // [(BS_L + 1) * 2][BS_NTHR]
-  dd* s_wacc = (dd*)(s_bins + (BS_L + 1) * 2 * BS_NTHR);  // [warps][1 + BS_M]
+  u64* s_lt = (u64*)smem;                                   // [4][256][3]
+  u64* s_wmid = s_lt + 4 * 256 * 3;                         // [2^L], scale 2^63
+  u64* s_bins = s_wmid + (1 << BS_L);                       // [(L + 1) * 2][NTHR]
+  dd* s_wacc = (dd*)(s_bins + (BS_L + 1) * 2 * BS_NTHR);    // [warps][1 + M]
   u64* s_nbins = (u64*)(s_wacc + (BS_NTHR / 32) * (1 + BS_M));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 4 * 256 * 3; i += BS_NTHR) s_lt[i] = lane_tab[i];
@@ -125,19 +195,11 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
   u64* bins = s_bins + tid;
   const bool thr_on = lane < (1 << BS_TB);
   const int pc_thr = __popc(lane & ((1 << BS_TB) - 1));
-  const dd thr_w = thr_on ? P.thr_w[lane] : dd{0.0, 0.0};
+  const u64 thw = thr_on ? P.thw[lane] : 0ull;
   const u64 t_start = bs_timer();
   u64 n_walk = 0, n_full = 0, n_dead = 0;
   u32 a[BS_M];
-  // lane arcs: fixed patterns over the 32 bits of the word
-#pragma unroll
-  for (int i = 0; i < BS_ELL; ++i)
-    a[i] = i == 0 ? 0xAAAAAAAAu : i == 1 ? 0xCCCCCCCCu : i == 2 ? 0xF0F0F0F0u : i == 3 ? 0xFF00FF00u : 0xFFFF0000u;
-  // thread arcs: all-ones or all-zeros from the lane id
-#pragma unroll
-  for (int i = 0; i < BS_TB; ++i) a[BS_ELL + i] = 0u - (u32)((lane >> i) & 1);
-#pragma unroll
-  for (int b = 0; b < BS_L; ++b) a[BS_WALK0 + b] = 0u;
+  bs_init_arcs(a, lane);
 
   for (;;) {
     u64 task = 0;
@@ -150,19 +212,14 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
     const u64 prefix = P.task_lo + task;
 #pragma unroll
     for (int j = 0; j < BS_D; ++j) a[BS_TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
-    const dd wpre = bs_prefix_mass(P, prefix);
     const int pc_pre = __popcll((long long)prefix);
     if (P.prune) {
-      u32 u[BS_M];
-#pragma unroll
-      for (int k = 0; k < BS_M; ++k) u[k] = k < BS_TOP ? ~0u : a[k];
-      if (bs_uniform(u) == 0u) { ++n_dead; continue; }
-#pragma unroll
-      for (int k = 0; k < BS_M; ++k) u[k] = k < BS_TOP ? 0u : a[k];
-      if (bs_uniform(u) != 0u) {
+      const int pr = bs_prune(a);
+      if (pr == 1) { ++n_dead; continue; }
+      if (pr == 2) {
         ++n_full;
         for (int j = lane; j <= BS_TOP; j += 32) atomicAdd(&s_nbins[pc_pre + j], P.binom[j]);
-        if (lane == 0) wacc[0] = dd_add(wacc[0], wpre);
+        if (lane == 0) wacc[0] = dd_add(wacc[0], bs_prefix_mass(P, ptab, prefix));
         continue;
       }
     }
@@ -172,149 +229,103 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
 #pragma unroll
     for (int r = 0; r < (BS_L + 1) * 2; ++r) bins[r * BS_NTHR] = 0ull;
     u128 T = u128{0ull, 0ull};
-    u32 g = 0;
-    int pc = 0;
+    u32 gout = 0;
+    int pco = 0;
 #pragma unroll 1
-    for (u32 s = 0; s < (1u << BS_L); ++s) {
+    for (u32 s = 0; s < (1u << BS_OUT); ++s) {
       if (s) {
         const int b = __ffs(s) - 1;
-        g ^= 1u << b;
-        pc += ((g >> b) & 1u) ? 1 : -1;
+        gout ^= 1u << b;
+        pco += ((gout >> b) & 1u) ? 1 : -1;
       }
       u32 w[BS_L > 0 ? BS_L : 1];
 #pragma unroll
-      for (int b = 0; b < BS_L; ++b) w[b] = 0u - ((g >> b) & 1u);
-      u32 c = bs_var(e, w) & BS_LANE_MASK;
-      if (c) {
-        const u64* t0 = s_lt + (0 * 256 + (c & 0xffu)) * 3;
-        const u64* t1 = s_lt + (1 * 256 + ((c >> 8) & 0xffu)) * 3;
-        const u64* t2 = s_lt + (2 * 256 + ((c >> 16) & 0xffu)) * 3;
-        const u64* t3 = s_lt + (3 * 256 + (c >> 24)) * 3;
-        const u64 sR = t0[0] + t1[0] + t2[0] + t3[0];
-        const u64 n0 = t0[1] + t1[1] + t2[1] + t3[1];
-        const u64 n1 = t0[2] + t1[2] + t2[2] + t3[2];
-        const u64 wm = s_wmid[g];
-        u128_add(T, sR * wm, __umul64hi(sR, wm));
-        bins[(2 * pc) * BS_NTHR] += n0;
-        bins[(2 * pc + 1) * BS_NTHR] += n1;
-      }
-    }
-    if (thr_on) {
-      const int base = pc_pre + pc_thr;
-#pragma unroll 1
-      for (int r = 0; r <= BS_L; ++r) {
-        const u64 n0 = bins[(2 * r) * BS_NTHR], n1 = bins[(2 * r + 1) * BS_NTHR];
+      for (int b = 0; b < BS_OUT; ++b) w[BS_IN + b] = 0u - ((gout >> b) & 1u);
 #pragma unroll
-        for (int cl = 0; cl < 3; ++cl) {
-          const u64 c0 = (n0 >> (21 * cl)) & 0x1fffffull, c1 = (n1 >> (21 * cl)) & 0x1fffffull;
-          if (c0) atomicAdd(&s_nbins[base + r + cl], c0);
-          if (c1) atomicAdd(&s_nbins[base + r + 3 + cl], c1);
+      for (int r = 0; r < (1 << BS_IN); ++r) {
+#pragma unroll
+        for (int b = 0; b < BS_IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
+        const u32 c = bs_var(e, w) & BS_LANE_MASK;
+        if (c) {
+          const u32 g = (gout << BS_IN) | (u32)r;
+          const int pc = pco + __popc(r);
+          const u64* t0 = s_lt + (0 * 256 + (c & 0xffu)) * 3;
+          const u64* t1 = s_lt + (1 * 256 + ((c >> 8) & 0xffu)) * 3;
+          const u64* t2 = s_lt + (2 * 256 + ((c >> 16) & 0xffu)) * 3;
+          const u64* t3 = s_lt + (3 * 256 + (c >> 24)) * 3;
+          const u64 sR = t0[0] + t1[0] + t2[0] + t3[0];
+          const u64 wm = s_wmid[g];
+          u128_add(T, sR * wm, __umul64hi(sR, wm));
+          bins[(2 * pc) * BS_NTHR] += t0[1] + t1[1] + t2[1] + t3[1];
+          bins[(2 * pc + 1) * BS_NTHR] += t0[2] + t1[2] + t2[2] + t3[2];
         }
       }
     }
-    const dd t = dd_ldexp(u128_to_dd(T), -125);
-    const dd ws = bs_warp_sum(dd_mul(thr_w, t));
-    if (lane == 0) wacc[0] = dd_add(wacc[0], dd_mul(wpre, ws));
+    if (thr_on) bs_flush_bins(bins, s_nbins, pc_pre + pc_thr);
+    // item total: exact warp sum of T x thread mass (scale 2^124), once per item
+    const u128 S = warp_sum_u128(mul64x128_shr64(thw, T.lo, T.hi));
+    if (lane == 0)
+      wacc[0] = dd_add(wacc[0], dd_mul(bs_prefix_mass(P, ptab, prefix), dd_ldexp(u128_to_dd(S), -124)));
   }
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
   }
   __syncthreads();
-  for (int i = tid; i <= BS_M; i += BS_NTHR) {
-    dd s = dd{0.0, 0.0};
-    for (int w = 0; w < BS_NTHR / 32; ++w) s = dd_add(s, s_wacc[w * (1 + BS_M) + i]);
-    W.part_acc[(size_t)blockIdx.x * (1 + BS_M) + i] = s;
-    W.part_n[(size_t)blockIdx.x * (BS_M + 1) + i] = s_nbins[i];
-  }
+  bs_write_partials(W, s_wacc, s_nbins);
 }
 
 #if BS_GRAD
 // ---------------------------------------------------------------------------
 // Fused R + N_k + dR/dp.  Every gradient term is a difference of two exact
-// integer sums over the two halves of a pair of states (X, X + e_i) that
-// carry identical weights, so it is exact and non-negative:
+// integer sums over the two halves of state pairs (X, X + e_i) that carry
+// identical weights, so it is exact and non-negative:
 //   thread arcs: per-thread totals T of warp lanes t and t ^ 2^i;
 //   lane arcs: the 32x32 bit matrix (threads x lanes) of a word is
 //     transposed across the warp, so lane j holds the states of lane pattern
-//     j; its total T' (thread-arc masses from byte tables) pairs lanes j and
-//     j ^ 2^i in the same way;
-//   walk arcs: A_b, the part of T collected while walk arc b works (T
-//     subtracted when it turns on, added when it turns off), against
-//     T - A_b, divided by p_b and 1 - p_b in double-double;
-//   prefix arcs: item totals in double-double, added with sign.
-// Walk masses are 128-bit here (scale 2^127), so the division by p_b or
-// 1 - p_b leaves an error far below 2^-100.
+//     j; its total T2 (thread-pattern masses from byte tables) pairs lanes j
+//     and j ^ 2^i in the same way;
+//   walk arcs: A_b, the part of T collected while walk arc b works, against
+//     T - A_b, divided by p_b and 1 - p_b in double-double (exact to 2^-100,
+//     because both come from the same integers);
+//   prefix arcs: item totals times the prefix mass without that arc, signed.
+// Per item every quantity is first summed exactly over the warp in 128-bit
+// integers with fixed-point per-lane weights; then the lane that owns an arc
+// (lanes k and k - 32 own internal arc k) does that arc's double-double
+// arithmetic, so the per-item floating-point work runs once per warp, in
+// parallel over arcs.  Walk masses are 128-bit (scale 2^127).
 struct BsGradParams {
-  dd thr_w_ex[5][32];
-  dd lane_w_ex[5][32];
+  u64 thw_ex[5][32];    // thread-pattern masses without thread arc i (2^63)
+  u64 lw_ex[5][32];     // lane-pattern masses without lane arc i (2^63)
   dd inv_p[64], inv_q[64];
 };
 
 __device__ __forceinline__ u32 bs_transpose32(u32 x, int lane) {
-  const u32 masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
     const int sh = 16 >> r;
-    const u32 mk = masks[r];
+    const u32 mk = r == 0 ? 0x0000FFFFu : r == 1 ? 0x00FF00FFu : r == 2 ? 0x0F0F0F0Fu : r == 3 ? 0x33333333u : 0x55555555u;
     const u32 y = __shfl_xor_sync(0xffffffffu, x, sh);
     x = (lane & sh) ? ((x & ~mk) | ((y & ~mk) >> sh)) : ((x & mk) | ((y & mk) << sh));
   }
   return x;
 }
 
-// (a * b) >> 64 for a 64-bit a and a 128-bit b, as 128 bits
-__device__ __forceinline__ void mul64x128_shr64(u64 a, u64 blo, u64 bhi, u64& rlo, u64& rhi) {
-  const u64 h0 = __umul64hi(a, blo);
-  const u64 l1 = a * bhi;
-  const u64 h1 = __umul64hi(a, bhi);
-  asm("add.cc.u64 %0, %2, %3;\n\taddc.u64 %1, %4, 0;" : "=l"(rlo), "=l"(rhi) : "l"(l1), "l"(h0), "l"(h1));
-}
-
-__device__ __forceinline__ double u128_to_double(u128 v) {
-  return fma((double)v.hi, 18446744073709551616.0, (double)v.lo);
-}
-
-__device__ __forceinline__ double bs_warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ u128 shfl_u128(u128 v, int src_lane_xor) {
-  u128 r;
-  r.lo = __shfl_xor_sync(0xffffffffu, v.lo, src_lane_xor);
-  r.hi = __shfl_xor_sync(0xffffffffu, v.hi, src_lane_xor);
-  return r;
-}
-
-__device__ __forceinline__ u128 u128_sub(u128 a, u128 b) {
-  u128 r;
-  asm("sub.cc.u64 %0, %2, %4;\n\tsubc.u64 %1, %3, %5;" : "=l"(r.lo), "=l"(r.hi) : "l"(a.lo), "l"(a.hi), "l"(b.lo), "l"(b.hi));
-  return r;
-}
-
-__device__ __forceinline__ dd bs_prefix_mass_ex(const BsParams& P, u64 prefix, int skip) {
-  dd w = dd{1.0, 0.0};
-#pragma unroll 1
-  for (int j = 0; j < BS_D; ++j) {
-    if (j == skip) continue;
-    const int k = BS_TOP + j;
-    w = ((prefix >> j) & 1ull) ? dd_mul_d(w, P.p[k]) : dd_mul(w, P.q[k]);
-  }
-  return w;
-}
+// exact 128-bit value as double-double times 2^-124
+__device__ __forceinline__ dd fx124(u128 v) { return dd_ldexp(u128_to_dd(v), -124); }
 
 extern "C" __global__ void __launch_bounds__(BS_NTHR)
 bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGradParams Q,
                const u64* __restrict__ lane_tab, const u64* __restrict__ thr_tab,
-               const u64* __restrict__ wmid128, BsWork W) {
+               const u64* __restrict__ wmid128, const dd* __restrict__ ptab,
+               const dd* __restrict__ ptab_ex, BsWork W) {
   extern __shared__ __align__(16) unsigned char smem[];
-  u64* s_lt = (u64*)smem;                          // [4][256][3]
-  u64* s_tt = s_lt + 4 * 256 * 3;                  // [4][256] thread-pattern masses (2^62)
-  u64* s_wm = s_tt + 4 * 256;                      // [2^L][2] walk masses (2^127)
-  u64* s_bins = s_wm + 2 * (1 << BS_L);            // [(L + 1) * 2][NTHR]
-  u128* s_A = (u128*)(s_bins + (BS_L + 1) * 2 * BS_NTHR);  // [L][NTHR]
-  dd* s_wacc = (dd*)(s_A + (BS_L > 0 ? BS_L : 1) * BS_NTHR);
+  u64* s_lt = (u64*)smem;                                   // [4][256][3]
+  u64* s_tt = s_lt + 4 * 256 * 3;                           // [4][256] thread-pattern masses (2^62)
+  u64* s_wm = s_tt + 4 * 256;                               // [2^L][2] walk masses (2^127)
+  u64* s_bins = s_wm + 2 * (1 << BS_L);                     // [(L + 1) * 2][NTHR]
+  u128* s_A = (u128*)(s_bins + (BS_L + 1) * 2 * BS_NTHR);   // [BS_OUT][NTHR]
+  u128* s_red = s_A + (BS_OUT > 0 ? BS_OUT : 1) * BS_NTHR;  // [warps][64] reduced values
+  dd* s_wacc = (dd*)(s_red + (BS_NTHR / 32) * 64);          // [warps][1 + M]
   u64* s_nbins = (u64*)(s_wacc + (BS_NTHR / 32) * (1 + BS_M));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 4 * 256 * 3; i += BS_NTHR) s_lt[i] = lane_tab[i];
@@ -324,21 +335,18 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   for (int i = tid; i <= BS_M; i += BS_NTHR) s_nbins[i] = 0ull;
   __syncthreads();
   dd* wacc = s_wacc + warp * (1 + BS_M);
+  u128* red = s_red + warp * 64;
   u64* bins = s_bins + tid;
   u128* A = s_A + tid;
   const bool thr_on = lane < (1 << BS_TB);
   const int pc_thr = __popc(lane & ((1 << BS_TB) - 1));
-  const dd thr_w = thr_on ? P.thr_w[lane] : dd{0.0, 0.0};
+  const u64 thw = thr_on ? P.thw[lane] : 0ull;
+  // owned arcs (internal positions lane and lane + 32) accumulate in registers
+  dd own0 = dd{0.0, 0.0}, own1 = dd{0.0, 0.0}, ownR = dd{0.0, 0.0};
   const u64 t_start = bs_timer();
   u64 n_walk = 0, n_full = 0, n_dead = 0;
   u32 a[BS_M];
-#pragma unroll
-  for (int i = 0; i < BS_ELL; ++i)
-    a[i] = i == 0 ? 0xAAAAAAAAu : i == 1 ? 0xCCCCCCCCu : i == 2 ? 0xF0F0F0F0u : i == 3 ? 0xFF00FF00u : 0xFFFF0000u;
-#pragma unroll
-  for (int i = 0; i < BS_TB; ++i) a[BS_ELL + i] = 0u - (u32)((lane >> i) & 1);
-#pragma unroll
-  for (int b = 0; b < BS_L; ++b) a[BS_WALK0 + b] = 0u;
+  bs_init_arcs(a, lane);
 
   for (;;) {
     u64 task = 0;
@@ -351,141 +359,337 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     const u64 prefix = P.task_lo + task;
 #pragma unroll
     for (int j = 0; j < BS_D; ++j) a[BS_TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
-    const dd wpre = bs_prefix_mass(P, prefix);
     const int pc_pre = __popcll((long long)prefix);
+    int pr = 0;
     if (P.prune) {
-      u32 u[BS_M];
+      pr = bs_prune(a);
+      if (pr == 1) { ++n_dead; continue; }
+    }
+    u128 S;      // sum over the warp of T x thread mass, scale 2^124
+    if (pr == 2) {
+      ++n_full;
+      for (int j = lane; j <= BS_TOP; j += 32) atomicAdd(&s_nbins[pc_pre + j], P.binom[j]);
+      S = u128{0ull, 1ull << 60};   // the whole item: mass 1 at scale 2^124
+    } else {
+      ++n_walk;
+      u32 e[BS_NCORE > 0 ? BS_NCORE : 1];
+      bs_inv(a, e);
 #pragma unroll
-      for (int k = 0; k < BS_M; ++k) u[k] = k < BS_TOP ? ~0u : a[k];
-      if (bs_uniform(u) == 0u) { ++n_dead; continue; }
+      for (int r = 0; r < (BS_L + 1) * 2; ++r) bins[r * BS_NTHR] = 0ull;
 #pragma unroll
-      for (int k = 0; k < BS_M; ++k) u[k] = k < BS_TOP ? 0u : a[k];
-      if (bs_uniform(u) != 0u) {
-        ++n_full;
-        for (int j = lane; j <= BS_TOP; j += 32) atomicAdd(&s_nbins[pc_pre + j], P.binom[j]);
-        if (lane == 0) wacc[0] = dd_add(wacc[0], wpre);
-        for (int j = lane; j < BS_D; j += 32) {
-          const dd ex = bs_prefix_mass_ex(P, prefix, j);
-          wacc[1 + BS_TOP + j] = ((prefix >> j) & 1ull) ? dd_add(wacc[1 + BS_TOP + j], ex)
-                                                         : dd_add(wacc[1 + BS_TOP + j], dd{-ex.hi, -ex.lo});
+      for (int b = 0; b < BS_OUT; ++b) A[b * BS_NTHR] = u128{0ull, 0ull};
+      u128 T = u128{0ull, 0ull}, T2 = u128{0ull, 0ull};
+      u128 Ain[BS_IN > 0 ? BS_IN : 1];
+#pragma unroll
+      for (int b = 0; b < BS_IN; ++b) Ain[b] = u128{0ull, 0ull};
+      u32 gout = 0;
+      int pco = 0;
+#pragma unroll 1
+      for (u32 s = 0; s < (1u << BS_OUT); ++s) {
+        if (s) {
+          const int b = __ffs(s) - 1;
+          gout ^= 1u << b;
+          const bool on = (gout >> b) & 1u;
+          pco += on ? 1 : -1;
+          // outer walk arc b: A collects the growth of T while the arc works
+          u128 ab = A[b * BS_NTHR];
+          if (on) ab = u128_sub(ab, T); else u128_add(ab, T.lo, T.hi);
+          A[b * BS_NTHR] = ab;
         }
-        continue;
-      }
-    }
-    ++n_walk;
-    u32 e[BS_NCORE > 0 ? BS_NCORE : 1];
-    bs_inv(a, e);
+        u32 w[BS_L > 0 ? BS_L : 1];
 #pragma unroll
-    for (int r = 0; r < (BS_L + 1) * 2; ++r) bins[r * BS_NTHR] = 0ull;
+        for (int b = 0; b < BS_OUT; ++b) w[BS_IN + b] = 0u - ((gout >> b) & 1u);
 #pragma unroll
-    for (int b = 0; b < BS_L; ++b) A[b * BS_NTHR] = u128{0ull, 0ull};
-    u128 T = u128{0ull, 0ull}, T2 = u128{0ull, 0ull};
-    u32 g = 0;
-    int pc = 0;
-#pragma unroll 1
-    for (u32 s = 0; s < (1u << BS_L); ++s) {
-      if (s) {
-        const int b = __ffs(s) - 1;
-        g ^= 1u << b;
-        const bool on = (g >> b) & 1u;
-        pc += on ? 1 : -1;
-        // walk arc b: A_b collects the growth of T while arc b works
-        u128 ab = A[b * BS_NTHR];
-        if (on) ab = u128_sub(ab, T); else u128_add(ab, T.lo, T.hi);
-        A[b * BS_NTHR] = ab;
-      }
-      u32 w[BS_L > 0 ? BS_L : 1];
+        for (int r = 0; r < (1 << BS_IN); ++r) {
 #pragma unroll
-      for (int b = 0; b < BS_L; ++b) w[b] = 0u - ((g >> b) & 1u);
-      const u32 c = bs_var(e, w) & BS_LANE_MASK;
-      const u32 ct = bs_transpose32(c, lane);
-      const u64 wlo = s_wm[2 * g], whi = s_wm[2 * g + 1];
-      if (c) {
-        const u64* t0 = s_lt + (0 * 256 + (c & 0xffu)) * 3;
-        const u64* t1 = s_lt + (1 * 256 + ((c >> 8) & 0xffu)) * 3;
-        const u64* t2 = s_lt + (2 * 256 + ((c >> 16) & 0xffu)) * 3;
-        const u64* t3 = s_lt + (3 * 256 + (c >> 24)) * 3;
-        const u64 sR = t0[0] + t1[0] + t2[0] + t3[0];
-        u64 plo, phi;
-        mul64x128_shr64(sR, wlo, whi, plo, phi);
-        u128_add(T, plo, phi);
-        bins[(2 * pc) * BS_NTHR] += t0[1] + t1[1] + t2[1] + t3[1];
-        bins[(2 * pc + 1) * BS_NTHR] += t0[2] + t1[2] + t2[2] + t3[2];
-      }
-      if (ct) {
-        const u64 s2 = s_tt[ct & 0xffu] + s_tt[256 + ((ct >> 8) & 0xffu)] +
-                       s_tt[512 + ((ct >> 16) & 0xffu)] + s_tt[768 + (ct >> 24)];
-        u64 plo, phi;
-        mul64x128_shr64(s2, wlo, whi, plo, phi);
-        u128_add(T2, plo, phi);
-      }
-    }
-    // walk arcs still working at the end of the walk close their segment
+          for (int b = 0; b < BS_IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
+          const u32 g = (gout << BS_IN) | (u32)r;
+          const u32 c = bs_var(e, w) & BS_LANE_MASK;
+          const u32 ct = bs_transpose32(c, lane);
+          const u64 wlo = s_wm[2 * g], whi = s_wm[2 * g + 1];
+          if (c) {
+            const int pc = pco + __popc(r);
+            const u64* t0 = s_lt + (0 * 256 + (c & 0xffu)) * 3;
+            const u64* t1 = s_lt + (1 * 256 + ((c >> 8) & 0xffu)) * 3;
+            const u64* t2 = s_lt + (2 * 256 + ((c >> 16) & 0xffu)) * 3;
+            const u64* t3 = s_lt + (3 * 256 + (c >> 24)) * 3;
+            const u128 x = mul64x128_shr64(t0[0] + t1[0] + t2[0] + t3[0], wlo, whi);
+            u128_add(T, x.lo, x.hi);
 #pragma unroll
-    for (int b = 0; b < BS_L; ++b)
-      if ((g >> b) & 1u) { u128 ab = A[b * BS_NTHR]; u128_add(ab, T.lo, T.hi); A[b * BS_NTHR] = ab; }
-    if (thr_on) {
-      const int base = pc_pre + pc_thr;
-#pragma unroll 1
-      for (int r = 0; r <= BS_L; ++r) {
-        const u64 n0 = bins[(2 * r) * BS_NTHR], n1 = bins[(2 * r + 1) * BS_NTHR];
-#pragma unroll
-        for (int cl = 0; cl < 3; ++cl) {
-          const u64 c0 = (n0 >> (21 * cl)) & 0x1fffffull, c1 = (n1 >> (21 * cl)) & 0x1fffffull;
-          if (c0) atomicAdd(&s_nbins[base + r + cl], c0);
-          if (c1) atomicAdd(&s_nbins[base + r + 3 + cl], c1);
+            for (int b = 0; b < BS_IN; ++b)
+              if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
+            bins[(2 * pc) * BS_NTHR] += t0[1] + t1[1] + t2[1] + t3[1];
+            bins[(2 * pc + 1) * BS_NTHR] += t0[2] + t1[2] + t2[2] + t3[2];
+          }
+          if (ct) {
+            const u64 s2 = s_tt[ct & 0xffu] + s_tt[256 + ((ct >> 8) & 0xffu)] +
+                           s_tt[512 + ((ct >> 16) & 0xffu)] + s_tt[768 + (ct >> 24)];
+            const u128 x2 = mul64x128_shr64(s2, wlo, whi);
+            u128_add(T2, x2.lo, x2.hi);
+          }
         }
       }
-    }
-    // ---- item epilogue
-    const dd t = dd_ldexp(u128_to_dd(T), -125);
-    const dd S = bs_warp_sum(dd_mul(thr_w, t));      // sum over threads of thread mass * T
-    if (lane == 0) wacc[0] = dd_add(wacc[0], dd_mul(wpre, S));
-    for (int j = lane; j < BS_D; j += 32) {
-      const dd ex = dd_mul(bs_prefix_mass_ex(P, prefix, j), S);
-      wacc[1 + BS_TOP + j] = ((prefix >> j) & 1ull) ? dd_add(wacc[1 + BS_TOP + j], ex)
-                                                     : dd_add(wacc[1 + BS_TOP + j], dd{-ex.hi, -ex.lo});
-    }
-    const double sc = 2.3509887016445750e-38;  // 2^-125
 #pragma unroll
-    for (int i = 0; i < BS_TB; ++i) {
-      const u128 o = shfl_u128(T, 1 << i);
-      double y = 0.0;
-      if (((lane >> i) & 1) && thr_on) y = u128_to_double(u128_sub(T, o)) * sc * Q.thr_w_ex[i][lane].hi;
-      y = bs_warp_sum_d(y);
-      if (lane == i) wacc[1 + BS_ELL + i] = dd_add(wacc[1 + BS_ELL + i], dd_mul_d(wpre, y));
-    }
+      for (int b = 0; b < BS_OUT; ++b)
+        if ((gout >> b) & 1u) { u128 ab = A[b * BS_NTHR]; u128_add(ab, T.lo, T.hi); A[b * BS_NTHR] = ab; }
+      if (thr_on) bs_flush_bins(bins, s_nbins, pc_pre + pc_thr);
+      // ---- exact warp sums; slot k of `red` holds internal arc k's value
+      S = warp_sum_u128(mul64x128_shr64(thw, T.lo, T.hi));
 #pragma unroll
-    for (int i = 0; i < BS_ELL; ++i) {
-      const u128 o = shfl_u128(T2, 1 << i);
-      double y = 0.0;
-      if ((lane >> i) & 1) y = u128_to_double(u128_sub(T2, o)) * sc * Q.lane_w_ex[i][lane].hi;
-      y = bs_warp_sum_d(y);
-      if (lane == i) wacc[1 + i] = dd_add(wacc[1 + i], dd_mul_d(wpre, y));
+      for (int i = 0; i < BS_ELL; ++i) {
+        const u128 o = shfl_xor_u128(T2, 1 << i);
+        const u128 d2 = u128_sub(T2, o);
+        const u128 v = ((lane >> i) & 1) ? mul64x128_shr64(Q.lw_ex[i][lane], d2.lo, d2.hi) : u128{0ull, 0ull};
+        const u128 sv = warp_sum_u128(v);
+        if (lane == 0) red[i] = sv;
+      }
+#pragma unroll
+      for (int i = 0; i < BS_TB; ++i) {
+        const u128 o = shfl_xor_u128(T, 1 << i);
+        const u128 d1 = u128_sub(T, o);
+        const u128 v = (((lane >> i) & 1) && thr_on) ? mul64x128_shr64(Q.thw_ex[i][lane], d1.lo, d1.hi)
+                                                     : u128{0ull, 0ull};
+        const u128 sv = warp_sum_u128(v);
+        if (lane == 0) red[BS_ELL + i] = sv;
+      }
+#pragma unroll
+      for (int b = 0; b < BS_L; ++b) {
+        const u128 Ab = b < BS_IN ? Ain[b < BS_IN ? b : 0] : A[(b >= BS_IN ? b - BS_IN : 0) * BS_NTHR];
+        const u128 sa = warp_sum_u128(mul64x128_shr64(thw, Ab.lo, Ab.hi));
+        const u128 z = u128_sub(T, Ab);
+        const u128 sz = warp_sum_u128(mul64x128_shr64(thw, z.lo, z.hi));
+        if (lane == 0) { red[BS_WALK0 + b] = sa; red[32 + ((BS_WALK0 + b) & 31)] = sz; }
+      }
+      __syncwarp();
     }
-#pragma unroll 1
-    for (int b = 0; b < BS_L; ++b) {
-      const int k = BS_WALK0 + b;
-      const u128 Ab = A[b * BS_NTHR];
-      const dd av = u128_to_dd(Ab), zv = u128_to_dd(u128_sub(T, Ab));
-      const dd yv = dd_add(dd_mul(av, Q.inv_p[k]), dd{-(dd_mul(zv, Q.inv_q[k])).hi, -(dd_mul(zv, Q.inv_q[k])).lo});
-      double y = thr_on ? dd_mul(dd_ldexp(yv, -125), thr_w).hi : 0.0;
-      y = bs_warp_sum_d(y);
-      if (lane == (k & 31)) wacc[1 + k] = dd_add(wacc[1 + k], dd_mul_d(wpre, y));
+    // ---- per-arc arithmetic on the owning lanes (internal arcs lane, lane + 32)
+    const dd wpre = bs_prefix_mass(P, ptab, prefix);
+    const dd Sd = fx124(S);
+    if (lane == 0) ownR = dd_add(ownR, dd_mul(wpre, Sd));
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int k = lane + 32 * half;
+      if (k >= BS_M) continue;
+      dd v = dd{0.0, 0.0};
+      if (k >= BS_TOP) {
+        // prefix arc: the item's mass without this arc's factor, with sign
+        const int j = k - BS_TOP;
+        int l = 0, sh = 0;
+        while (sh + P.lev_bits[l] <= j) { sh += P.lev_bits[l]; ++l; }
+        dd ex = dd{1.0, 0.0};
+        int s2 = 0;
+        for (int q = 0; q < P.nlev; ++q) {
+          const u64 bits = (prefix >> s2) & ((1ull << P.lev_bits[q]) - 1ull);
+          const dd f = q == l ? ptab_ex[((size_t)j << 11) + bits] : ptab[P.lev_off[q] + bits];
+          ex = q ? dd_mul(ex, f) : f;
+          s2 += P.lev_bits[q];
+        }
+        v = dd_mul(ex, Sd);
+        if (!((prefix >> j) & 1ull)) v = dd_neg(v);
+      } else if (pr != 2) {
+        if (k < BS_WALK0) {
+          v = dd_mul(wpre, fx124(red[k]));
+        } else {
+          // walk arc: A / p - (T - A) / (1 - p), both exact integers
+          const dd av = fx124(red[k]), zv = fx124(red[32 + (k & 31)]);
+          v = dd_mul(wpre, dd_add(dd_mul(av, Q.inv_p[k]), dd_neg(dd_mul(zv, Q.inv_q[k]))));
+        }
+      }
+      if (half == 0) own0 = dd_add(own0, v); else own1 = dd_add(own1, v);
     }
+    __syncwarp();
   }
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
   }
+  if (lane == 0) wacc[0] = ownR;
+  if (lane < BS_M) wacc[1 + lane] = own0;
+  if (lane + 32 < BS_M) wacc[1 + lane + 32] = own1;
   __syncthreads();
-  for (int i = tid; i <= BS_M; i += BS_NTHR) {
-    dd sacc = dd{0.0, 0.0};
-    for (int w2 = 0; w2 < BS_NTHR / 32; ++w2) sacc = dd_add(sacc, s_wacc[w2 * (1 + BS_M) + i]);
-    W.part_acc[(size_t)blockIdx.x * (1 + BS_M) + i] = sacc;
-    W.part_n[(size_t)blockIdx.x * (BS_M + 1) + i] = s_nbins[i];
-  }
+  bs_write_partials(W, s_wacc, s_nbins);
 }
 #endif
 )PBAT";
 
+
+// Batched: every network's connectivity program is a struct of static
+// functions (inv, var) with its sizes as constants; one persistent kernel
+// takes (network, prefix) items from one ticket -- networks with the most
+// items first -- and switches to that network's item function.  Each word's
+// 32-state connectivity is computed once and weighted by every p-vector of
+// the chunk (byte tables interleaved by p-vector, read through L1); per item
+// and p-vector the result is added exactly into a 160-bit accumulator of
+// five 64-bit limbs with integer atomics.
+static const char* kBsBatchTemplate = R"PBAT(
+#define BSB_LIMBS 5
+#define BSB_SCALE 158
+struct BGraph {
+  u64 task_begin, n_tasks;
+  int gidx, m, nlev, prune;
+  int lev_bits[6], lev_off[6];
+  int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, pad;
+  u64 binom[64];
+};
+
+// add round(x * 2^BSB_SCALE) (x may be negative) to the limbs, 32 bits per limb
+__device__ void bsb_limb_add(u64* limbs, double x) {
+  if (x == 0.0) return;
+  const bool neg = x < 0.0;
+  int ex;
+  const double mant = frexp(fabs(x), &ex);
+  long long M = (long long)ldexp(mant, 53);
+  int e = ex - 53 + BSB_SCALE;
+  if (e < 0) {
+    if (-e > 62) return;
+    M = (M + (1ll << (-e - 1))) >> (-e);
+    e = 0;
+    if (M == 0) return;
+  }
+  const int c = e >> 5, sh = e & 31;
+  const unsigned __int128 v = (unsigned __int128)(u64)M << sh;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const u64 chunk = (u64)(u32)(v >> (32 * i));
+    if (chunk && c + i < BSB_LIMBS) atomicAdd(&limbs[c + i], neg ? (u64)(-(long long)chunk) : chunk);
+  }
+}
+
+__device__ __forceinline__ dd bsb_prefix_mass(const BGraph& B, const dd* __restrict__ pt, int k, u64 prefix) {
+  dd w = dd{1.0, 0.0};
+  int sh = 0;
+  const dd* t = pt + B.pt_off + (size_t)k * B.pt_size;
+  for (int l = 0; l < B.nlev; ++l) {
+    const u64 v = (prefix >> sh) & ((1ull << B.lev_bits[l]) - 1ull);
+    w = l ? dd_mul(w, t[B.lev_off[l] + v]) : t[B.lev_off[l] + v];
+    sh += B.lev_bits[l];
+  }
+  return w;
+}
+
+template <class G>
+__device__ __forceinline__ u32 bsb_uniform(const u32* a) {
+  u32 e[G::NCORE > 0 ? G::NCORE : 1];
+  G::inv(a, e);
+  u32 w[G::L > 0 ? G::L : 1];
+#pragma unroll
+  for (int b = 0; b < G::L; ++b) w[b] = a[G::WALK0 + b];
+  return G::var(e, w);
+}
+
+template <class G, int KC>
+__device__ void bsb_item(const BGraph& B, u64 prefix, int lane, int K, int k0, int kc,
+                         const u64* __restrict__ lt, const u64* __restrict__ nt,
+                         const u64* __restrict__ wm, const dd* __restrict__ pt,
+                         const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins) {
+  constexpr int IN = G::L >= 2 ? 2 : G::L;
+  constexpr int OUT = G::L - IN;
+  u32 a[G::M];
+#pragma unroll
+  for (int i = 0; i < G::ELL; ++i)
+    a[i] = i == 0 ? 0xAAAAAAAAu : i == 1 ? 0xCCCCCCCCu : i == 2 ? 0xF0F0F0F0u : i == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+#pragma unroll
+  for (int i = 0; i < G::TB; ++i) a[G::ELL + i] = 0u - (u32)((lane >> i) & 1);
+#pragma unroll
+  for (int b = 0; b < G::L; ++b) a[G::WALK0 + b] = 0u;
+#pragma unroll
+  for (int j = 0; j < G::D; ++j) a[G::TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
+  const int pc_pre = __popcll((long long)prefix);
+  const size_t gk0 = (size_t)B.gidx * K + k0;
+  if (B.prune) {
+    u32 u[G::M];
+#pragma unroll
+    for (int k = 0; k < G::M; ++k) u[k] = k < G::TOP ? ~0u : a[k];
+    if (bsb_uniform<G>(u) == 0u) return;
+#pragma unroll
+    for (int k = 0; k < G::M; ++k) u[k] = k < G::TOP ? 0u : a[k];
+    if (bsb_uniform<G>(u) != 0u) {
+      if (k0 == 0)
+        for (int j = lane; j <= G::TOP; j += 32) atomicAdd(&nk[B.nk_off + pc_pre + j], B.binom[j]);
+      if (lane < kc) {
+        const dd w = bsb_prefix_mass(B, pt, k0 + lane, prefix);
+        bsb_limb_add(limbs + (gk0 + lane) * BSB_LIMBS, w.hi);
+        bsb_limb_add(limbs + (gk0 + lane) * BSB_LIMBS, w.lo);
+      }
+      return;
+    }
+  }
+  u32 e[G::NCORE > 0 ? G::NCORE : 1];
+  G::inv(a, e);
+  const bool count = k0 == 0;
+  if (count)
+#pragma unroll
+    for (int r = 0; r < (G::L + 1) * 2; ++r) bins[r * BSB_NTHR] = 0ull;
+  u128 T[KC];
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) T[kk] = u128{0ull, 0ull};
+  const u64* ltk = lt + B.lt_off + k0;
+  const u64* wmk = wm + B.wm_off + k0;
+  const u64* ntg = nt + B.nt_off;
+  u32 gout = 0;
+  int pco = 0;
+#pragma unroll 1
+  for (u32 s = 0; s < (1u << OUT); ++s) {
+    if (s) {
+      const int b = __ffs(s) - 1;
+      gout ^= 1u << b;
+      pco += ((gout >> b) & 1u) ? 1 : -1;
+    }
+    u32 w[G::L > 0 ? G::L : 1];
+#pragma unroll
+    for (int b = 0; b < OUT; ++b) w[IN + b] = 0u - ((gout >> b) & 1u);
+#pragma unroll
+    for (int r = 0; r < (1 << IN); ++r) {
+#pragma unroll
+      for (int b = 0; b < IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
+      const u32 c = G::var(e, w) & G::LANE_MASK;
+      if (!c) continue;
+      const u32 g = (gout << IN) | (u32)r;
+      const size_t i0 = (size_t)(0 * 256 + (c & 0xffu)) * K, i1 = (size_t)(1 * 256 + ((c >> 8) & 0xffu)) * K;
+      const size_t i2 = (size_t)(2 * 256 + ((c >> 16) & 0xffu)) * K, i3 = (size_t)(3 * 256 + (c >> 24)) * K;
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) {
+        if (kk >= kc) break;
+        const u64 sR = __ldg(ltk + i0 + kk) + __ldg(ltk + i1 + kk) + __ldg(ltk + i2 + kk) + __ldg(ltk + i3 + kk);
+        const u64 wmv = __ldg(wmk + (size_t)g * K + kk);
+        u128_add(T[kk], sR * wmv, __umul64hi(sR, wmv));
+      }
+      if (count) {
+        const int pc = pco + __popc(r);
+        const u64* n0 = ntg + (size_t)(0 * 256 + (c & 0xffu)) * 2;
+        const u64* n1 = ntg + (size_t)(1 * 256 + ((c >> 8) & 0xffu)) * 2;
+        const u64* n2 = ntg + (size_t)(2 * 256 + ((c >> 16) & 0xffu)) * 2;
+        const u64* n3 = ntg + (size_t)(3 * 256 + (c >> 24)) * 2;
+        bins[(2 * pc) * BSB_NTHR] += __ldg(n0) + __ldg(n1) + __ldg(n2) + __ldg(n3);
+        bins[(2 * pc + 1) * BSB_NTHR] += __ldg(n0 + 1) + __ldg(n1 + 1) + __ldg(n2 + 1) + __ldg(n3 + 1);
+      }
+    }
+  }
+  if (count && lane < (1 << G::TB)) {
+    const int base = B.nk_off + pc_pre + __popc(lane & ((1 << G::TB) - 1));
+#pragma unroll 1
+    for (int r = 0; r <= G::L; ++r) {
+      const u64 n0 = bins[(2 * r) * BSB_NTHR], n1 = bins[(2 * r + 1) * BSB_NTHR];
+#pragma unroll
+      for (int cl = 0; cl < 3; ++cl) {
+        const u64 c0 = (n0 >> (21 * cl)) & 0x1fffffull, c1 = (n1 >> (21 * cl)) & 0x1fffffull;
+        if (c0) atomicAdd(&nk[base + r + cl], c0);
+        if (c1) atomicAdd(&nk[base + r + 3 + cl], c1);
+      }
+    }
+  }
+  const bool thr_on = lane < (1 << G::TB);
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) {
+    if (kk >= kc) break;
+    const u64 tw = thr_on ? __ldg(thw + B.thw_off + (size_t)lane * K + k0 + kk) : 0ull;
+    const u128 S = warp_sum_u128(mul64x128_shr64(tw, T[kk].lo, T[kk].hi));
+    if (lane == kk) {
+      const dd v = dd_mul(bsb_prefix_mass(B, pt, k0 + kk, prefix), dd_ldexp(u128_to_dd(S), -124));
+      bsb_limb_add(limbs + (gk0 + kk) * BSB_LIMBS, v.hi);
+      bsb_limb_add(limbs + (gk0 + kk) * BSB_LIMBS, v.lo);
+    }
+  }
+}
+//@@BATCH_KERNEL@@
+)PBAT";
 }  // namespace pbat

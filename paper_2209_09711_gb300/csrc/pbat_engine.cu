@@ -43,7 +43,9 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
                const DeviceInfo& dev, BsLaunch& bl);
 cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsigned long long* d_lane,
                       const unsigned long long* d_thr, const unsigned long long* d_wmid,
-                      const DevWork& W);
+                      const dd* d_ptab, const dd* d_ptab_ex, const DevWork& W);
+const std::vector<dd>& bs_ptab(const BsLaunch& bl);
+const std::vector<dd>& bs_ptab_ex(const BsLaunch& bl);
 const std::vector<unsigned long long>& bs_thr_tab(const BsLaunch& bl);
 bool bs_grad(const BsLaunch& bl);
 const std::vector<int>& bs_perm(const BsLaunch& bl);
@@ -54,7 +56,8 @@ int bs_nthr(const BsLaunch& bl);
 const std::vector<unsigned long long>& bs_lane_tab(const BsLaunch& bl);
 const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl);
 void bs_describe(const BsLaunch& bl, int* out6);
-int bs_source_for(const GraphIn& g, const pbat_options& o, std::string& out);
+int bs_source_for(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
+                  std::string& out);
 
 // ---------------------------------------------------------------------------
 // errors
@@ -375,6 +378,8 @@ struct Job {
   unsigned long long* d_lane = nullptr;
   unsigned long long* d_thr = nullptr;
   unsigned long long* d_wmid64 = nullptr;
+  dd* d_ptab = nullptr;
+  dd* d_ptabx = nullptr;
   double abs_err_bound = 0.0;  // of R, relative to the enumerated probability mass
   double mass = 1.0;           // probability mass of the enumerated states
   std::vector<int> perm;       // internal arc position -> input arc
@@ -497,7 +502,7 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
   double best_ms = 1e300;
   int best_L = -1, best_nt = 128;
   for (int L : Ls)
-    for (int nt : {128, 256}) {
+    for (int nt : {128, 192, 256}) {
       pbat_options t = o;
       t.autotune = 0;
       t.walk_bits = L;
@@ -616,11 +621,14 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t o_out_acc = off; off = up16(off + (size_t)(1 + m) * sizeof(dd));
   const size_t o_out_n = off; off = up16(off + (size_t)(m + 1) * 8);
   const size_t o_wmid = off; off = up16(off + wmid.size() * sizeof(u128));
-  size_t o_lane = 0, o_thr = 0, o_wmid64 = 0;
+  size_t o_lane = 0, o_thr = 0, o_wmid64 = 0, o_ptab = 0, o_ptabx = 0, o_tab_end = 0;
   if (J->bs) {
     o_lane = off; off = up16(off + bs_lane_tab(*J->bs).size() * 8);
     o_thr = off; off = up16(off + bs_thr_tab(*J->bs).size() * 8);
     o_wmid64 = off; off = up16(off + bs_wmid(*J->bs).size() * 8);
+    o_ptab = off; off = up16(off + bs_ptab(*J->bs).size() * sizeof(dd));
+    o_ptabx = off; off = up16(off + bs_ptab_ex(*J->bs).size() * sizeof(dd));
+    o_tab_end = off;
   }
   const size_t dbytes = off;
   // host (pinned) layout: results + staging of the walk table
@@ -630,11 +638,10 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t h_status = hoff; hoff = up16(hoff + 4);
   const size_t h_stats = hoff; hoff = up16(hoff + 3 * 8);
   const size_t h_wmid = hoff; hoff = up16(hoff + wmid.size() * sizeof(u128));
-  size_t h_lane = 0, h_thr = 0, h_wmid64 = 0;
+  size_t h_lane = 0;
   if (J->bs) {
-    h_lane = hoff; hoff = up16(hoff + bs_lane_tab(*J->bs).size() * 8);
-    h_thr = hoff; hoff = up16(hoff + bs_thr_tab(*J->bs).size() * 8);
-    h_wmid64 = hoff; hoff = up16(hoff + bs_wmid(*J->bs).size() * 8);
+    h_lane = hoff;
+    hoff = up16(hoff + (o_tab_end - o_lane));  // same layout as the device tables
   }
   const size_t hbytes = hoff;
   if ((rc = scratch_acquire(J->dev.device, dbytes, hbytes, &J->scr))) return rc;
@@ -660,14 +667,21 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
     const auto& lt = bs_lane_tab(*J->bs);
     const auto& tt = bs_thr_tab(*J->bs);
     const auto& wm = bs_wmid(*J->bs);
-    memcpy(h + h_lane, lt.data(), lt.size() * 8);
-    if (!tt.empty()) memcpy(h + h_thr, tt.data(), tt.size() * 8);
-    memcpy(h + h_wmid64, wm.data(), wm.size() * 8);
+    const auto& pt = bs_ptab(*J->bs);
+    const auto& px = bs_ptab_ex(*J->bs);
+    char* hb = h + h_lane - o_lane;  // host mirror of the device table block
+    memcpy(hb + o_lane, lt.data(), lt.size() * 8);
+    if (!tt.empty()) memcpy(hb + o_thr, tt.data(), tt.size() * 8);
+    memcpy(hb + o_wmid64, wm.data(), wm.size() * 8);
+    memcpy(hb + o_ptab, pt.data(), pt.size() * sizeof(dd));
+    if (!px.empty()) memcpy(hb + o_ptabx, px.data(), px.size() * sizeof(dd));
     J->d_lane = (unsigned long long*)(d + o_lane);
     J->d_thr = (unsigned long long*)(d + o_thr);
     J->d_wmid64 = (unsigned long long*)(d + o_wmid64);
+    J->d_ptab = (dd*)(d + o_ptab);
+    J->d_ptabx = (dd*)(d + o_ptabx);
     J->wmid_host_staging = h + h_lane;
-    J->wmid_bytes = (o_wmid64 - o_lane) + wm.size() * 8;
+    J->wmid_bytes = o_tab_end - o_lane;
     J->d_wmid = (u128*)(d + o_lane);  // upload destination
   }
   *out = J.release();
@@ -696,7 +710,8 @@ int job_launch(Job* J, cudaStream_t st) {
   }
   if (timed) PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].first, st));
   if (J->bs)
-    PBAT_CUDA(bs_launch(*J->bs, J->grid, st, J->d_lane, J->d_thr, J->d_wmid64, J->W));
+    PBAT_CUDA(bs_launch(*J->bs, J->grid, st, J->d_lane, J->d_thr, J->d_wmid64, J->d_ptab,
+                        J->d_ptabx, J->W));
   else
     PBAT_CUDA(launch_frontier(J->pl.grad, J->pl.wide, J->grid, J->pl.nthr, J->pl.smem, st, J->P,
                               J->d_wmid, J->W));
@@ -835,18 +850,19 @@ int pbat_reliability_grad(int n_nodes, int n_arcs, const int32_t* tail, const in
 }
 
 int pbat_kernel_source(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
-                       int directed, int source, int sink, const pbat_options* opt, char* buf,
-                       size_t cap) {
+                       int directed, const double* p, int source, int sink, int want_grad,
+                       const pbat_options* opt, char* buf, size_t cap) {
   try {
     pbat::clear_error();
     pbat::GraphIn g{n_nodes, n_arcs, tail, head, directed, source, sink};
     int rc;
     if ((rc = pbat::validate_graph(g)) || (rc = pbat::validate_options(opt, n_arcs))) return rc;
+    if (p && (rc = pbat::validate_p(p, n_arcs))) return rc;
     pbat_options o;
     pbat_options_init(&o);
     if (opt) o = *opt;
     std::string src;
-    if ((rc = pbat::bs_source_for(g, o, src))) return rc;
+    if ((rc = pbat::bs_source_for(g, p, want_grad != 0, o, src))) return rc;
     if (buf && cap) {
       const size_t n = std::min(cap - 1, src.size());
       memcpy(buf, src.data(), n);

@@ -85,6 +85,33 @@ def test_generated_program_matches_oracle(pb, directed):
             _check(pb, net, seed, pb.options(walk_bits=walk))
 
 
+def test_plans_are_consistent_for_every_shape(pb):
+    """Role assignment of the bit-sliced kernels: a permutation of the arcs,
+    range arcs on top in input order, walk length within the free arcs --
+    over sizes, ranges, walk requests and both kernels (a plan that broke
+    these sent out-of-range arc indices to the device)."""
+    checked = 0
+    for seed in range(40):
+        rng = synth.SplitMix64(31337 + seed)
+        m = 1 + rng.below(63)
+        n = 2 + rng.below(62)
+        net = synth.random_small(12000 + seed, n=n, m=m, directed=bool(seed & 1))
+        for grad in (False, True):
+            for r in sorted({0, m // 2, max(0, m - 12), m}):
+                if r and m - r < 0:
+                    continue
+                for walk in (-1, 0, 4, 10, 12):
+                    o = pb.options(walk_bits=walk, range_bits=r, range_lo=0, range_hi=1 if r else 0)
+                    src = pb.kernel_source(net, o, grad=grad)
+                    perm, D, _, _ = _parse(src)
+                    assert sorted(perm) == list(range(m)), (m, r, walk, grad)
+                    assert all(perm[m - 1 - i] == i for i in range(r))
+                    assert D["BS_D"] >= r and 0 <= D["BS_L"] <= 10
+                    assert D["BS_ELL"] + D["BS_TB"] + D["BS_L"] + D["BS_D"] == m
+                    checked += 1
+    assert checked > 500
+
+
 def test_generated_program_workloads(pb):
     for net in (synth.workload_grid_3x6(), synth.workload_directed_20_34(),
                 synth.workload_random_24_40(), synth.workload_small_random(), synth.figure1()):

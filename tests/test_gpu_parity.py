@@ -224,6 +224,17 @@ def test_batched_against_oracle(pb):
                     ref.grad_t1t0[i], ref.T1[i], ref.T0[i], ref.R)
 
 
+def test_batched_frontier_kernel_matches_bitsliced(pb):
+    nets, pvecs = synth.workload_batched(12, 5)
+    R1, N1, _ = pb.reliability_batched(nets, pvecs, opts=pb.options(algo=pb.ALGO_FRONTIER))
+    R2, N2, _ = pb.reliability_batched(nets, pvecs, opts=pb.options(algo=pb.ALGO_BITSLICE))
+    assert N1 == N2
+    assert np.max(np.abs(R1 - R2) / R1) <= 1e-13
+    # prune off gives the same counts
+    R3, N3, _ = pb.reliability_batched(nets, pvecs, opts=pb.options(prune=0))
+    assert N3 == N2 and np.max(np.abs(R3 - R2) / R2) <= 1e-13
+
+
 def test_batched_workload_matches_single(pb):
     nets, pvecs = synth.workload_batched()
     R, Nk, _ = pb.reliability_batched(nets, pvecs)
