@@ -46,12 +46,13 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "grid-3x6"
 
 # Warp instructions executed per state by the fused enumeration kernel
-# (bs_kernel_grad) on each workload, from ncu (smsp__inst_executed.sum of
-# one launch / 2^m): the per-unit figure of the issue-rate roofline.
+# (bs_kernel_grad), from ncu (smsp__inst_executed.sum of one launch / 2^m):
+# the per-unit figure of the issue-rate roofline, keyed by workload and the
+# launch shape (walk arcs, threads per block) the capture ran with, because
+# the autotuner picks the shape per run.  DRAM traffic per launch
+# (dram__bytes_read.sum + dram__bytes_write.sum) from the same capture.
 # Source: profiles/bs_kernel_grad_grid3x6.md
 INST_PER_STATE = {}
-# DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum),
-# same capture; None until measured for the current kernel.
 DRAM_BYTES_PER_LAUNCH = {}
 
 SM_COUNT = 152
@@ -290,13 +291,15 @@ def run_ours(a):
                          f"(R, N_k, T1/T0 gradient), {info['wall_s']:.1f} s wall on {cores} host "
                          f"processes, extrapolated to states/s"}
 
-    ipc = INST_PER_STATE.get(a.workload)
+    shape = fused.describe()
+    shape_key = (a.workload, shape["walk_bits"], shape["block_threads"])
+    ipc = INST_PER_STATE.get(shape_key)
     peak = SM_COUNT * ISSUE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9  # G warp-inst/s
     if ipc is not None:
         achieved = ipc * states / (kern_f / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
                 "frac": achieved / peak,
-                "traffic": DRAM_BYTES_PER_LAUNCH.get(a.workload),
+                "traffic": DRAM_BYTES_PER_LAUNCH.get(shape_key),
                 "kernel": "bs_kernel_grad", "kernel_ms": kern_f}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s",
@@ -311,8 +314,9 @@ def run_ours(a):
                    "l2": "flushed between steps (256 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": roof,
+        "fused_shape": shape,
         "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r,
-                   "kernel": "bs_kernel"},
+                   "kernel": "bs_kernel", "shape": ronly.describe()},
         "plain_gpu_bat": {"value": ws * states / (ms_p / 1e3), "ms_per_step": ms_p,
                           "kernel": "frontier_kernel (one state per thread, PLSA frontier)",
                           "fused_value": ws * states / (ms_pg / 1e3), "fused_ms_per_step": ms_pg},
@@ -348,7 +352,7 @@ def run_probe(a):
     plan.execute(0)
     r = plan.read(0)
     print(json.dumps({"probe": a.probe, "workload": a.workload, "R": r.R,
-                      "kernel_ms": r.stats[4] / 1e6, "items": r.stats[6]}))
+                      "kernel_ms": r.stats[4] / 1e6, "items": r.stats[6], "shape": plan.describe()}))
     plan.close()
     return 0
 

@@ -158,6 +158,11 @@ int pbat_plan_execute(pbat_plan plan, void* cuda_stream);
 int pbat_plan_read(pbat_plan plan, void* cuda_stream, double* R_out, uint64_t* Nk_out,
                    double* dRdp_out);
 void pbat_plan_destroy(pbat_plan plan);
+/* Describe a plan (no device work): out8 = {algo (PBAT_ALGO_FRONTIER or
+ * PBAT_ALGO_BITSLICE), lane arcs, thread arcs (0 for the frontier kernel),
+ * walk arcs, prefix arcs, threads per block, blocks, 1 if the gradient is
+ * computed}. */
+int pbat_plan_describe(pbat_plan plan, int* out8);
 /* Copy the plan's statistics (the pbat_options.stats[8] layout, as filled by
  * the last pbat_plan_read) into stats_out[8]. */
 int pbat_plan_stats(pbat_plan plan, uint64_t* stats_out);
@@ -204,6 +209,13 @@ int pbat_reliability_noalloc(int n_nodes, int n_arcs, const int32_t* tail, const
 int pbat_kernel_source(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
                        int directed, const double* p, int source, int sink, int want_grad,
                        const pbat_options* opt, char* buf, size_t cap);
+
+/* Diagnostic, no GPU needed: the CUDA C++ source of the batched bit-sliced
+ * module (every network's connectivity program and the persistent kernel)
+ * for these networks and n_pvec p-vectors.  Same buffer convention as
+ * pbat_kernel_source. */
+int pbat_batch_kernel_source(int n_graphs, const pbat_graph* graphs, int n_pvec,
+                             const pbat_options* opt, char* buf, size_t cap);
 
 /* Thread-local description of the last error in this thread ("" if none). */
 const char* pbat_last_error(void);

@@ -80,7 +80,8 @@ _lib = None
 EXPORTED = [
     "pbat_options_init", "pbat_reliability", "pbat_reliability_grad",
     "pbat_reliability_batched", "pbat_plan_create", "pbat_plan_execute", "pbat_plan_read",
-    "pbat_plan_destroy", "pbat_plan_stats", "pbat_reliability_noalloc", "pbat_kernel_source",
+    "pbat_plan_destroy", "pbat_plan_stats", "pbat_plan_describe", "pbat_reliability_noalloc",
+    "pbat_kernel_source", "pbat_batch_kernel_source",
     "pbat_last_error", "pbat_version",
 ]
 
@@ -117,6 +118,8 @@ def load(path: Optional[str] = None):
         lib.pbat_plan_read.restype = I
         lib.pbat_plan_stats.argtypes = [V, PU]
         lib.pbat_plan_stats.restype = I
+        lib.pbat_plan_describe.argtypes = [V, ctypes.POINTER(ctypes.c_int)]
+        lib.pbat_plan_describe.restype = I
         lib.pbat_plan_destroy.argtypes = [V]
         lib.pbat_plan_destroy.restype = None
         lib.pbat_reliability_noalloc.argtypes = [I, I, PI32, PI32, I, PD, I, I, PO, V, PD, PU]
@@ -124,6 +127,9 @@ def load(path: Optional[str] = None):
         lib.pbat_kernel_source.argtypes = [I, I, PI32, PI32, I, PD, I, I, I, PO, ctypes.c_char_p,
                                            ctypes.c_size_t]
         lib.pbat_kernel_source.restype = I
+        lib.pbat_batch_kernel_source.argtypes = [I, ctypes.POINTER(Graph), I, PO, ctypes.c_char_p,
+                                                 ctypes.c_size_t]
+        lib.pbat_batch_kernel_source.restype = I
         lib.pbat_last_error.argtypes = []
         lib.pbat_last_error.restype = ctypes.c_char_p
         lib.pbat_version.argtypes = []
@@ -273,6 +279,14 @@ class Plan:
         _check(load().pbat_plan_stats(self._handle, st))
         return Result(R.value, list(Nk), g, list(st))
 
+    def describe(self) -> dict:
+        """Kernel and split the plan uses (pbat_plan_describe)."""
+        out = (ctypes.c_int * 8)()
+        _check(load().pbat_plan_describe(self._handle, out))
+        return dict(kernel="bitslice" if out[0] == ALGO_BITSLICE else "frontier", lane_bits=out[1],
+                    thread_bits=out[2], walk_bits=out[3], prefix_bits=out[4], block_threads=out[5],
+                    blocks=out[6], grad=bool(out[7]))
+
     def close(self):
         if self._handle:
             load().pbat_plan_destroy(self._handle)
@@ -299,6 +313,25 @@ def kernel_source(net, opts: Optional[Options] = None, grad: bool = False, p=Non
     buf = ctypes.create_string_buffer(n + 1)
     lib.pbat_kernel_source(net.n, len(t), tp, hp, int(net.directed), pp, net.source, net.sink,
                            int(grad), ctypes.byref(o), buf, n + 1)
+    return buf.value.decode()
+
+
+def batch_kernel_source(nets, n_pvec: int, opts: Optional[Options] = None) -> str:
+    """The generated CUDA source of the batched bit-sliced module."""
+    lib = load()
+    keep = []
+    graphs = (Graph * len(nets))()
+    for i, net in enumerate(nets):
+        t, tp = _i32(net.tail)
+        h, hp = _i32(net.head)
+        keep += [t, h]
+        graphs[i] = Graph(net.n, len(t), tp, hp, int(net.directed), net.source, net.sink)
+    o = opts if opts is not None else options()
+    n = lib.pbat_batch_kernel_source(len(nets), graphs, n_pvec, ctypes.byref(o), None, 0)
+    if n < 0:
+        _check(n)
+    buf = ctypes.create_string_buffer(n + 1)
+    lib.pbat_batch_kernel_source(len(nets), graphs, n_pvec, ctypes.byref(o), buf, n + 1)
     return buf.value.decode()
 
 

@@ -340,14 +340,24 @@ static int jit_compile(const std::string& src, const DeviceInfo& dev, const char
       NVRTC_SUCCESS)
     return fail(PBAT_ECUDA, "nvrtcCreateProgram failed");
   const std::string arch = "-arch=sm_" + std::to_string(dev.cc_major * 10 + dev.cc_minor) + "a";
-  const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo"};
-  const nvrtcResult rc = nvrtcCompileProgram(prog, 3, opts);
+  const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo", "-diag-suppress=177"};
+  const nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
   if (rc != NVRTC_SUCCESS) {
     size_t ls = 0;
     nvrtcGetProgramLogSize(prog, &ls);
-    std::string log(ls, '\0');
-    if (ls) nvrtcGetProgramLog(prog, &log[0]);
+    std::string all(ls, '\0');
+    if (ls) nvrtcGetProgramLog(prog, &all[0]);
     nvrtcDestroyProgram(&prog);
+    // keep the error lines only
+    std::string log;
+    size_t at = 0;
+    while (at < all.size()) {
+      size_t nl = all.find('\n', at);
+      if (nl == std::string::npos) nl = all.size();
+      const std::string line = all.substr(at, nl - at);
+      if (line.find("error") != std::string::npos) log += line + " | ";
+      at = nl + 1;
+    }
     if (log.size() > 400) log.resize(400);
     return fail(PBAT_ECUDA, "NVRTC compile of the bit-sliced kernel failed: %s %s",
                 nvrtcGetErrorString(rc), log.c_str());
@@ -437,15 +447,53 @@ int bs_source_for(const GraphIn& g, const double* p, bool grad, const pbat_optio
   return PBAT_OK;
 }
 
+// Plans (and their compiled kernels) depend on the network's structure, the
+// options and -- for the fused kernel -- which arcs may be walk arcs; they
+// are cached so that repeated calls only rebuild the p-dependent tables.
+struct BsCached {
+  BsPlan plan;
+  JitEntry jit;
+};
+static std::mutex g_bsplan_mu;
+static std::map<std::string, BsCached> g_bsplan;
+
+static std::string bs_plan_key(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
+                               int nthr, int device) {
+  std::string k;
+  auto put = [&](long long v) { k.append((const char*)&v, sizeof v); };
+  put(device); put(g.n); put(g.m); put(g.directed); put(g.source); put(g.sink); put(grad);
+  put(o.walk_bits); put(o.prefix_bits); put(o.range_bits); put(nthr);
+  k.append((const char*)g.tail, sizeof(int32_t) * g.m);
+  k.append((const char*)g.head, sizeof(int32_t) * g.m);
+  if (grad)
+    for (int a = 0; a < g.m; ++a) k.push_back(bs_walk_ok(p, a) ? '1' : '0');
+  return k;
+}
+
 int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
                const DeviceInfo& dev, BsLaunch& bl) {
   bl.nthr = o.block_threads > 0 ? o.block_threads : 128;
-  int rc = bs_make_plan(g, o, bl.nthr, bl.plan, grad ? p : nullptr);
-  if (rc) return rc;
+  int rc;
+  const std::string key = bs_plan_key(g, p, grad, o, bl.nthr, dev.device);
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lk(g_bsplan_mu);
+    auto it = g_bsplan.find(key);
+    if (it != g_bsplan.end()) {
+      bl.plan = it->second.plan;
+      bl.jit = it->second.jit;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    if ((rc = bs_make_plan(g, o, bl.nthr, bl.plan, grad ? p : nullptr))) return rc;
+    const std::string src = bs_source(g, bl.plan, bl.nthr);
+    if ((rc = jit_compile(src, dev, grad ? "bs_kernel_grad" : "bs_kernel", &bl.jit))) return rc;
+    std::lock_guard<std::mutex> lk(g_bsplan_mu);
+    g_bsplan[key] = BsCached{bl.plan, bl.jit};
+  }
   const BsPlan& bp = bl.plan;
   const int m = g.m, top = bp.ell + bp.tb + bp.L;
-  const std::string src = bs_source(g, bp, bl.nthr);
-  if ((rc = jit_compile(src, dev, grad ? "bs_kernel_grad" : "bs_kernel", &bl.jit))) return rc;
   // parameters
   BsParamsHost& P = bl.P;
   memset(&P, 0, sizeof P);
@@ -483,13 +531,15 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
       bl.ptab.push_back(w);
     }
     if (grad)
-      for (int jj = 0; jj < bits; ++jj)
-        for (int v = 0; v < (1 << bits); ++v) {
-          dd w = dd_make(1.0);
-          for (int x = 0; x < bits; ++x)
-            if (x != jj) w = dd_mul(w, arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
-          bl.ptab_ex[((size_t)(sh + jj) << 11) + v] = w;
-        }
+      for (int v = 0; v < (1 << bits); ++v) {
+        // products of the level's factors before and after each arc
+        dd pre[12], suf[12];
+        pre[0] = dd_make(1.0);
+        for (int x = 0; x < bits; ++x) pre[x + 1] = dd_mul(pre[x], arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
+        suf[bits] = dd_make(1.0);
+        for (int x = bits - 1; x >= 0; --x) suf[x] = dd_mul(suf[x + 1], arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
+        for (int jj = 0; jj < bits; ++jj) bl.ptab_ex[((size_t)(sh + jj) << 11) + v] = dd_mul(pre[jj], suf[jj + 1]);
+      }
     sh += bits;
   }
   if (bl.ptab.empty()) bl.ptab.push_back(dd_make(1.0));
@@ -675,13 +725,30 @@ static std::vector<BsBatch*> g_bsb;
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const pbat_options& o,
+                      const DeviceInfo& dev, const std::vector<unsigned long long>& items);
+
+// Plans every network, orders them by work, and writes the module source.
+static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const pbat_options& o,
+                      std::vector<unsigned long long>& items, std::string& src_out);
+
 static int bsb_build(BsBatch& E, int G, const pbat_graph* graphs, int K, const pbat_options& o,
                      const DeviceInfo& dev) {
+  E.device = dev.device;
+  std::vector<unsigned long long> items;
+  std::string src;
+  int rc = bsb_source(E, G, graphs, K, o, items, src);
+  if (rc) return rc;
+  if ((rc = jit_compile(src, dev, "bs_batch", &E.jit))) return rc;
+  return bsb_layout(E, G, graphs, K, o, dev, items);
+}
+
+static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const pbat_options& o,
+                      std::vector<unsigned long long>& items, std::string& src_out) {
   E.G = G;
   E.K = K;
-  E.device = dev.device;
   E.plans.resize(G);
-  std::vector<unsigned long long> items(G);
+  items.assign(G, 0ull);
   for (int i = 0; i < G; ++i) {
     GraphIn g{graphs[i].n_nodes, graphs[i].n_arcs, graphs[i].tail, graphs[i].head,
               graphs[i].directed, graphs[i].source, graphs[i].sink};
@@ -748,9 +815,14 @@ static int bsb_build(BsBatch& E, int G, const pbat_graph* graphs, int K, const p
   std::string bt = kBsBatchTemplate;
   const size_t cut = bt.find("//@@BATCH_KERNEL@@");
   src += bt.substr(0, cut) + kern;
-  int rc = jit_compile(src, dev, "bs_batch", &E.jit);
-  if (rc) return rc;
-  // descriptors and table layout (launch order)
+  src_out = src;
+  return PBAT_OK;
+}
+
+// Descriptors, table layout (launch order), scratch and launch shape.
+static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const pbat_options& o,
+                      const DeviceInfo& dev, const std::vector<unsigned long long>& items) {
+  int rc;
   E.bg.resize(G);
   unsigned long long begin = 0;
   size_t lt = 0, nt = 0, wm = 0, pt = 0, th = 0;
@@ -929,6 +1001,14 @@ static double bsb_limbs_value(const unsigned long long* limbs) {
   dd s = dd{0.0, 0.0};
   for (int i = kBsbLimbs + 1; i >= 0; --i) s = dd_add(s, dd_make(ldexp((double)chunk[i], 32 * i - kBsbScale)));
   return s.hi + s.lo;
+}
+
+// Source of the batched module (diagnostic; no device needed).
+int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o, std::string& out) {
+  if (G > kBsbMaxGraphs) return fail(PBAT_ERANGE, "at most %d networks per bit-sliced batch", kBsbMaxGraphs);
+  BsBatch E;
+  std::vector<unsigned long long> items;
+  return bsb_source(E, G, graphs, K, o, items, out);
 }
 
 // R (and N_k) of a batch with the bit-sliced batched kernel; returns

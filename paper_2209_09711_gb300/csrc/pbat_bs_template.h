@@ -546,10 +546,12 @@ __device__ void bsb_limb_add(u64* limbs, double x) {
     if (M == 0) return;
   }
   const int c = e >> 5, sh = e & 31;
-  const unsigned __int128 v = (unsigned __int128)(u64)M << sh;
+  // M < 2^54 shifted left by sh < 32: three 32-bit chunks
+  const u64 lo = (u64)M << sh, hi = sh ? ((u64)M >> (64 - sh)) : 0ull;
+  const u64 chunks[3] = {lo & 0xffffffffull, lo >> 32, hi};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const u64 chunk = (u64)(u32)(v >> (32 * i));
+    const u64 chunk = chunks[i];
     if (chunk && c + i < BSB_LIMBS) atomicAdd(&limbs[c + i], neg ? (u64)(-(long long)chunk) : chunk);
   }
 }

@@ -58,6 +58,7 @@ const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl);
 void bs_describe(const BsLaunch& bl, int* out6);
 int bs_source_for(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
                   std::string& out);
+int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o, std::string& out);
 
 // ---------------------------------------------------------------------------
 // errors
@@ -874,6 +875,35 @@ int pbat_kernel_source(int n_nodes, int n_arcs, const int32_t* tail, const int32
   }
 }
 
+int pbat_batch_kernel_source(int n_graphs, const pbat_graph* graphs, int n_pvec,
+                             const pbat_options* opt, char* buf, size_t cap) {
+  try {
+    pbat::clear_error();
+    if (n_graphs < 1 || !graphs || n_pvec < 1 || n_pvec > 64)
+      return pbat::fail(PBAT_EINVAL, "bad batch");
+    for (int i = 0; i < n_graphs; ++i) {
+      pbat::GraphIn g{graphs[i].n_nodes, graphs[i].n_arcs, graphs[i].tail, graphs[i].head,
+                      graphs[i].directed, graphs[i].source, graphs[i].sink};
+      int rc = pbat::validate_graph(g);
+      if (rc) return rc;
+    }
+    pbat_options o;
+    pbat_options_init(&o);
+    if (opt) o = *opt;
+    std::string src;
+    int rc = pbat::bsb_source_for(n_graphs, graphs, n_pvec, o, src);
+    if (rc) return rc;
+    if (buf && cap) {
+      const size_t n = std::min(cap - 1, src.size());
+      memcpy(buf, src.data(), n);
+      buf[n] = '\0';
+    }
+    return (int)std::min<size_t>(src.size(), 0x7fffffff);
+  } catch (...) {
+    return pbat::fail(PBAT_ENOMEM, "host exception");
+  }
+}
+
 struct pbat_plan_s {
   pbat::Job* job;
   pbat_options opt;
@@ -918,6 +948,28 @@ int pbat_plan_read(pbat_plan plan, void* cuda_stream, double* R_out, uint64_t* N
   if (!plan || !R_out) return pbat::fail(PBAT_EINVAL, "plan and R_out must not be NULL");
   return pbat::job_read(plan->job, (cudaStream_t)cuda_stream, R_out, Nk_out,
                         plan->job->pl.grad ? dRdp_out : nullptr, &plan->opt);
+}
+
+int pbat_plan_describe(pbat_plan plan, int* out8) {
+  pbat::clear_error();
+  if (!plan || !out8) return pbat::fail(PBAT_EINVAL, "plan and out8 must not be NULL");
+  const pbat::Job* J = plan->job;
+  if (J->bs) {
+    int d6[6];
+    pbat::bs_describe(*J->bs, d6);
+    out8[0] = PBAT_ALGO_BITSLICE;
+    for (int i = 0; i < 4; ++i) out8[1 + i] = d6[i];
+  } else {
+    out8[0] = PBAT_ALGO_FRONTIER;
+    out8[1] = J->pl.ell;
+    out8[2] = 0;
+    out8[3] = J->pl.L;
+    out8[4] = J->pl.d;
+  }
+  out8[5] = J->grid_nthr;
+  out8[6] = J->grid;
+  out8[7] = J->pl.grad ? 1 : 0;
+  return PBAT_OK;
 }
 
 int pbat_plan_stats(pbat_plan plan, uint64_t* stats_out) {

@@ -118,3 +118,39 @@ def test_generated_program_workloads(pb):
         _check(pb, net, 9, trials=4)
     net = synth.workload_random_24_40()
     _check(pb, net, 3, pb.options(range_bits=6, range_lo=5, range_hi=6), trials=3)
+
+
+def _nvrtc_compile(src):
+    import ctypes.util
+    import os
+    path = None
+    for cand in ("/usr/local/cuda/lib64/libnvrtc.so", ctypes.util.find_library("nvrtc")):
+        if cand and os.path.exists(cand):
+            path = cand
+            break
+    if path is None:
+        pytest.skip("NVRTC not found")
+    import ctypes
+    lib = ctypes.CDLL(path)
+    prog = ctypes.c_void_p()
+    lib.nvrtcCreateProgram(ctypes.byref(prog), src.encode(), b"gen.cu", 0, None, None)
+    opts = (ctypes.c_char_p * 4)(b"-arch=sm_103a", b"-std=c++17", b"-lineinfo", b"-diag-suppress=177")
+    rc = lib.nvrtcCompileProgram(prog, 4, opts)
+    n = ctypes.c_size_t()
+    lib.nvrtcGetProgramLogSize(prog, ctypes.byref(n))
+    log = ctypes.create_string_buffer(max(1, n.value))
+    lib.nvrtcGetProgramLog(prog, log)
+    lib.nvrtcDestroyProgram(ctypes.byref(prog))
+    errors = [l for l in log.value.decode(errors="replace").splitlines() if "error" in l]
+    assert rc == 0, errors[:5]
+
+
+def test_generated_sources_compile_with_nvrtc(pb):
+    """Every kernel the engine generates at run time compiles for sm_103a
+    (NVRTC runs on the CPU): R only, fused, and a batched module."""
+    net = synth.workload_grid_3x6()
+    for grad in (False, True):
+        src = pb.kernel_source(net, grad=grad)
+        _nvrtc_compile(src.split("\n", 1)[1])
+    nets, _ = synth.workload_batched(6, 3)
+    _nvrtc_compile(pb.batch_kernel_source(nets, 3))
