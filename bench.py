@@ -45,13 +45,19 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "grid-3x6"
 
-# Warp instructions executed per state by the fused enumeration kernel
-# (bs_kernel_grad), from ncu (smsp__inst_executed.sum of one launch / 2^m):
-# the per-unit figure of the issue-rate roofline, keyed by workload and the
-# launch shape (walk arcs, threads per block) the capture ran with, because
-# the autotuner picks the shape per run.  DRAM traffic per launch
-# (dram__bytes_read.sum + dram__bytes_write.sum) from the same capture.
-# Source: profiles/bs_kernel_grad_grid3x6.md
+# Launch shapes (walk arcs L, threads per block) the autotuner picked for
+# these workloads on GB300; the bench pins them (unless --autotune) so that
+# the timed launch is the one the instruction counts below were taken from.
+SHAPES = {
+    "grid-3x6": {"fused": (6, 128), "r_only": (6, 128)},
+    "random-directed-n20-m34": {"fused": (8, 256), "r_only": (10, 192)},
+}
+
+# Warp instructions executed per state (smsp__inst_executed.sum of one launch
+# / 2^m, from ncu) -- the per-unit figure of the issue-rate roofline -- and
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum), keyed
+# by (kernel, workload, L, threads per block).  Source: the summaries under
+# profiles/.
 INST_PER_STATE = {}
 DRAM_BYTES_PER_LAUNCH = {}
 
@@ -249,10 +255,19 @@ def run_ours(a):
     sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit()
                            else local)
-    fused = pb.Plan(net, grad=True, stream=sp)
+    shp = {} if a.autotune else dict(SHAPES.get(a.workload, {}))
+    if a.walk_bits is not None and a.block_threads is not None:
+        shp["fused"] = (a.walk_bits, a.block_threads)
+
+    def opts_for(kind):
+        if kind not in shp:
+            return pb.options()
+        return pb.options(walk_bits=shp[kind][0], block_threads=shp[kind][1])
+
+    fused = pb.Plan(net, grad=True, opts=opts_for("fused"), stream=sp)
     ms_f, kern_f, wall_f, res_f = time_plan(fused, a.steps, a.warmup)
     clocks = sampler.stop()
-    ronly = pb.Plan(net, grad=False, stream=sp)
+    ronly = pb.Plan(net, grad=False, opts=opts_for("r_only"), stream=sp)
     ms_r, kern_r, _, res_r = time_plan(ronly, a.steps, a.warmup)
     # the plain GPU BAT: one state per thread, per-state PLSA frontier expansion
     plain = pb.Plan(net, grad=False, opts=pb.options(algo=pb.ALGO_FRONTIER), stream=sp)
@@ -291,19 +306,20 @@ def run_ours(a):
                          f"(R, N_k, T1/T0 gradient), {info['wall_s']:.1f} s wall on {cores} host "
                          f"processes, extrapolated to states/s"}
 
-    shape = fused.describe()
-    shape_key = (a.workload, shape["walk_bits"], shape["block_threads"])
-    ipc = INST_PER_STATE.get(shape_key)
     peak = SM_COUNT * ISSUE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9  # G warp-inst/s
-    if ipc is not None:
-        achieved = ipc * states / (kern_f / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": achieved / peak,
-                "traffic": DRAM_BYTES_PER_LAUNCH.get(shape_key),
-                "kernel": "bs_kernel_grad", "kernel_ms": kern_f}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": None, "traffic": None, "kernel": "bs_kernel_grad", "kernel_ms": kern_f}
+
+    def roofline(kernel, plan, kern_ms):
+        sh = plan.describe()
+        key = (kernel, a.workload, sh["walk_bits"], sh["block_threads"])
+        ipc = INST_PER_STATE.get(key)
+        achieved = ipc * states / (kern_ms / 1e3) / 1e9 if ipc is not None else None
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
+                "frac": achieved / peak if achieved is not None else None,
+                "traffic": DRAM_BYTES_PER_LAUNCH.get(key), "kernel": kernel, "kernel_ms": kern_ms,
+                "peak_source": "4 warp-inst/clk/SM x 152 SMs x 2070 MHz"}
+
+    shape = fused.describe()
+    roof = roofline("bs_kernel_grad", fused, kern_f)
     value = ws * states / (ms_f / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": ws, "steps": a.steps,
@@ -316,7 +332,8 @@ def run_ours(a):
         "roofline": roof,
         "fused_shape": shape,
         "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r,
-                   "kernel": "bs_kernel", "shape": ronly.describe()},
+                   "kernel": "bs_kernel", "shape": ronly.describe(),
+                   "roofline": roofline("bs_kernel", ronly, kern_r)},
         "plain_gpu_bat": {"value": ws * states / (ms_p / 1e3), "ms_per_step": ms_p,
                           "kernel": "frontier_kernel (one state per thread, PLSA frontier)",
                           "fused_value": ws * states / (ms_pg / 1e3), "fused_ms_per_step": ms_pg},
@@ -346,9 +363,24 @@ def run_probe(a):
     build.build()
     import paper_2209_09711_gb300 as pb
     net = WORKLOADS[a.workload]()
+    if a.probe == "batched":
+        nets, pvecs = synth.workload_batched()
+        t0 = time.perf_counter()
+        R, Nk, _ = pb.reliability_batched(nets, pvecs, opts=pb.options(algo=pb.ALGO_BITSLICE))
+        print(json.dumps({"probe": a.probe, "networks": len(nets), "p_vectors": len(pvecs[0]),
+                          "R00": R[0][0], "first_call_s": time.perf_counter() - t0}))
+        return 0
     algo = pb.ALGO_FRONTIER if a.probe.startswith("plain") else pb.ALGO_AUTO
     grad = a.probe.endswith("fused")
-    plan = pb.Plan(net, grad=grad, opts=pb.options(algo=algo))
+    kw = {}
+    kind = "fused" if grad else "r_only"
+    if algo == pb.ALGO_AUTO and not a.autotune and kind in SHAPES.get(a.workload, {}):
+        kw["walk_bits"], kw["block_threads"] = SHAPES[a.workload][kind]
+    if a.walk_bits is not None:
+        kw["walk_bits"] = a.walk_bits
+    if a.block_threads is not None:
+        kw["block_threads"] = a.block_threads
+    plan = pb.Plan(net, grad=grad, opts=pb.options(algo=algo, **kw))
     plan.execute(0)
     r = plan.read(0)
     print(json.dumps({"probe": a.probe, "workload": a.workload, "R": r.R,
@@ -369,8 +401,14 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=6.0,
                     help="target wall time of one --impl reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", choices=["fused", "r-only", "plain-r-only", "plain-fused"],
+    ap.add_argument("--probe", choices=["fused", "r-only", "plain-r-only", "plain-fused", "batched"],
                     help="run one untimed launch of that kernel (for profiler captures)")
+    ap.add_argument("--walk-bits", type=int, default=None,
+                    help="pin the walk length L (default: the tuned shape of the workload)")
+    ap.add_argument("--block-threads", type=int, default=None,
+                    help="pin the block size (default: the tuned shape of the workload)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the autotuner pick the launch shapes instead of the recorded ones")
     a = ap.parse_args()
     if a.probe:
         return run_probe(a)

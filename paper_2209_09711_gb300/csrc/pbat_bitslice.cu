@@ -693,12 +693,13 @@ struct BGraphHost {
   unsigned long long task_begin, n_tasks;
   int gidx, m, nlev, prune;
   int lev_bits[6], lev_off[6];
-  int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, pad;
+  int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, tb;
+  int L, top, pad0, pad1;
   unsigned long long binom[64];
 };
 
 constexpr int kBsbThreads = 128;
-constexpr int kBsbChunk = 16;
+constexpr int kBsbMaxWalk = 5;  // 2^L connectivity words per thread staged in shared memory
 constexpr int kBsbLimbs = 5;
 constexpr int kBsbScale = 158;
 constexpr int kBsbMaxGraphs = 256;
@@ -706,7 +707,7 @@ constexpr int kBsbMaxGraphs = 256;
 struct BsBatch {
   std::string key;
   bool busy = false;
-  int device = -1, G = 0, K = 0, grid = 0, lmax = 0;
+  int device = -1, G = 0, K = 0, Kp = 0, grid = 0, lmax = 0;
   size_t smem = 0;
   JitEntry jit;
   std::vector<BsPlan> plans;        // input order
@@ -754,7 +755,7 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
               graphs[i].directed, graphs[i].source, graphs[i].sink};
     pbat_options oo;
     pbat_options_init(&oo);
-    oo.walk_bits = o.walk_bits;
+    oo.walk_bits = std::min(o.walk_bits >= 0 ? o.walk_bits : kBsbMaxWalk, kBsbMaxWalk);
     int rc = bs_make_plan(g, oo, kBsbThreads, E.plans[i], nullptr);
     if (rc) return rc;
     items[i] = 1ull << E.plans[i].d;
@@ -765,8 +766,8 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   std::stable_sort(E.order.begin(), E.order.end(), [&](int a, int b) { return items[a] > items[b]; });
   // source: prelude, one struct per network (launch order), item template, kernel
   const std::string tmpl = kBsTemplate;
-  std::string src = "#define BSB_NTHR " + std::to_string(kBsbThreads) + "\n" +
-                    tmpl.substr(0, tmpl.find("//@@GENERATED@@"));
+  std::string src = "#define BSB_NTHR " + std::to_string(kBsbThreads) + "\n#define BSB_LMAX " +
+                    std::to_string(E.lmax) + "\n" + tmpl.substr(0, tmpl.find("//@@GENERATED@@"));
   for (int r = 0; r < G; ++r) {
     const BsPlan& bp = E.plans[E.order[r]];
     std::string gen = bp.gen;
@@ -785,15 +786,15 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
              r, m, bp.ell, bp.tb, bp.L, bp.d, bp.ncore, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, lane_mask);
     src += head + gen + "};\n";
   }
-  const int kc_max = std::min(K, kBsbChunk);
   std::string kern = "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR)\n"
-      "bs_batch(const BGraph* __restrict__ graphs, int G, int K, int k0, int kc, u64 total,\n"
+      "bs_batch(const BGraph* __restrict__ graphs, int G, int K, int Kp, u64 total,\n"
       "         const u64* __restrict__ lt, const u64* __restrict__ nt, const u64* __restrict__ wm,\n"
       "         const dd* __restrict__ pt, const u64* __restrict__ thw, u64* limbs, u64* nk,\n"
       "         u64* counter, u32* status, u64 budget_ns) {\n"
       "  extern __shared__ __align__(16) u64 s_bins[];\n"
       "  const int lane = threadIdx.x & 31;\n"
       "  u64* bins = s_bins + threadIdx.x;\n"
+      "  u32* cw = (u32*)(s_bins + (BSB_LMAX + 1) * 2 * BSB_NTHR) + threadIdx.x;\n"
       "  const u64 t0 = bs_timer();\n"
       "  for (;;) {\n"
       "    u64 task = 0;\n"
@@ -809,8 +810,8 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
       "    const u64 prefix = task - B.task_begin;\n"
       "    switch (lo) {\n";
   for (int r = 0; r < G; ++r)
-    kern += "      case " + std::to_string(r) + ": bsb_item<G" + std::to_string(r) + ", " +
-            std::to_string(kc_max) + ">(B, prefix, lane, K, k0, kc, lt, nt, wm, pt, thw, limbs, nk, bins); break;\n";
+    kern += "      case " + std::to_string(r) + ": bsb_item<G" + std::to_string(r) +
+            ">(B, prefix, lane, K, Kp, lt, nt, wm, pt, thw, limbs, nk, bins, cw); break;\n";
   kern += "    }\n    __syncwarp();\n  }\n}\n";
   std::string bt = kBsBatchTemplate;
   const size_t cut = bt.find("//@@BATCH_KERNEL@@");
@@ -824,6 +825,8 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
                       const DeviceInfo& dev, const std::vector<unsigned long long>& items) {
   int rc;
   E.bg.resize(G);
+  E.Kp = K + (K & 1);
+  const int Kp = E.Kp;
   unsigned long long begin = 0;
   size_t lt = 0, nt = 0, wm = 0, pt = 0, th = 0;
   int nk_off = 0;
@@ -853,12 +856,15 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
     }
     b.pt_size = std::max(off, 1);
     for (int j = 0; j < 64; ++j) b.binom[j] = binom_u64(bp.ell + bp.tb + bp.L, j);
-    b.lt_off = (int)lt; lt += (size_t)1024 * K;
+    b.lt_off = (int)lt; lt += (size_t)1024 * Kp;
     b.nt_off = (int)nt; nt += 1024 * 2;
-    b.wm_off = (int)wm; wm += ((size_t)1 << bp.L) * K;
+    b.wm_off = (int)wm; wm += ((size_t)1 << bp.L) * Kp;
     b.pt_off = (int)pt; pt += (size_t)b.pt_size * K;
-    b.thw_off = (int)th; th += (size_t)32 * K;
+    b.thw_off = (int)th; th += (size_t)32 * Kp;
     b.nk_off = nk_offs[i];
+    b.tb = bp.tb;
+    b.L = bp.L;
+    b.top = bp.ell + bp.tb + bp.L;
   }
   E.total = begin;
   E.n_lt = lt; E.n_nt = nt; E.n_wm = wm; E.n_pt = pt; E.n_thw = th;
@@ -877,7 +883,7 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   E.o_end = off;
   if ((rc = scratch_acquire(dev.device, E.o_end, E.o_end, &E.scr))) return rc;
   memcpy((char*)E.scr->hmem + E.o_graphs, E.bg.data(), sizeof(BGraphHost) * G);
-  E.smem = (size_t)(E.lmax + 1) * 2 * kBsbThreads * 8;
+  E.smem = (size_t)(E.lmax + 1) * 2 * kBsbThreads * 8 + ((size_t)1 << E.lmax) * kBsbThreads * 4;
   cudaError_t e = cudaFuncSetAttribute((const void*)E.jit.kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E.smem);
   if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
@@ -899,7 +905,7 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
   unsigned long long* wm = (unsigned long long*)(h + E.o_wm);
   dd* pt = (dd*)(h + E.o_pt);
   unsigned long long* th = (unsigned long long*)(h + E.o_thw);
-  const int K = E.K;
+  const int K = E.K, Kp = E.Kp;
   std::vector<size_t> poff(E.G);
   size_t acc = 0;
   for (int i = 0; i < E.G; ++i) {
@@ -923,6 +929,11 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
       nt[b.nt_off + 2 * v] = n0;
       nt[b.nt_off + 2 * v + 1] = n1;
     }
+    for (int k = K; k < Kp; ++k) {  // padding p-vector: zero mass
+      for (int v = 0; v < 1024; ++v) lt[b.lt_off + (size_t)v * Kp + k] = 0;
+      for (int gi = 0; gi < (1 << bp.L); ++gi) wm[b.wm_off + (size_t)gi * Kp + k] = 0;
+      for (int t = 0; t < 32; ++t) th[b.thw_off + (size_t)t * Kp + k] = 0;
+    }
     for (int k = 0; k < K; ++k) {
       const double* pv = p + poff[i] + (size_t)k * m;
       dd lw[32];
@@ -938,12 +949,12 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
         dd s = dd{0.0, 0.0};
         for (int x = 0; x < 8; ++x)
           if ((val >> x) & 1) s = dd_add(s, lw[8 * by + x]);
-        lt[b.lt_off + (size_t)v * K + k] = fixed_u64(s, 62);
+        lt[b.lt_off + (size_t)v * Kp + k] = fixed_u64(s, 62);
       }
       for (int gi = 0; gi < (1 << bp.L); ++gi) {
         dd w = dd_make(1.0);
         for (int a = 0; a < bp.L; ++a) w = dd_mul(w, arc_w(pv, bp.perm[bp.ell + bp.tb + a], (gi >> a) & 1));
-        wm[b.wm_off + (size_t)gi * K + k] = fixed_u64(w, 63);
+        wm[b.wm_off + (size_t)gi * Kp + k] = fixed_u64(w, 63);
       }
       for (int t = 0; t < 32; ++t) {
         unsigned long long f = 0;
@@ -952,7 +963,7 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
           for (int a = 0; a < bp.tb; ++a) w = dd_mul(w, arc_w(pv, bp.perm[bp.ell + a], (t >> a) & 1));
           f = fixed_u64(w, 63);
         }
-        th[b.thw_off + (size_t)t * K + k] = f;
+        th[b.thw_off + (size_t)t * Kp + k] = f;
       }
       dd* ptk = pt + b.pt_off + (size_t)k * b.pt_size;
       if (b.nlev == 0) ptk[0] = dd_make(1.0);
@@ -975,16 +986,12 @@ static int bsb_enqueue(BsBatch& E, cudaStream_t st, unsigned long long budget_ns
   const void* graphs = d + E.o_graphs;
   const void *lt = d + E.o_lt, *nt = d + E.o_nt, *wm = d + E.o_wm, *pt = d + E.o_pt, *thw = d + E.o_thw;
   void *limbs = d + E.o_limbs, *nk = d + E.o_nk, *counter = d + E.o_counter, *status = d + E.o_status;
-  for (int k0 = 0; k0 < E.K; k0 += kBsbChunk) {
-    if (k0 > 0 && (e = cudaMemsetAsync(counter, 0, 8, st)) != cudaSuccess)
-      return fail(PBAT_ECUDA, "memset: %s", cudaGetErrorString(e));
-    int G = E.G, K = E.K, kk0 = k0, kc = std::min(kBsbChunk, E.K - k0);
-    unsigned long long total = E.total, bud = budget_ns;
-    void* args[] = {(void*)&graphs, &G, &K, &kk0, &kc, &total, (void*)&lt, (void*)&nt, (void*)&wm,
-                    (void*)&pt, (void*)&thw, &limbs, &nk, &counter, &status, &bud};
-    e = cudaLaunchKernel((const void*)E.jit.kernel, dim3(E.grid), dim3(kBsbThreads), args, E.smem, st);
-    if (e != cudaSuccess) return fail(PBAT_ECUDA, "batched launch: %s", cudaGetErrorString(e));
-  }
+  int G = E.G, K = E.K, Kp = E.Kp;
+  unsigned long long total = E.total, bud = budget_ns;
+  void* args[] = {(void*)&graphs, &G, &K, &Kp, &total, (void*)&lt, (void*)&nt, (void*)&wm,
+                  (void*)&pt, (void*)&thw, &limbs, &nk, &counter, &status, &bud};
+  e = cudaLaunchKernel((const void*)E.jit.kernel, dim3(E.grid), dim3(kBsbThreads), args, E.smem, st);
+  if (e != cudaSuccess) return fail(PBAT_ECUDA, "batched launch: %s", cudaGetErrorString(e));
   return PBAT_OK;
 }
 

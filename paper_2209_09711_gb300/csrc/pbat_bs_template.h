@@ -523,11 +523,13 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
 static const char* kBsBatchTemplate = R"PBAT(
 #define BSB_LIMBS 5
 #define BSB_SCALE 158
+#define BSB_KC 16
 struct BGraph {
   u64 task_begin, n_tasks;
   int gidx, m, nlev, prune;
   int lev_bits[6], lev_off[6];
-  int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, pad;
+  int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, tb;
+  int L, top, pad0, pad1;
   u64 binom[64];
 };
 
@@ -568,6 +570,100 @@ __device__ __forceinline__ dd bsb_prefix_mass(const BGraph& B, const dd* __restr
   return w;
 }
 
+// An item whose every state connects s to t (monotone prune): its counts are
+// binomials and its mass, per p-vector, is the prefix mass.
+__device__ __noinline__ void bsb_full(const BGraph& B, u64 prefix, int lane, int K, const dd* __restrict__ pt,
+                                      u64* limbs, u64* nk) {
+  const int pc_pre = __popcll((long long)prefix);
+  for (int j = lane; j <= B.top; j += 32) atomicAdd(&nk[B.nk_off + pc_pre + j], B.binom[j]);
+  for (int k = lane; k < K; k += 32) {
+    const dd w = bsb_prefix_mass(B, pt, k, prefix);
+    u64* lk = limbs + ((size_t)B.gidx * K + k) * BSB_LIMBS;
+    bsb_limb_add(lk, w.hi);
+    bsb_limb_add(lk, w.lo);
+  }
+}
+
+// Everything of an item past connectivity, shared by every network: cw holds
+// this thread's 2^L connectivity words (stride BSB_NTHR), word g for walk
+// state g.  Counts N_k once, then sums the exact fixed-point mass of every
+// p-vector, BSB_KC of them at a time (Eq. 1 restricted to the item).
+__device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefix, int lane, int K, int Kp,
+                                       const u64* __restrict__ lt, const u64* __restrict__ nt,
+                                       const u64* __restrict__ wm, const dd* __restrict__ pt,
+                                       const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins) {
+  const int nw = 1 << B.L;
+  const int pc_pre = __popcll((long long)prefix);
+  for (int r = 0; r <= B.L; ++r) {
+    bins[(2 * r) * BSB_NTHR] = 0ull;
+    bins[(2 * r + 1) * BSB_NTHR] = 0ull;
+  }
+  const u64* ntg = nt + B.nt_off;
+  for (int g = 0; g < nw; ++g) {
+    const u32 c = cw[g * BSB_NTHR];
+    if (!c) continue;
+    const int pc = __popc(g);
+    const u64* n0 = ntg + (size_t)(0 * 256 + (c & 0xffu)) * 2;
+    const u64* n1 = ntg + (size_t)(1 * 256 + ((c >> 8) & 0xffu)) * 2;
+    const u64* n2 = ntg + (size_t)(2 * 256 + ((c >> 16) & 0xffu)) * 2;
+    const u64* n3 = ntg + (size_t)(3 * 256 + (c >> 24)) * 2;
+    bins[(2 * pc) * BSB_NTHR] += __ldg(n0) + __ldg(n1) + __ldg(n2) + __ldg(n3);
+    bins[(2 * pc + 1) * BSB_NTHR] += __ldg(n0 + 1) + __ldg(n1 + 1) + __ldg(n2 + 1) + __ldg(n3 + 1);
+  }
+  const bool thr_on = lane < (1 << B.tb);
+  if (thr_on) {
+    const int base = B.nk_off + pc_pre + __popc(lane);
+    for (int r = 0; r <= B.L; ++r) {
+      const u64 n0 = bins[(2 * r) * BSB_NTHR], n1 = bins[(2 * r + 1) * BSB_NTHR];
+#pragma unroll
+      for (int cl = 0; cl < 3; ++cl) {
+        const u64 c0 = (n0 >> (21 * cl)) & 0x1fffffull, c1 = (n1 >> (21 * cl)) & 0x1fffffull;
+        if (c0) atomicAdd(&nk[base + r + cl], c0);
+        if (c1) atomicAdd(&nk[base + r + 3 + cl], c1);
+      }
+    }
+  }
+  const u64* ltg = lt + B.lt_off;
+  const u64* wmg = wm + B.wm_off;
+  for (int k0 = 0; k0 < K; k0 += BSB_KC) {
+    const int kc = min(BSB_KC, K - k0);
+    u128 T[BSB_KC];
+#pragma unroll
+    for (int kk = 0; kk < BSB_KC; ++kk) T[kk] = u128{0ull, 0ull};
+    for (int g = 0; g < nw; ++g) {
+      const u32 c = cw[g * BSB_NTHR];
+      if (!c) continue;
+      // tables are padded to an even Kp, so pairs of p-vectors load as 16 bytes
+      const ulonglong2* l0 = (const ulonglong2*)(ltg + (size_t)(0 * 256 + (c & 0xffu)) * Kp + k0);
+      const ulonglong2* l1 = (const ulonglong2*)(ltg + (size_t)(1 * 256 + ((c >> 8) & 0xffu)) * Kp + k0);
+      const ulonglong2* l2 = (const ulonglong2*)(ltg + (size_t)(2 * 256 + ((c >> 16) & 0xffu)) * Kp + k0);
+      const ulonglong2* l3 = (const ulonglong2*)(ltg + (size_t)(3 * 256 + (c >> 24)) * Kp + k0);
+      const ulonglong2* wv = (const ulonglong2*)(wmg + (size_t)g * Kp + k0);
+#pragma unroll
+      for (int h = 0; h < BSB_KC / 2; ++h) {
+        if (2 * h >= kc) break;
+        const ulonglong2 a0 = __ldg(l0 + h), a1 = __ldg(l1 + h), a2 = __ldg(l2 + h), a3 = __ldg(l3 + h);
+        const ulonglong2 ww = __ldg(wv + h);
+        const u64 sx = a0.x + a1.x + a2.x + a3.x, sy = a0.y + a1.y + a2.y + a3.y;
+        u128_add(T[2 * h], sx * ww.x, __umul64hi(sx, ww.x));
+        u128_add(T[2 * h + 1], sy * ww.y, __umul64hi(sy, ww.y));
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < BSB_KC; ++kk) {
+      if (kk >= kc) break;
+      const u64 tw = thr_on ? __ldg(thw + B.thw_off + (size_t)lane * Kp + k0 + kk) : 0ull;
+      const u128 S = warp_sum_u128(mul64x128_shr64(tw, T[kk].lo, T[kk].hi));
+      if (lane == kk) {
+        const dd v = dd_mul(bsb_prefix_mass(B, pt, k0 + kk, prefix), dd_ldexp(u128_to_dd(S), -124));
+        u64* lk = limbs + ((size_t)B.gidx * K + k0 + kk) * BSB_LIMBS;
+        bsb_limb_add(lk, v.hi);
+        bsb_limb_add(lk, v.lo);
+      }
+    }
+  }
+}
+
 template <class G>
 __device__ __forceinline__ u32 bsb_uniform(const u32* a) {
   u32 e[G::NCORE > 0 ? G::NCORE : 1];
@@ -578,13 +674,13 @@ __device__ __forceinline__ u32 bsb_uniform(const u32* a) {
   return G::var(e, w);
 }
 
-template <class G, int KC>
-__device__ void bsb_item(const BGraph& B, u64 prefix, int lane, int K, int k0, int kc,
+// The per-network part of one item: its state words, the monotone prune, and
+// the connectivity word of every walk state into cw.
+template <class G>
+__device__ void bsb_item(const BGraph& B, u64 prefix, int lane, int K, int Kp,
                          const u64* __restrict__ lt, const u64* __restrict__ nt,
                          const u64* __restrict__ wm, const dd* __restrict__ pt,
-                         const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins) {
-  constexpr int IN = G::L >= 2 ? 2 : G::L;
-  constexpr int OUT = G::L - IN;
+                         const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins, u32* cw) {
   u32 a[G::M];
 #pragma unroll
   for (int i = 0; i < G::ELL; ++i)
@@ -595,102 +691,30 @@ __device__ void bsb_item(const BGraph& B, u64 prefix, int lane, int K, int k0, i
   for (int b = 0; b < G::L; ++b) a[G::WALK0 + b] = 0u;
 #pragma unroll
   for (int j = 0; j < G::D; ++j) a[G::TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
-  const int pc_pre = __popcll((long long)prefix);
-  const size_t gk0 = (size_t)B.gidx * K + k0;
   if (B.prune) {
+    // one evaluation for both extremes: bit 0 has every arc below the prefix
+    // up, the other bits have them all down (the prefix arcs are the same in
+    // every bit)
     u32 u[G::M];
 #pragma unroll
-    for (int k = 0; k < G::M; ++k) u[k] = k < G::TOP ? ~0u : a[k];
-    if (bsb_uniform<G>(u) == 0u) return;
-#pragma unroll
-    for (int k = 0; k < G::M; ++k) u[k] = k < G::TOP ? 0u : a[k];
-    if (bsb_uniform<G>(u) != 0u) {
-      if (k0 == 0)
-        for (int j = lane; j <= G::TOP; j += 32) atomicAdd(&nk[B.nk_off + pc_pre + j], B.binom[j]);
-      if (lane < kc) {
-        const dd w = bsb_prefix_mass(B, pt, k0 + lane, prefix);
-        bsb_limb_add(limbs + (gk0 + lane) * BSB_LIMBS, w.hi);
-        bsb_limb_add(limbs + (gk0 + lane) * BSB_LIMBS, w.lo);
-      }
+    for (int k = 0; k < G::M; ++k) u[k] = k < G::TOP ? 1u : a[k];
+    const u32 ext = bsb_uniform<G>(u);
+    if (!(ext & 1u)) return;
+    if (ext & 2u) {
+      bsb_full(B, prefix, lane, K, pt, limbs, nk);
       return;
     }
   }
   u32 e[G::NCORE > 0 ? G::NCORE : 1];
   G::inv(a, e);
-  const bool count = k0 == 0;
-  if (count)
-#pragma unroll
-    for (int r = 0; r < (G::L + 1) * 2; ++r) bins[r * BSB_NTHR] = 0ull;
-  u128 T[KC];
-#pragma unroll
-  for (int kk = 0; kk < KC; ++kk) T[kk] = u128{0ull, 0ull};
-  const u64* ltk = lt + B.lt_off + k0;
-  const u64* wmk = wm + B.wm_off + k0;
-  const u64* ntg = nt + B.nt_off;
-  u32 gout = 0;
-  int pco = 0;
 #pragma unroll 1
-  for (u32 s = 0; s < (1u << OUT); ++s) {
-    if (s) {
-      const int b = __ffs(s) - 1;
-      gout ^= 1u << b;
-      pco += ((gout >> b) & 1u) ? 1 : -1;
-    }
+  for (u32 g = 0; g < (1u << G::L); ++g) {
     u32 w[G::L > 0 ? G::L : 1];
 #pragma unroll
-    for (int b = 0; b < OUT; ++b) w[IN + b] = 0u - ((gout >> b) & 1u);
-#pragma unroll
-    for (int r = 0; r < (1 << IN); ++r) {
-#pragma unroll
-      for (int b = 0; b < IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
-      const u32 c = G::var(e, w) & G::LANE_MASK;
-      if (!c) continue;
-      const u32 g = (gout << IN) | (u32)r;
-      const size_t i0 = (size_t)(0 * 256 + (c & 0xffu)) * K, i1 = (size_t)(1 * 256 + ((c >> 8) & 0xffu)) * K;
-      const size_t i2 = (size_t)(2 * 256 + ((c >> 16) & 0xffu)) * K, i3 = (size_t)(3 * 256 + (c >> 24)) * K;
-#pragma unroll
-      for (int kk = 0; kk < KC; ++kk) {
-        if (kk >= kc) break;
-        const u64 sR = __ldg(ltk + i0 + kk) + __ldg(ltk + i1 + kk) + __ldg(ltk + i2 + kk) + __ldg(ltk + i3 + kk);
-        const u64 wmv = __ldg(wmk + (size_t)g * K + kk);
-        u128_add(T[kk], sR * wmv, __umul64hi(sR, wmv));
-      }
-      if (count) {
-        const int pc = pco + __popc(r);
-        const u64* n0 = ntg + (size_t)(0 * 256 + (c & 0xffu)) * 2;
-        const u64* n1 = ntg + (size_t)(1 * 256 + ((c >> 8) & 0xffu)) * 2;
-        const u64* n2 = ntg + (size_t)(2 * 256 + ((c >> 16) & 0xffu)) * 2;
-        const u64* n3 = ntg + (size_t)(3 * 256 + (c >> 24)) * 2;
-        bins[(2 * pc) * BSB_NTHR] += __ldg(n0) + __ldg(n1) + __ldg(n2) + __ldg(n3);
-        bins[(2 * pc + 1) * BSB_NTHR] += __ldg(n0 + 1) + __ldg(n1 + 1) + __ldg(n2 + 1) + __ldg(n3 + 1);
-      }
-    }
+    for (int b = 0; b < G::L; ++b) w[b] = 0u - ((g >> b) & 1u);
+    cw[g * BSB_NTHR] = G::var(e, w) & G::LANE_MASK;
   }
-  if (count && lane < (1 << G::TB)) {
-    const int base = B.nk_off + pc_pre + __popc(lane & ((1 << G::TB) - 1));
-#pragma unroll 1
-    for (int r = 0; r <= G::L; ++r) {
-      const u64 n0 = bins[(2 * r) * BSB_NTHR], n1 = bins[(2 * r + 1) * BSB_NTHR];
-#pragma unroll
-      for (int cl = 0; cl < 3; ++cl) {
-        const u64 c0 = (n0 >> (21 * cl)) & 0x1fffffull, c1 = (n1 >> (21 * cl)) & 0x1fffffull;
-        if (c0) atomicAdd(&nk[base + r + cl], c0);
-        if (c1) atomicAdd(&nk[base + r + 3 + cl], c1);
-      }
-    }
-  }
-  const bool thr_on = lane < (1 << G::TB);
-#pragma unroll
-  for (int kk = 0; kk < KC; ++kk) {
-    if (kk >= kc) break;
-    const u64 tw = thr_on ? __ldg(thw + B.thw_off + (size_t)lane * K + k0 + kk) : 0ull;
-    const u128 S = warp_sum_u128(mul64x128_shr64(tw, T[kk].lo, T[kk].hi));
-    if (lane == kk) {
-      const dd v = dd_mul(bsb_prefix_mass(B, pt, k0 + kk, prefix), dd_ldexp(u128_to_dd(S), -124));
-      bsb_limb_add(limbs + (gk0 + kk) * BSB_LIMBS, v.hi);
-      bsb_limb_add(limbs + (gk0 + kk) * BSB_LIMBS, v.lo);
-    }
-  }
+  bsb_accum(B, cw, prefix, lane, K, Kp, lt, nt, wm, pt, thw, limbs, nk, bins);
 }
 //@@BATCH_KERNEL@@
 )PBAT";

@@ -224,6 +224,26 @@ def test_batched_against_oracle(pb):
                     ref.grad_t1t0[i], ref.T1[i], ref.T0[i], ref.R)
 
 
+def test_batched_bitsliced_against_oracle_odd_many_pvectors(pb):
+    """The bit-sliced batched module against the oracle: 19 p-vectors (one
+    full register chunk of 16 plus a ragged 3, and an odd count that leaves a
+    zero padding column in the tables), networks from 12 to 18 arcs so that
+    items have walk arcs and prefix arcs, with and without the prune."""
+    nets, pvecs = [], []
+    for i in range(5):
+        rng = synth.SplitMix64(71 + i)
+        m = 12 + rng.below(7)
+        nets.append(synth.random_small(950 + i, n=5 + rng.below(5), m=m, directed=bool(i & 1)))
+        pvecs.append([synth.uniform_p(rng, m, 0.05, 0.95) for _ in range(19)])
+    refs = [[oracle.enumerate_states(net, p=pvecs[g][k]) for k in range(19)] for g, net in enumerate(nets)]
+    for prune in (1, 0):
+        R, Nk, _ = pb.reliability_batched(nets, pvecs, opts=pb.options(algo=pb.ALGO_BITSLICE, prune=prune))
+        for g in range(len(nets)):
+            assert Nk[g] == refs[g][0].Nk
+            for k in range(19):
+                assert abs(R[g][k] - refs[g][k].R) <= R_TOL * refs[g][k].R + 1e-300
+
+
 def test_batched_frontier_kernel_matches_bitsliced(pb):
     nets, pvecs = synth.workload_batched(12, 5)
     R1, N1, _ = pb.reliability_batched(nets, pvecs, opts=pb.options(algo=pb.ALGO_FRONTIER))
