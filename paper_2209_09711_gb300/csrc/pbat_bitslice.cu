@@ -395,9 +395,9 @@ struct BsLaunch {
   BsGradParamsHost Q;
   std::vector<unsigned long long> thr_tab;   // [4][256] (fused kernel)
   std::vector<unsigned long long> wmid128;   // [2^L][2] (fused kernel)
-  std::vector<dd> ptab;                      // prefix masses per level
-  std::vector<dd> ptab_ex;                   // [prefix arc][2^11]: its level without it
-  std::vector<unsigned long long> lane_tab;  // [4][256][3]
+  std::vector<MxHost> ptab;                  // prefix masses per level
+  std::vector<MxHost> ptab_ex;               // [prefix arc][2^11]: its level without it
+  std::vector<unsigned long long> lane_tab;  // [4][256][2]: lane mass, packed class counts
   std::vector<unsigned long long> wmid;      // [2^L]
   JitEntry jit;
   int nthr = 128;
@@ -520,7 +520,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   // entry is the exact double-double product over one level's arcs
   P.nlev = (bp.d + 10) / 11;
   bl.ptab.clear();
-  bl.ptab_ex.assign(grad ? (size_t)bp.d << 11 : 0, dd{0.0, 0.0});
+  bl.ptab_ex.assign(grad ? (size_t)bp.d << 11 : 0, MxHost{0, 0, 0});
   for (int l = 0, sh = 0; l < P.nlev; ++l) {
     const int bits = bp.d / P.nlev + (l < bp.d % P.nlev ? 1 : 0);
     P.lev_bits[l] = bits;
@@ -528,7 +528,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     for (int v = 0; v < (1 << bits); ++v) {
       dd w = dd_make(1.0);
       for (int x = 0; x < bits; ++x) w = dd_mul(w, arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
-      bl.ptab.push_back(w);
+      bl.ptab.push_back(to_mx(w));
     }
     if (grad)
       for (int v = 0; v < (1 << bits); ++v) {
@@ -538,14 +538,16 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
         for (int x = 0; x < bits; ++x) pre[x + 1] = dd_mul(pre[x], arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
         suf[bits] = dd_make(1.0);
         for (int x = bits - 1; x >= 0; --x) suf[x] = dd_mul(suf[x + 1], arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
-        for (int jj = 0; jj < bits; ++jj) bl.ptab_ex[((size_t)(sh + jj) << 11) + v] = dd_mul(pre[jj], suf[jj + 1]);
+        for (int jj = 0; jj < bits; ++jj) bl.ptab_ex[((size_t)(sh + jj) << 11) + v] = to_mx(dd_mul(pre[jj], suf[jj + 1]));
       }
     sh += bits;
   }
-  if (bl.ptab.empty()) bl.ptab.push_back(dd_make(1.0));
-  // lane tables: byte position b, value v -> lane mass (scale 2^62) and
-  // packed counts by lane popcount class (21-bit fields; classes 0-2, 3-5)
-  bl.lane_tab.assign(4 * 256 * 3, 0ull);
+  if (bl.ptab.empty()) bl.ptab.push_back(to_mx(dd_make(1.0)));
+  // lane tables: byte position b, value v -> lane mass (scale 2^62) and the
+  // counts of its set lanes by lane popcount class, packed in fields of
+  // 8, 11, 12, 12, 11, 8 bits
+  static const int kNkShift[6] = {0, 8, 19, 31, 43, 54};
+  bl.lane_tab.assign(4 * 256 * 2, 0ull);
   dd lw[32];
   for (int j = 0; j < 32; ++j) {
     lw[j] = dd{0.0, 0.0};
@@ -557,22 +559,17 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   for (int b = 0; b < 4; ++b)
     for (int v = 0; v < 256; ++v) {
       dd s = dd{0.0, 0.0};
-      unsigned long long n0 = 0, n1 = 0;
+      unsigned long long n = 0;
       for (int k = 0; k < 8; ++k) {
         if (!((v >> k) & 1)) continue;
         const int j = 8 * b + k;
         if (j >= (1 << bp.ell)) continue;
         s = dd_add(s, lw[j]);
-        const int cl = __builtin_popcount((unsigned)j);
-        if (cl < 3)
-          n0 += 1ull << (21 * cl);
-        else
-          n1 += 1ull << (21 * (cl - 3));
+        n += 1ull << kNkShift[__builtin_popcount((unsigned)j)];
       }
-      unsigned long long* e = &bl.lane_tab[(b * 256 + v) * 3];
+      unsigned long long* e = &bl.lane_tab[(b * 256 + v) * 2];
       e[0] = fixed_u64(s, 62);
-      e[1] = n0;
-      e[2] = n1;
+      e[1] = n;
     }
   const int L_in = std::min(bp.L, 2), L_out = bp.L - L_in;
   if (!grad) {
@@ -582,7 +579,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
       for (int b = 0; b < bp.L; ++b) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + bp.tb + b], (gi >> b) & 1));
       bl.wmid[gi] = fixed_u64(w, 63);
     }
-    bl.smem = (size_t)(4 * 256 * 3 + (1 << bp.L) + (bp.L + 1) * 2 * bl.nthr) * 8 +
+    bl.smem = (size_t)(4 * 256 * 2 + (1 << bp.L) + (bp.L + 1) * bl.nthr) * 8 +
               (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
   } else {
     // fused kernel: thread-pattern masses, 128-bit walk masses, fixed-point
@@ -624,8 +621,9 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
       bl.Q.inv_p[k] = dd_recip(pk);
       bl.Q.inv_q[k] = dd_recip_dd(dd_one_minus(pk));
     }
-    bl.smem = (size_t)(4 * 256 * 3 + 4 * 256 + 2 * (1 << bp.L) + (bp.L + 1) * 2 * bl.nthr) * 8 +
+    bl.smem = (size_t)(4 * 256 * 2 + 2 * (1 << bp.L) + 4 * 256 + (bp.L + 1) * bl.nthr) * 8 +
               (size_t)std::max(L_out, 1) * bl.nthr * 16 + (size_t)(bl.nthr / 32) * 64 * 16 +
+              (size_t)(bl.nthr / 32) * (1 + 2 * m) * 16 +
               (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
   }
   if (bl.smem > (size_t)dev.smem_optin)
@@ -647,7 +645,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
 // Launch with the device copies of the tables (see bs_tables for the order).
 cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsigned long long* d_lane,
                       const unsigned long long* d_thr, const unsigned long long* d_wmid,
-                      const dd* d_ptab, const dd* d_ptab_ex, const DevWork& W) {
+                      const void* d_ptab, const void* d_ptab_ex, const DevWork& W) {
   const BsParamsHost& P = bl.P;
   if (bl.plan.grad) {
     const BsGradParamsHost& Q = bl.Q;
@@ -672,8 +670,8 @@ const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl) {
   return bl.plan.grad ? bl.wmid128 : bl.wmid;
 }
 const std::vector<unsigned long long>& bs_thr_tab(const BsLaunch& bl) { return bl.thr_tab; }
-const std::vector<dd>& bs_ptab(const BsLaunch& bl) { return bl.ptab; }
-const std::vector<dd>& bs_ptab_ex(const BsLaunch& bl) { return bl.ptab_ex; }
+const std::vector<MxHost>& bs_ptab(const BsLaunch& bl) { return bl.ptab; }
+const std::vector<MxHost>& bs_ptab_ex(const BsLaunch& bl) { return bl.ptab_ex; }
 bool bs_grad(const BsLaunch& bl) { return bl.plan.grad; }
 BsLaunch* bs_new() { return new BsLaunch(); }
 void bs_delete(BsLaunch* b) { delete b; }
@@ -700,8 +698,8 @@ struct BGraphHost {
 
 constexpr int kBsbThreads = 128;
 constexpr int kBsbMaxWalk = 5;  // 2^L connectivity words per thread staged in shared memory
-constexpr int kBsbLimbs = 5;
-constexpr int kBsbScale = 158;
+constexpr int kBsbLimbs = 4;    // 32-bit chunks of a value at scale 2^123, in 64-bit atomics
+constexpr int kBsbScale = 123;
 constexpr int kBsbMaxGraphs = 256;
 
 struct BsBatch {
@@ -786,15 +784,15 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
              r, m, bp.ell, bp.tb, bp.L, bp.d, bp.ncore, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, lane_mask);
     src += head + gen + "};\n";
   }
-  std::string kern = "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR)\n"
+  std::string kern = "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR, 4)\n"
       "bs_batch(const BGraph* __restrict__ graphs, int G, int K, int Kp, u64 total,\n"
       "         const u64* __restrict__ lt, const u64* __restrict__ nt, const u64* __restrict__ wm,\n"
-      "         const dd* __restrict__ pt, const u64* __restrict__ thw, u64* limbs, u64* nk,\n"
+      "         const mx* __restrict__ pt, const u64* __restrict__ thw, u64* limbs, u64* nk,\n"
       "         u64* counter, u32* status, u64 budget_ns) {\n"
       "  extern __shared__ __align__(16) u64 s_bins[];\n"
       "  const int lane = threadIdx.x & 31;\n"
       "  u64* bins = s_bins + threadIdx.x;\n"
-      "  u32* cw = (u32*)(s_bins + (BSB_LMAX + 1) * 2 * BSB_NTHR) + threadIdx.x;\n"
+      "  u32* cw = (u32*)(s_bins + (BSB_LMAX + 1) * BSB_NTHR) + threadIdx.x;\n"
       "  const u64 t0 = bs_timer();\n"
       "  for (;;) {\n"
       "    u64 task = 0;\n"
@@ -857,7 +855,7 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
     b.pt_size = std::max(off, 1);
     for (int j = 0; j < 64; ++j) b.binom[j] = binom_u64(bp.ell + bp.tb + bp.L, j);
     b.lt_off = (int)lt; lt += (size_t)1024 * Kp;
-    b.nt_off = (int)nt; nt += 1024 * 2;
+    b.nt_off = (int)nt; nt += 1024;
     b.wm_off = (int)wm; wm += ((size_t)1 << bp.L) * Kp;
     b.pt_off = (int)pt; pt += (size_t)b.pt_size * K;
     b.thw_off = (int)th; th += (size_t)32 * Kp;
@@ -873,7 +871,7 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   E.o_lt = off; off = a256(off + 8 * lt);
   E.o_nt = off; off = a256(off + 8 * nt);
   E.o_wm = off; off = a256(off + 8 * wm);
-  E.o_pt = off; off = a256(off + sizeof(dd) * pt);
+  E.o_pt = off; off = a256(off + sizeof(MxHost) * pt);
   E.o_thw = off; off = a256(off + 8 * th);
   E.o_upload_end = off;
   E.o_limbs = off; off = a256(off + 8 * (size_t)kBsbLimbs * G * K);
@@ -883,7 +881,7 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   E.o_end = off;
   if ((rc = scratch_acquire(dev.device, E.o_end, E.o_end, &E.scr))) return rc;
   memcpy((char*)E.scr->hmem + E.o_graphs, E.bg.data(), sizeof(BGraphHost) * G);
-  E.smem = (size_t)(E.lmax + 1) * 2 * kBsbThreads * 8 + ((size_t)1 << E.lmax) * kBsbThreads * 4;
+  E.smem = (size_t)(E.lmax + 1) * kBsbThreads * 8 + ((size_t)1 << E.lmax) * kBsbThreads * 4;
   cudaError_t e = cudaFuncSetAttribute((const void*)E.jit.kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E.smem);
   if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
@@ -903,7 +901,7 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
   unsigned long long* lt = (unsigned long long*)(h + E.o_lt);
   unsigned long long* nt = (unsigned long long*)(h + E.o_nt);
   unsigned long long* wm = (unsigned long long*)(h + E.o_wm);
-  dd* pt = (dd*)(h + E.o_pt);
+  MxHost* pt = (MxHost*)(h + E.o_pt);
   unsigned long long* th = (unsigned long long*)(h + E.o_thw);
   const int K = E.K, Kp = E.Kp;
   std::vector<size_t> poff(E.G);
@@ -917,17 +915,16 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
     const int i = b.gidx, m = b.m;
     const BsPlan& bp = E.plans[i];
     const int top = bp.ell + bp.tb + bp.L;
+    static const int kNkShift[6] = {0, 8, 19, 31, 43, 54};
     for (int v = 0; v < 1024; ++v) {  // packed N counts by lane class (same for every p-vector)
       const int by = v >> 8, val = v & 255;
-      unsigned long long n0 = 0, n1 = 0;
+      unsigned long long n = 0;
       for (int k = 0; k < 8; ++k) {
         const int j = 8 * by + k;
         if (!((val >> k) & 1) || j >= (1 << bp.ell)) continue;
-        const int cl = __builtin_popcount((unsigned)j);
-        if (cl < 3) n0 += 1ull << (21 * cl); else n1 += 1ull << (21 * (cl - 3));
+        n += 1ull << kNkShift[__builtin_popcount((unsigned)j)];
       }
-      nt[b.nt_off + 2 * v] = n0;
-      nt[b.nt_off + 2 * v + 1] = n1;
+      nt[b.nt_off + v] = n;
     }
     for (int k = K; k < Kp; ++k) {  // padding p-vector: zero mass
       for (int v = 0; v < 1024; ++v) lt[b.lt_off + (size_t)v * Kp + k] = 0;
@@ -965,13 +962,13 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
         }
         th[b.thw_off + (size_t)t * Kp + k] = f;
       }
-      dd* ptk = pt + b.pt_off + (size_t)k * b.pt_size;
-      if (b.nlev == 0) ptk[0] = dd_make(1.0);
+      MxHost* ptk = pt + b.pt_off + (size_t)k * b.pt_size;
+      if (b.nlev == 0) ptk[0] = to_mx(dd_make(1.0));
       for (int l = 0, sh = 0; l < b.nlev; ++l) {
         for (int v = 0; v < (1 << b.lev_bits[l]); ++v) {
           dd w = dd_make(1.0);
           for (int x = 0; x < b.lev_bits[l]; ++x) w = dd_mul(w, arc_w(pv, bp.perm[top + sh + x], (v >> x) & 1));
-          ptk[b.lev_off[l] + v] = w;
+          ptk[b.lev_off[l] + v] = to_mx(w);
         }
         sh += b.lev_bits[l];
       }

@@ -16,9 +16,12 @@
 // Per word the connectivity of its 32 states is c = bs_var(inv, walk words):
 // bit j set iff the sink is reachable from the source in state j (the PLSA
 // answer of Sec. 3.2).  R (Eq. 1) accumulates exactly: the lane mass of the
-// connected bits comes from four byte tables (u64, scale 2^62), times the
-// walk mass of g, into a 128-bit integer T per thread (scale 2^125); the
-// thread-arc and prefix masses are applied once per item.
+// connected bits comes from four byte tables (u64, scale 2^62, each entry
+// paired with the bit counts of its lane-popcount classes so that one 16-byte
+// load serves R and N_k), times the walk mass of g, into a 128-bit integer T
+// per thread (scale 2^125); the thread-arc and prefix masses are applied once
+// per item, in integer arithmetic (the FP64 rate of this part is 1/64 of its
+// FP32 rate, so no per-item work uses FP64).
 #pragma once
 
 namespace pbat {
@@ -90,6 +93,36 @@ __device__ __forceinline__ u128 warp_sum_u128(u128 v) {
   return v;
 }
 
+__device__ __forceinline__ u128 u128_shr(u128 v, int s) {
+  if (s <= 0) return v;
+  if (s >= 128) return u128{0ull, 0ull};
+  if (s >= 64) return u128{v.hi >> (s - 64), 0ull};
+  return u128{(v.lo >> s) | (v.hi << (64 - s)), v.hi >> s};
+}
+// exact 128-bit value as double-double times 2^-e
+__device__ __forceinline__ dd u128_dd_scaled(u128 v, int e) { return dd_ldexp(u128_to_dd(v), -e); }
+
+// Products of arc reliabilities (the prefix masses) as integer floating
+// point: value m * 2^(-63 - e), m in [2^63, 2^64) or m = 0, e >= 0.  A
+// product keeps 63 significant bits.
+struct mx { u64 m; int e; int pad; };
+__device__ __forceinline__ mx mx_mul(mx a, mx b) {
+  u64 h = __umul64hi(a.m, b.m);
+  int e = a.e + b.e - 1;
+  if (!(h >> 63)) { h <<= 1; ++e; }
+  return mx{h, e, 0};
+}
+// x times a 128-bit value at scale 2^124, at scale 2^123 (truncated)
+__device__ __forceinline__ u128 mx_apply(mx x, u128 v) {
+  return u128_shr(mul64x128_shr64(x.m, v.lo, v.hi), x.e);
+}
+
+// N_k counts of one word, packed by lane-popcount class cl = 0..5 into
+// fields of 8, 11, 12, 12, 11 and 8 bits: wide enough for one item's sum
+// over 2^L words with L <= 10 (at most C(10,5) * C(5,cl) per field).
+#define BS_NK_SHIFTS {0, 8, 19, 31, 43, 54}
+#define BS_NK_WIDTHS {8, 11, 12, 12, 11, 8}
+
 struct BsParams {
   u64 task_lo, n_tasks, budget_ns;
   int prune, nlev;       // prefix-mass table levels
@@ -108,12 +141,13 @@ __device__ __forceinline__ u64 bs_timer() {
 }
 
 // Mass of the prefix arcs of `prefix`: product over table levels.
-__device__ __forceinline__ dd bs_prefix_mass(const BsParams& P, const dd* __restrict__ ptab, u64 prefix) {
-  dd w = dd{1.0, 0.0};
+__device__ __forceinline__ mx bs_prefix_mass(const BsParams& P, const mx* __restrict__ ptab, u64 prefix) {
+  mx w = mx{1ull << 63, 0, 0};
   int sh = 0;
   for (int l = 0; l < P.nlev; ++l) {
     const u64 v = (prefix >> sh) & ((1ull << P.lev_bits[l]) - 1ull);
-    w = l ? dd_mul(w, ptab[P.lev_off[l] + v]) : ptab[P.lev_off[l] + v];
+    const mx t = ptab[P.lev_off[l] + v];
+    w = l ? mx_mul(w, t) : t;
     sh += P.lev_bits[l];
   }
   return w;
@@ -151,14 +185,14 @@ __device__ __forceinline__ int bs_prune(const u32* a) {
 }
 
 __device__ __forceinline__ void bs_flush_bins(u64* bins, u64* s_nbins, int base) {
+  constexpr int sh[6] = BS_NK_SHIFTS, wd[6] = BS_NK_WIDTHS;
 #pragma unroll 1
   for (int r = 0; r <= BS_L; ++r) {
-    const u64 n0 = bins[(2 * r) * BS_NTHR], n1 = bins[(2 * r + 1) * BS_NTHR];
+    const u64 n = bins[r * BS_NTHR];
 #pragma unroll
-    for (int cl = 0; cl < 3; ++cl) {
-      const u64 c0 = (n0 >> (21 * cl)) & 0x1fffffull, c1 = (n1 >> (21 * cl)) & 0x1fffffull;
-      if (c0) atomicAdd(&s_nbins[base + r + cl], c0);
-      if (c1) atomicAdd(&s_nbins[base + r + 3 + cl], c1);
+    for (int cl = 0; cl < 6; ++cl) {
+      const u64 c = (n >> sh[cl]) & ((1ull << wd[cl]) - 1ull);
+      if (c) atomicAdd(&s_nbins[base + r + cl], c);
     }
   }
 }
@@ -178,15 +212,15 @@ __device__ __forceinline__ void bs_write_partials(const BsWork& W, const dd* s_w
 // ---------------------------------------------------------------------------
 extern "C" __global__ void __launch_bounds__(BS_NTHR)
 bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
-          const u64* __restrict__ wmid_tab, const dd* __restrict__ ptab, BsWork W) {
+          const u64* __restrict__ wmid_tab, const mx* __restrict__ ptab, BsWork W) {
   extern __shared__ __align__(16) unsigned char smem[];
-  u64* s_lt = (u64*)smem;                                   // [4][256][3]
-  u64* s_wmid = s_lt + 4 * 256 * 3;                         // [2^L], scale 2^63
-  u64* s_bins = s_wmid + (1 << BS_L);                       // [(L + 1) * 2][NTHR]
-  dd* s_wacc = (dd*)(s_bins + (BS_L + 1) * 2 * BS_NTHR);    // [warps][1 + M]
+  ulonglong2* s_lt = (ulonglong2*)smem;                     // [4][256] {lane mass 2^62, packed counts}
+  u64* s_wmid = (u64*)(s_lt + 4 * 256);                     // [2^L], scale 2^63
+  u64* s_bins = s_wmid + (1 << BS_L);                       // [L + 1][NTHR]
+  dd* s_wacc = (dd*)(s_bins + (BS_L + 1) * BS_NTHR);        // [warps][1 + M]
   u64* s_nbins = (u64*)(s_wacc + (BS_NTHR / 32) * (1 + BS_M));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < 4 * 256 * 3; i += BS_NTHR) s_lt[i] = lane_tab[i];
+  for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
   for (int i = tid; i < (1 << BS_L); i += BS_NTHR) s_wmid[i] = wmid_tab[i];
   for (int i = tid; i < (BS_NTHR / 32) * (1 + BS_M); i += BS_NTHR) s_wacc[i] = dd{0.0, 0.0};
   for (int i = tid; i <= BS_M; i += BS_NTHR) s_nbins[i] = 0ull;
@@ -198,6 +232,7 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
   const u64 thw = thr_on ? P.thw[lane] : 0ull;
   const u64 t_start = bs_timer();
   u64 n_walk = 0, n_full = 0, n_dead = 0;
+  u128 accR = u128{0ull, 0ull};   // this warp's R, scale 2^123 (the same in every lane)
   u32 a[BS_M];
   bs_init_arcs(a, lane);
 
@@ -219,7 +254,8 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
       if (pr == 2) {
         ++n_full;
         for (int j = lane; j <= BS_TOP; j += 32) atomicAdd(&s_nbins[pc_pre + j], P.binom[j]);
-        if (lane == 0) wacc[0] = dd_add(wacc[0], bs_prefix_mass(P, ptab, prefix));
+        const u128 c = mx_apply(bs_prefix_mass(P, ptab, prefix), u128{0ull, 1ull << 60});
+        u128_add(accR, c.lo, c.hi);
         continue;
       }
     }
@@ -227,7 +263,7 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
     u32 e[BS_NCORE > 0 ? BS_NCORE : 1];
     bs_inv(a, e);
 #pragma unroll
-    for (int r = 0; r < (BS_L + 1) * 2; ++r) bins[r * BS_NTHR] = 0ull;
+    for (int r = 0; r <= BS_L; ++r) bins[r * BS_NTHR] = 0ull;
     u128 T = u128{0ull, 0ull};
     u32 gout = 0;
     int pco = 0;
@@ -249,26 +285,25 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
         if (c) {
           const u32 g = (gout << BS_IN) | (u32)r;
           const int pc = pco + __popc(r);
-          const u64* t0 = s_lt + (0 * 256 + (c & 0xffu)) * 3;
-          const u64* t1 = s_lt + (1 * 256 + ((c >> 8) & 0xffu)) * 3;
-          const u64* t2 = s_lt + (2 * 256 + ((c >> 16) & 0xffu)) * 3;
-          const u64* t3 = s_lt + (3 * 256 + (c >> 24)) * 3;
-          const u64 sR = t0[0] + t1[0] + t2[0] + t3[0];
+          const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
+          const ulonglong2 t2 = s_lt[2 * 256 + ((c >> 16) & 0xffu)], t3 = s_lt[3 * 256 + (c >> 24)];
+          const u64 sR = t0.x + t1.x + t2.x + t3.x;
           const u64 wm = s_wmid[g];
           u128_add(T, sR * wm, __umul64hi(sR, wm));
-          bins[(2 * pc) * BS_NTHR] += t0[1] + t1[1] + t2[1] + t3[1];
-          bins[(2 * pc + 1) * BS_NTHR] += t0[2] + t1[2] + t2[2] + t3[2];
+          bins[pc * BS_NTHR] += t0.y + t1.y + t2.y + t3.y;
         }
       }
     }
     if (thr_on) bs_flush_bins(bins, s_nbins, pc_pre + pc_thr);
-    // item total: exact warp sum of T x thread mass (scale 2^124), once per item
+    // item total: exact warp sum of T x thread mass (scale 2^124), times the
+    // prefix mass, once per item
     const u128 S = warp_sum_u128(mul64x128_shr64(thw, T.lo, T.hi));
-    if (lane == 0)
-      wacc[0] = dd_add(wacc[0], dd_mul(bs_prefix_mass(P, ptab, prefix), dd_ldexp(u128_to_dd(S), -124)));
+    const u128 c = mx_apply(bs_prefix_mass(P, ptab, prefix), S);
+    u128_add(accR, c.lo, c.hi);
   }
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
+    wacc[0] = u128_dd_scaled(accR, 123);
   }
   __syncthreads();
   bs_write_partials(W, s_wacc, s_nbins);
@@ -285,64 +320,87 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
 //     j; its total T2 (thread-pattern masses from byte tables) pairs lanes j
 //     and j ^ 2^i in the same way;
 //   walk arcs: A_b, the part of T collected while walk arc b works, against
-//     T - A_b, divided by p_b and 1 - p_b in double-double (exact to 2^-100,
-//     because both come from the same integers);
-//   prefix arcs: item totals times the prefix mass without that arc, signed.
+//     T - A_b; both are summed over items and divided by p_b and 1 - p_b once,
+//     at the end;
+//   prefix arcs: item totals times the prefix mass without that arc, summed
+//     apart for the arc working and failed.
 // Per item every quantity is first summed exactly over the warp in 128-bit
 // integers with fixed-point per-lane weights; then the lane that owns an arc
-// (lanes k and k - 32 own internal arc k) does that arc's double-double
-// arithmetic, so the per-item floating-point work runs once per warp, in
-// parallel over arcs.  Walk masses are 128-bit (scale 2^127).
+// (lanes k and k - 32 own internal arc k) scales it by the item's prefix
+// mass (integer floating point) and adds it to that arc's two 128-bit
+// accumulators (scale 2^123) in shared memory.  Walk masses are 128-bit
+// (scale 2^127).
 struct BsGradParams {
   u64 thw_ex[5][32];    // thread-pattern masses without thread arc i (2^63)
   u64 lw_ex[5][32];     // lane-pattern masses without lane arc i (2^63)
   dd inv_p[64], inv_q[64];
 };
 
-__device__ __forceinline__ u32 bs_transpose32(u32 x, int lane) {
-#pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    const int sh = 16 >> r;
-    const u32 mk = r == 0 ? 0x0000FFFFu : r == 1 ? 0x00FF00FFu : r == 2 ? 0x0F0F0F0Fu : r == 3 ? 0x33333333u : 0x55555555u;
-    const u32 y = __shfl_xor_sync(0xffffffffu, x, sh);
-    x = (lane & sh) ? ((x & ~mk) | ((y & ~mk) >> sh)) : ((x & mk) | ((y & mk) << sh));
-  }
+// Per-lane constants of the 32x32 bit transpose below: byte selectors of the
+// 16- and 8-bit rounds, rotate amounts and keep-masks of the 4-, 2- and
+// 1-bit rounds.
+struct BsTr { u32 sel16, sel8, rot4, rot2, rot1, keep4, keep2, keep1; };
+__device__ __forceinline__ BsTr bs_tr_init(int lane) {
+  BsTr t;
+  t.sel16 = (lane & 16) ? 0x3276u : 0x5410u;
+  t.sel8 = (lane & 8) ? 0x3715u : 0x6240u;
+  t.rot4 = (lane & 4) ? 28u : 4u;
+  t.rot2 = (lane & 2) ? 30u : 2u;
+  t.rot1 = (lane & 1) ? 31u : 1u;
+  t.keep4 = (lane & 4) ? 0xF0F0F0F0u : 0x0F0F0F0Fu;
+  t.keep2 = (lane & 2) ? 0xCCCCCCCCu : 0x33333333u;
+  t.keep1 = (lane & 1) ? 0xAAAAAAAAu : 0x55555555u;
+  return t;
+}
+// Round with distance sh: lanes with bit sh clear keep the low half of
+// every 2sh-bit group and take the partner's low halves into their high
+// halves; lanes with the bit set keep the high halves and take the
+// partner's high halves into their low halves.  Byte-sized rounds are one
+// byte permute; smaller ones a rotate and a bit select.
+__device__ __forceinline__ u32 bs_transpose32(u32 x, const BsTr& t) {
+  u32 y = __shfl_xor_sync(0xffffffffu, x, 16);
+  x = __byte_perm(x, y, t.sel16);
+  y = __shfl_xor_sync(0xffffffffu, x, 8);
+  x = __byte_perm(x, y, t.sel8);
+  y = __shfl_xor_sync(0xffffffffu, x, 4);
+  x = (x & t.keep4) | (__funnelshift_l(y, y, t.rot4) & ~t.keep4);
+  y = __shfl_xor_sync(0xffffffffu, x, 2);
+  x = (x & t.keep2) | (__funnelshift_l(y, y, t.rot2) & ~t.keep2);
+  y = __shfl_xor_sync(0xffffffffu, x, 1);
+  x = (x & t.keep1) | (__funnelshift_l(y, y, t.rot1) & ~t.keep1);
   return x;
 }
-
-// exact 128-bit value as double-double times 2^-124
-__device__ __forceinline__ dd fx124(u128 v) { return dd_ldexp(u128_to_dd(v), -124); }
 
 extern "C" __global__ void __launch_bounds__(BS_NTHR)
 bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGradParams Q,
                const u64* __restrict__ lane_tab, const u64* __restrict__ thr_tab,
-               const u64* __restrict__ wmid128, const dd* __restrict__ ptab,
-               const dd* __restrict__ ptab_ex, BsWork W) {
+               const u64* __restrict__ wmid128, const mx* __restrict__ ptab,
+               const mx* __restrict__ ptab_ex, BsWork W) {
   extern __shared__ __align__(16) unsigned char smem[];
-  u64* s_lt = (u64*)smem;                                   // [4][256][3]
-  u64* s_tt = s_lt + 4 * 256 * 3;                           // [4][256] thread-pattern masses (2^62)
-  u64* s_wm = s_tt + 4 * 256;                               // [2^L][2] walk masses (2^127)
-  u64* s_bins = s_wm + 2 * (1 << BS_L);                     // [(L + 1) * 2][NTHR]
-  u128* s_A = (u128*)(s_bins + (BS_L + 1) * 2 * BS_NTHR);   // [BS_OUT][NTHR]
+  ulonglong2* s_lt = (ulonglong2*)smem;                     // [4][256] {lane mass 2^62, packed counts}
+  ulonglong2* s_wm = s_lt + 4 * 256;                        // [2^L] walk masses {lo, hi} (2^127)
+  u64* s_tt = (u64*)(s_wm + (1 << BS_L));                   // [4][256] thread-pattern masses (2^62)
+  u64* s_bins = s_tt + 4 * 256;                             // [L + 1][NTHR]
+  u128* s_A = (u128*)(s_bins + (BS_L + 1) * BS_NTHR);       // [BS_OUT][NTHR]
   u128* s_red = s_A + (BS_OUT > 0 ? BS_OUT : 1) * BS_NTHR;  // [warps][64] reduced values
-  dd* s_wacc = (dd*)(s_red + (BS_NTHR / 32) * 64);          // [warps][1 + M]
+  u128* s_acc = s_red + (BS_NTHR / 32) * 64;                // [warps][1 + 2M]: R, then A_k, B_k
+  dd* s_wacc = (dd*)(s_acc + (BS_NTHR / 32) * (1 + 2 * BS_M));  // [warps][1 + M]
   u64* s_nbins = (u64*)(s_wacc + (BS_NTHR / 32) * (1 + BS_M));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < 4 * 256 * 3; i += BS_NTHR) s_lt[i] = lane_tab[i];
+  for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
   for (int i = tid; i < 4 * 256; i += BS_NTHR) s_tt[i] = thr_tab[i];
-  for (int i = tid; i < 2 * (1 << BS_L); i += BS_NTHR) s_wm[i] = wmid128[i];
-  for (int i = tid; i < (BS_NTHR / 32) * (1 + BS_M); i += BS_NTHR) s_wacc[i] = dd{0.0, 0.0};
+  for (int i = tid; i < (1 << BS_L); i += BS_NTHR) s_wm[i] = ((const ulonglong2*)wmid128)[i];
+  for (int i = tid; i < (BS_NTHR / 32) * (1 + 2 * BS_M); i += BS_NTHR) s_acc[i] = u128{0ull, 0ull};
   for (int i = tid; i <= BS_M; i += BS_NTHR) s_nbins[i] = 0ull;
   __syncthreads();
-  dd* wacc = s_wacc + warp * (1 + BS_M);
+  u128* acc = s_acc + warp * (1 + 2 * BS_M);
   u128* red = s_red + warp * 64;
   u64* bins = s_bins + tid;
   u128* A = s_A + tid;
+  const BsTr tr = bs_tr_init(lane);
   const bool thr_on = lane < (1 << BS_TB);
   const int pc_thr = __popc(lane & ((1 << BS_TB) - 1));
   const u64 thw = thr_on ? P.thw[lane] : 0ull;
-  // owned arcs (internal positions lane and lane + 32) accumulate in registers
-  dd own0 = dd{0.0, 0.0}, own1 = dd{0.0, 0.0}, ownR = dd{0.0, 0.0};
   const u64 t_start = bs_timer();
   u64 n_walk = 0, n_full = 0, n_dead = 0;
   u32 a[BS_M];
@@ -375,7 +433,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
       u32 e[BS_NCORE > 0 ? BS_NCORE : 1];
       bs_inv(a, e);
 #pragma unroll
-      for (int r = 0; r < (BS_L + 1) * 2; ++r) bins[r * BS_NTHR] = 0ull;
+      for (int r = 0; r <= BS_L; ++r) bins[r * BS_NTHR] = 0ull;
 #pragma unroll
       for (int b = 0; b < BS_OUT; ++b) A[b * BS_NTHR] = u128{0ull, 0ull};
       u128 T = u128{0ull, 0ull}, T2 = u128{0ull, 0ull};
@@ -405,26 +463,23 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
           for (int b = 0; b < BS_IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
           const u32 g = (gout << BS_IN) | (u32)r;
           const u32 c = bs_var(e, w) & BS_LANE_MASK;
-          const u32 ct = bs_transpose32(c, lane);
-          const u64 wlo = s_wm[2 * g], whi = s_wm[2 * g + 1];
+          const u32 ct = bs_transpose32(c, tr);
+          const ulonglong2 wv = s_wm[g];
           if (c) {
             const int pc = pco + __popc(r);
-            const u64* t0 = s_lt + (0 * 256 + (c & 0xffu)) * 3;
-            const u64* t1 = s_lt + (1 * 256 + ((c >> 8) & 0xffu)) * 3;
-            const u64* t2 = s_lt + (2 * 256 + ((c >> 16) & 0xffu)) * 3;
-            const u64* t3 = s_lt + (3 * 256 + (c >> 24)) * 3;
-            const u128 x = mul64x128_shr64(t0[0] + t1[0] + t2[0] + t3[0], wlo, whi);
+            const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
+            const ulonglong2 t2 = s_lt[2 * 256 + ((c >> 16) & 0xffu)], t3 = s_lt[3 * 256 + (c >> 24)];
+            const u128 x = mul64x128_shr64(t0.x + t1.x + t2.x + t3.x, wv.x, wv.y);
             u128_add(T, x.lo, x.hi);
 #pragma unroll
             for (int b = 0; b < BS_IN; ++b)
               if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
-            bins[(2 * pc) * BS_NTHR] += t0[1] + t1[1] + t2[1] + t3[1];
-            bins[(2 * pc + 1) * BS_NTHR] += t0[2] + t1[2] + t2[2] + t3[2];
+            bins[pc * BS_NTHR] += t0.y + t1.y + t2.y + t3.y;
           }
           if (ct) {
             const u64 s2 = s_tt[ct & 0xffu] + s_tt[256 + ((ct >> 8) & 0xffu)] +
                            s_tt[512 + ((ct >> 16) & 0xffu)] + s_tt[768 + (ct >> 24)];
-            const u128 x2 = mul64x128_shr64(s2, wlo, whi);
+            const u128 x2 = mul64x128_shr64(s2, wv.x, wv.y);
             u128_add(T2, x2.lo, x2.hi);
           }
         }
@@ -462,49 +517,66 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
       }
       __syncwarp();
     }
-    // ---- per-arc arithmetic on the owning lanes (internal arcs lane, lane + 32)
-    const dd wpre = bs_prefix_mass(P, ptab, prefix);
-    const dd Sd = fx124(S);
-    if (lane == 0) ownR = dd_add(ownR, dd_mul(wpre, Sd));
+    // ---- per-arc scaling on the owning lanes (internal arcs lane, lane + 32)
+    const mx wpre = bs_prefix_mass(P, ptab, prefix);
+    if (lane == 0) {
+      const u128 c = mx_apply(wpre, S);
+      u128 r0 = acc[0];
+      u128_add(r0, c.lo, c.hi);
+      acc[0] = r0;
+    }
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       const int k = lane + 32 * half;
       if (k >= BS_M) continue;
-      dd v = dd{0.0, 0.0};
+      u128 X = u128{0ull, 0ull}, Y = u128{0ull, 0ull};
+      mx f = wpre;
       if (k >= BS_TOP) {
-        // prefix arc: the item's mass without this arc's factor, with sign
+        // prefix arc: the item's mass without this arc's factor, into A
+        // when the arc works in this item and into B when it fails
         const int j = k - BS_TOP;
         int l = 0, sh = 0;
         while (sh + P.lev_bits[l] <= j) { sh += P.lev_bits[l]; ++l; }
-        dd ex = dd{1.0, 0.0};
         int s2 = 0;
         for (int q = 0; q < P.nlev; ++q) {
           const u64 bits = (prefix >> s2) & ((1ull << P.lev_bits[q]) - 1ull);
-          const dd f = q == l ? ptab_ex[((size_t)j << 11) + bits] : ptab[P.lev_off[q] + bits];
-          ex = q ? dd_mul(ex, f) : f;
+          const mx t = q == l ? ptab_ex[((size_t)j << 11) + bits] : ptab[P.lev_off[q] + bits];
+          f = q ? mx_mul(f, t) : t;
           s2 += P.lev_bits[q];
         }
-        v = dd_mul(ex, Sd);
-        if (!((prefix >> j) & 1ull)) v = dd_neg(v);
+        if ((prefix >> j) & 1ull) X = S; else Y = S;
       } else if (pr != 2) {
-        if (k < BS_WALK0) {
-          v = dd_mul(wpre, fx124(red[k]));
-        } else {
-          // walk arc: A / p - (T - A) / (1 - p), both exact integers
-          const dd av = fx124(red[k]), zv = fx124(red[32 + (k & 31)]);
-          v = dd_mul(wpre, dd_add(dd_mul(av, Q.inv_p[k]), dd_neg(dd_mul(zv, Q.inv_q[k]))));
-        }
+        X = red[k];
+        if (k >= BS_WALK0) Y = red[32 + (k & 31)];
+      } else {
+        continue;   // every state of the item connected: no internal arc matters
       }
-      if (half == 0) own0 = dd_add(own0, v); else own1 = dd_add(own1, v);
+      u128* ak = acc + 1 + 2 * k;
+      const u128 cx = mx_apply(f, X), cy = mx_apply(f, Y);
+      u128 va = ak[0], vb = ak[1];
+      u128_add(va, cx.lo, cx.hi);
+      u128_add(vb, cy.lo, cy.hi);
+      ak[0] = va;
+      ak[1] = vb;
     }
     __syncwarp();
   }
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
   }
-  if (lane == 0) wacc[0] = ownR;
-  if (lane < BS_M) wacc[1 + lane] = own0;
-  if (lane + 32 < BS_M) wacc[1 + lane + 32] = own1;
+  // ---- once per warp: the accumulators as double-double; walk arcs divide
+  // by p and 1 - p here
+  __syncwarp();
+  dd* wacc = s_wacc + warp * (1 + BS_M);
+  if (lane == 0) wacc[0] = u128_dd_scaled(acc[0], 123);
+  for (int k = lane; k < BS_M; k += 32) {
+    const dd av = u128_dd_scaled(acc[1 + 2 * k], 123), bv = u128_dd_scaled(acc[2 + 2 * k], 123);
+    dd v;
+    if (k >= BS_TOP) v = dd_add(av, dd_neg(bv));
+    else if (k >= BS_WALK0) v = dd_add(dd_mul(av, Q.inv_p[k]), dd_neg(dd_mul(bv, Q.inv_q[k])));
+    else v = av;
+    wacc[1 + k] = v;
+  }
   __syncthreads();
   bs_write_partials(W, s_wacc, s_nbins);
 }
@@ -515,14 +587,15 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
 // Batched: every network's connectivity program is a struct of static
 // functions (inv, var) with its sizes as constants; one persistent kernel
 // takes (network, prefix) items from one ticket -- networks with the most
-// items first -- and switches to that network's item function.  Each word's
-// 32-state connectivity is computed once and weighted by every p-vector of
-// the chunk (byte tables interleaved by p-vector, read through L1); per item
-// and p-vector the result is added exactly into a 160-bit accumulator of
-// five 64-bit limbs with integer atomics.
+// items first -- and switches to that network's item function.  That
+// function only stages the item's 2^L connectivity words in shared memory;
+// one shared accumulate (compiled once, so the module's compile time barely
+// grows with the number of networks) weights each word by every p-vector,
+// 16 at a time in registers (byte tables interleaved by p-vector, read
+// through L1); per item and p-vector the result is added exactly into a
+// 160-bit accumulator of five 64-bit limbs with integer atomics.
 static const char* kBsBatchTemplate = R"PBAT(
-#define BSB_LIMBS 5
-#define BSB_SCALE 158
+#define BSB_LIMBS 4
 #define BSB_KC 16
 struct BGraph {
   u64 task_begin, n_tasks;
@@ -533,38 +606,23 @@ struct BGraph {
   u64 binom[64];
 };
 
-// add round(x * 2^BSB_SCALE) (x may be negative) to the limbs, 32 bits per limb
-__device__ void bsb_limb_add(u64* limbs, double x) {
-  if (x == 0.0) return;
-  const bool neg = x < 0.0;
-  int ex;
-  const double mant = frexp(fabs(x), &ex);
-  long long M = (long long)ldexp(mant, 53);
-  int e = ex - 53 + BSB_SCALE;
-  if (e < 0) {
-    if (-e > 62) return;
-    M = (M + (1ll << (-e - 1))) >> (-e);
-    e = 0;
-    if (M == 0) return;
-  }
-  const int c = e >> 5, sh = e & 31;
-  // M < 2^54 shifted left by sh < 32: three 32-bit chunks
-  const u64 lo = (u64)M << sh, hi = sh ? ((u64)M >> (64 - sh)) : 0ull;
-  const u64 chunks[3] = {lo & 0xffffffffull, lo >> 32, hi};
+// add a value at scale 2^123 to the limbs, 32 bits per 64-bit limb (the
+// upper halves absorb the carries)
+__device__ __forceinline__ void bsb_limb_add(u64* limbs, u128 v) {
+  const u64 c[4] = {v.lo & 0xffffffffull, v.lo >> 32, v.hi & 0xffffffffull, v.hi >> 32};
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const u64 chunk = chunks[i];
-    if (chunk && c + i < BSB_LIMBS) atomicAdd(&limbs[c + i], neg ? (u64)(-(long long)chunk) : chunk);
-  }
+  for (int i = 0; i < 4; ++i)
+    if (c[i]) atomicAdd(&limbs[i], c[i]);
 }
 
-__device__ __forceinline__ dd bsb_prefix_mass(const BGraph& B, const dd* __restrict__ pt, int k, u64 prefix) {
-  dd w = dd{1.0, 0.0};
+__device__ __forceinline__ mx bsb_prefix_mass(const BGraph& B, const mx* __restrict__ pt, int k, u64 prefix) {
+  mx w = mx{1ull << 63, 0, 0};
   int sh = 0;
-  const dd* t = pt + B.pt_off + (size_t)k * B.pt_size;
+  const mx* t = pt + B.pt_off + (size_t)k * B.pt_size;
   for (int l = 0; l < B.nlev; ++l) {
     const u64 v = (prefix >> sh) & ((1ull << B.lev_bits[l]) - 1ull);
-    w = l ? dd_mul(w, t[B.lev_off[l] + v]) : t[B.lev_off[l] + v];
+    const mx f = t[B.lev_off[l] + v];
+    w = l ? mx_mul(w, f) : f;
     sh += B.lev_bits[l];
   }
   return w;
@@ -572,59 +630,53 @@ __device__ __forceinline__ dd bsb_prefix_mass(const BGraph& B, const dd* __restr
 
 // An item whose every state connects s to t (monotone prune): its counts are
 // binomials and its mass, per p-vector, is the prefix mass.
-__device__ __noinline__ void bsb_full(const BGraph& B, u64 prefix, int lane, int K, const dd* __restrict__ pt,
+__device__ __noinline__ void bsb_full(const BGraph& B, u64 prefix, int lane, int K, const mx* __restrict__ pt,
                                       u64* limbs, u64* nk) {
   const int pc_pre = __popcll((long long)prefix);
   for (int j = lane; j <= B.top; j += 32) atomicAdd(&nk[B.nk_off + pc_pre + j], B.binom[j]);
-  for (int k = lane; k < K; k += 32) {
-    const dd w = bsb_prefix_mass(B, pt, k, prefix);
-    u64* lk = limbs + ((size_t)B.gidx * K + k) * BSB_LIMBS;
-    bsb_limb_add(lk, w.hi);
-    bsb_limb_add(lk, w.lo);
-  }
+  for (int k = lane; k < K; k += 32)
+    bsb_limb_add(limbs + ((size_t)B.gidx * K + k) * BSB_LIMBS,
+                 mx_apply(bsb_prefix_mass(B, pt, k, prefix), u128{0ull, 1ull << 60}));
 }
 
 // Everything of an item past connectivity, shared by every network: cw holds
 // this thread's 2^L connectivity words (stride BSB_NTHR), word g for walk
 // state g.  Counts N_k once, then sums the exact fixed-point mass of every
-// p-vector, BSB_KC of them at a time (Eq. 1 restricted to the item).
+// p-vector, BSB_KC of them at a time (Eq. 1 restricted to the item): per
+// thread in registers, then over the warp by a reduce-scatter that leaves
+// p-vector kk's item total on lanes 2 idx(kk) and 2 idx(kk) + 1, so that the
+// prefix scaling and the limb additions run on 16 lanes at once.
 __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefix, int lane, int K, int Kp,
                                        const u64* __restrict__ lt, const u64* __restrict__ nt,
-                                       const u64* __restrict__ wm, const dd* __restrict__ pt,
+                                       const u64* __restrict__ wm, const mx* __restrict__ pt,
                                        const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins) {
+  constexpr int nsh[6] = BS_NK_SHIFTS, nwd[6] = BS_NK_WIDTHS;
   const int nw = 1 << B.L;
   const int pc_pre = __popcll((long long)prefix);
-  for (int r = 0; r <= B.L; ++r) {
-    bins[(2 * r) * BSB_NTHR] = 0ull;
-    bins[(2 * r + 1) * BSB_NTHR] = 0ull;
-  }
+  for (int r = 0; r <= B.L; ++r) bins[r * BSB_NTHR] = 0ull;
   const u64* ntg = nt + B.nt_off;
   for (int g = 0; g < nw; ++g) {
     const u32 c = cw[g * BSB_NTHR];
     if (!c) continue;
-    const int pc = __popc(g);
-    const u64* n0 = ntg + (size_t)(0 * 256 + (c & 0xffu)) * 2;
-    const u64* n1 = ntg + (size_t)(1 * 256 + ((c >> 8) & 0xffu)) * 2;
-    const u64* n2 = ntg + (size_t)(2 * 256 + ((c >> 16) & 0xffu)) * 2;
-    const u64* n3 = ntg + (size_t)(3 * 256 + (c >> 24)) * 2;
-    bins[(2 * pc) * BSB_NTHR] += __ldg(n0) + __ldg(n1) + __ldg(n2) + __ldg(n3);
-    bins[(2 * pc + 1) * BSB_NTHR] += __ldg(n0 + 1) + __ldg(n1 + 1) + __ldg(n2 + 1) + __ldg(n3 + 1);
+    bins[__popc(g) * BSB_NTHR] += __ldg(ntg + (c & 0xffu)) + __ldg(ntg + 256 + ((c >> 8) & 0xffu)) +
+                                  __ldg(ntg + 512 + ((c >> 16) & 0xffu)) + __ldg(ntg + 768 + (c >> 24));
   }
   const bool thr_on = lane < (1 << B.tb);
   if (thr_on) {
     const int base = B.nk_off + pc_pre + __popc(lane);
     for (int r = 0; r <= B.L; ++r) {
-      const u64 n0 = bins[(2 * r) * BSB_NTHR], n1 = bins[(2 * r + 1) * BSB_NTHR];
+      const u64 n = bins[r * BSB_NTHR];
 #pragma unroll
-      for (int cl = 0; cl < 3; ++cl) {
-        const u64 c0 = (n0 >> (21 * cl)) & 0x1fffffull, c1 = (n1 >> (21 * cl)) & 0x1fffffull;
-        if (c0) atomicAdd(&nk[base + r + cl], c0);
-        if (c1) atomicAdd(&nk[base + r + 3 + cl], c1);
+      for (int cl = 0; cl < 6; ++cl) {
+        const u64 v = (n >> nsh[cl]) & ((1ull << nwd[cl]) - 1ull);
+        if (v) atomicAdd(&nk[base + r + cl], v);
       }
     }
   }
   const u64* ltg = lt + B.lt_off;
   const u64* wmg = wm + B.wm_off;
+  // p-vector whose total this lane holds after the reduce-scatter
+  const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
   for (int k0 = 0; k0 < K; k0 += BSB_KC) {
     const int kc = min(BSB_KC, K - k0);
     u128 T[BSB_KC];
@@ -649,18 +701,32 @@ __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefi
         u128_add(T[2 * h + 1], sy * ww.y, __umul64hi(sy, ww.y));
       }
     }
+    // thread-pattern masses (scale 2^124 after this), then the reduce-scatter
 #pragma unroll
     for (int kk = 0; kk < BSB_KC; ++kk) {
-      if (kk >= kc) break;
-      const u64 tw = thr_on ? __ldg(thw + B.thw_off + (size_t)lane * Kp + k0 + kk) : 0ull;
-      const u128 S = warp_sum_u128(mul64x128_shr64(tw, T[kk].lo, T[kk].hi));
-      if (lane == kk) {
-        const dd v = dd_mul(bsb_prefix_mass(B, pt, k0 + kk, prefix), dd_ldexp(u128_to_dd(S), -124));
-        u64* lk = limbs + ((size_t)B.gidx * K + k0 + kk) * BSB_LIMBS;
-        bsb_limb_add(lk, v.hi);
-        bsb_limb_add(lk, v.lo);
+      const u64 tw = (thr_on && kk < kc) ? __ldg(thw + B.thw_off + (size_t)lane * Kp + k0 + kk) : 0ull;
+      T[kk] = mul64x128_shr64(tw, T[kk].lo, T[kk].hi);
+    }
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const int o = 16 >> st, n = 8 >> st;
+      const bool up = lane & o;
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        const u128 send = up ? T[i] : T[i + n];
+        const u128 keep = up ? T[i + n] : T[i];
+        const u128 got = shfl_xor_u128(send, o);
+        T[i] = keep;
+        u128_add(T[i], got.lo, got.hi);
       }
     }
+    {
+      const u128 got = shfl_xor_u128(T[0], 1);
+      u128_add(T[0], got.lo, got.hi);
+    }
+    if (!(lane & 1) && idx < kc)
+      bsb_limb_add(limbs + ((size_t)B.gidx * K + k0 + idx) * BSB_LIMBS,
+                   mx_apply(bsb_prefix_mass(B, pt, k0 + idx, prefix), T[0]));
   }
 }
 
@@ -679,7 +745,7 @@ __device__ __forceinline__ u32 bsb_uniform(const u32* a) {
 template <class G>
 __device__ void bsb_item(const BGraph& B, u64 prefix, int lane, int K, int Kp,
                          const u64* __restrict__ lt, const u64* __restrict__ nt,
-                         const u64* __restrict__ wm, const dd* __restrict__ pt,
+                         const u64* __restrict__ wm, const mx* __restrict__ pt,
                          const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins, u32* cw) {
   u32 a[G::M];
 #pragma unroll

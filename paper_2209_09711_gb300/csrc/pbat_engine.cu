@@ -43,9 +43,9 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
                const DeviceInfo& dev, BsLaunch& bl);
 cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsigned long long* d_lane,
                       const unsigned long long* d_thr, const unsigned long long* d_wmid,
-                      const dd* d_ptab, const dd* d_ptab_ex, const DevWork& W);
-const std::vector<dd>& bs_ptab(const BsLaunch& bl);
-const std::vector<dd>& bs_ptab_ex(const BsLaunch& bl);
+                      const void* d_ptab, const void* d_ptab_ex, const DevWork& W);
+const std::vector<MxHost>& bs_ptab(const BsLaunch& bl);
+const std::vector<MxHost>& bs_ptab_ex(const BsLaunch& bl);
 const std::vector<unsigned long long>& bs_thr_tab(const BsLaunch& bl);
 bool bs_grad(const BsLaunch& bl);
 const std::vector<int>& bs_perm(const BsLaunch& bl);
@@ -379,8 +379,8 @@ struct Job {
   unsigned long long* d_lane = nullptr;
   unsigned long long* d_thr = nullptr;
   unsigned long long* d_wmid64 = nullptr;
-  dd* d_ptab = nullptr;
-  dd* d_ptabx = nullptr;
+  void* d_ptab = nullptr;
+  void* d_ptabx = nullptr;
   double abs_err_bound = 0.0;  // of R, relative to the enumerated probability mass
   double mass = 1.0;           // probability mass of the enumerated states
   std::vector<int> perm;       // internal arc position -> input arc
@@ -627,8 +627,8 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
     o_lane = off; off = up16(off + bs_lane_tab(*J->bs).size() * 8);
     o_thr = off; off = up16(off + bs_thr_tab(*J->bs).size() * 8);
     o_wmid64 = off; off = up16(off + bs_wmid(*J->bs).size() * 8);
-    o_ptab = off; off = up16(off + bs_ptab(*J->bs).size() * sizeof(dd));
-    o_ptabx = off; off = up16(off + bs_ptab_ex(*J->bs).size() * sizeof(dd));
+    o_ptab = off; off = up16(off + bs_ptab(*J->bs).size() * sizeof(MxHost));
+    o_ptabx = off; off = up16(off + bs_ptab_ex(*J->bs).size() * sizeof(MxHost));
     o_tab_end = off;
   }
   const size_t dbytes = off;
@@ -674,13 +674,13 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
     memcpy(hb + o_lane, lt.data(), lt.size() * 8);
     if (!tt.empty()) memcpy(hb + o_thr, tt.data(), tt.size() * 8);
     memcpy(hb + o_wmid64, wm.data(), wm.size() * 8);
-    memcpy(hb + o_ptab, pt.data(), pt.size() * sizeof(dd));
-    if (!px.empty()) memcpy(hb + o_ptabx, px.data(), px.size() * sizeof(dd));
+    memcpy(hb + o_ptab, pt.data(), pt.size() * sizeof(MxHost));
+    if (!px.empty()) memcpy(hb + o_ptabx, px.data(), px.size() * sizeof(MxHost));
     J->d_lane = (unsigned long long*)(d + o_lane);
     J->d_thr = (unsigned long long*)(d + o_thr);
     J->d_wmid64 = (unsigned long long*)(d + o_wmid64);
-    J->d_ptab = (dd*)(d + o_ptab);
-    J->d_ptabx = (dd*)(d + o_ptabx);
+    J->d_ptab = (void*)(d + o_ptab);
+    J->d_ptabx = (void*)(d + o_ptabx);
     J->wmid_host_staging = h + h_lane;
     J->wmid_bytes = o_tab_end - o_lane;
     J->d_wmid = (u128*)(d + o_lane);  // upload destination

@@ -90,6 +90,40 @@ inline u128 to_fixed127(dd v) {
   return u128{(uint64_t)r, (uint64_t)(r >> 64)};
 }
 
+// Products of arc reliabilities in the kernels' integer floating point:
+// value m * 2^(-63 - e) with m in [2^63, 2^64) (or m = 0) and e >= 0, m
+// rounded from the double-double.
+struct MxHost {
+  uint64_t m;
+  int32_t e, pad;
+};
+inline MxHost to_mx(dd v) {
+  MxHost out{0, 0, 0};
+  if (!(v.hi > 0.0)) return out;
+  int k;
+  frexp(v.hi, &k);
+  int e = 1 - k;
+  uint128_host r = scaled_round_u(v.hi, 64 - k);
+  if (v.lo > 0)
+    r += scaled_round_u(v.lo, 64 - k);
+  else if (v.lo < 0)
+    r -= scaled_round_u(-v.lo, 64 - k);
+  if (r >> 64) {
+    r >>= 1;
+    --e;
+  } else if (!(r >> 63)) {
+    r <<= 1;
+    ++e;
+  }
+  if (e < 0) {  // a rounded product of reliabilities never exceeds 1
+    r = (uint128_host)1 << 63;
+    e = 0;
+  }
+  out.m = (uint64_t)r;
+  out.e = e;
+  return out;
+}
+
 inline dd dd_recip(double x) {
   // Newton step on 1/x in double-double: y1 = y0 + y0 * (1 - x y0)
   const double y0 = 1.0 / x;
