@@ -269,12 +269,20 @@ def run_ours(a):
     clocks = sampler.stop()
     ronly = pb.Plan(net, grad=False, opts=opts_for("r_only"), stream=sp)
     ms_r, kern_r, _, res_r = time_plan(ronly, a.steps, a.warmup)
-    # the plain GPU BAT: one state per thread, per-state PLSA frontier expansion
-    plain = pb.Plan(net, grad=False, opts=pb.options(algo=pb.ALGO_FRONTIER), stream=sp)
+    # the plain GPU BAT: one state per thread, per-state PLSA frontier
+    # expansion; above 2^34 states it runs on the first of 2^(m-34) equal
+    # divisions (same per-state work) so that the bench stays within minutes
+    plain_rb = max(0, m - 34)
+    popt = dict(algo=pb.ALGO_FRONTIER, range_bits=plain_rb, range_lo=0, range_hi=1) if plain_rb \
+        else dict(algo=pb.ALGO_FRONTIER)
+    plain_states = states >> plain_rb
+    plain = pb.Plan(net, grad=False, opts=pb.options(**popt), stream=sp)
     ms_p, kern_p, _, res_p = time_plan(plain, max(3, a.steps // 10), min(a.warmup, 3))
-    plain_g = pb.Plan(net, grad=True, opts=pb.options(algo=pb.ALGO_FRONTIER), stream=sp)
+    plain_g = pb.Plan(net, grad=True, opts=pb.options(**popt), stream=sp)
     ms_pg, kern_pg, _, res_pg = time_plan(plain_g, max(3, a.steps // 10), min(a.warmup, 3))
-    assert res_r.Nk == res_f.Nk == res_p.Nk == res_pg.Nk, "kernels disagree on N_k"
+    assert res_r.Nk == res_f.Nk, "kernels disagree on N_k"
+    if not plain_rb:
+        assert res_r.Nk == res_p.Nk == res_pg.Nk, "kernels disagree on N_k"
 
     # e2e: the public call with host buffers, copies included
     e2e_t = []
@@ -334,11 +342,13 @@ def run_ours(a):
         "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r,
                    "kernel": "bs_kernel", "shape": ronly.describe(),
                    "roofline": roofline("bs_kernel", ronly, kern_r)},
-        "plain_gpu_bat": {"value": ws * states / (ms_p / 1e3), "ms_per_step": ms_p,
+        "plain_gpu_bat": {"value": ws * plain_states / (ms_p / 1e3), "ms_per_step": ms_p,
                           "kernel": "frontier_kernel (one state per thread, PLSA frontier)",
-                          "fused_value": ws * states / (ms_pg / 1e3), "fused_ms_per_step": ms_pg},
+                          "states": plain_states,
+                          "fused_value": ws * plain_states / (ms_pg / 1e3), "fused_ms_per_step": ms_pg},
         "fused_over_r_only_time": ms_f / ms_r,
-        "speedup_over_plain_gpu_bat": {"R": ms_p / ms_r, "R+grad": ms_pg / ms_f},
+        "speedup_over_plain_gpu_bat": {"R": (ms_p / plain_states) / (ms_r / states),
+                                       "R+grad": (ms_pg / plain_states) / (ms_f / states)},
         "R": res_f.R, "pruned_states": res_f.stats[1], "walked_states": res_f.stats[0],
         "cpu_baseline": cpu,
         "e2e": {"value": ws * states / e2e_s, "unit": "states/s",

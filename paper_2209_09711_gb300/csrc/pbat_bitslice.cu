@@ -623,7 +623,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     }
     bl.smem = (size_t)(4 * 256 * 2 + 2 * (1 << bp.L) + 4 * 256 + (bp.L + 1) * bl.nthr) * 8 +
               (size_t)std::max(L_out, 1) * bl.nthr * 16 + (size_t)(bl.nthr / 32) * 64 * 16 +
-              (size_t)(bl.nthr / 32) * (1 + 2 * m) * 16 +
+              (size_t)(bl.nthr / 32) * (1 + 2 * m) * 24 +
               (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
   }
   if (bl.smem > (size_t)dev.smem_optin)
@@ -698,8 +698,8 @@ struct BGraphHost {
 
 constexpr int kBsbThreads = 128;
 constexpr int kBsbMaxWalk = 5;  // 2^L connectivity words per thread staged in shared memory
-constexpr int kBsbLimbs = 4;    // 32-bit chunks of a value at scale 2^123, in 64-bit atomics
-constexpr int kBsbScale = 123;
+constexpr int kBsbLimbs = 8;    // 32-bit chunks of a value at scale 2^250, in 64-bit atomics
+constexpr int kBsbScale = 250;
 constexpr int kBsbMaxGraphs = 256;
 
 struct BsBatch {

@@ -112,10 +112,28 @@ __device__ __forceinline__ mx mx_mul(mx a, mx b) {
   if (!(h >> 63)) { h <<= 1; ++e; }
   return mx{h, e, 0};
 }
-// x times a 128-bit value at scale 2^124, at scale 2^123 (truncated)
-__device__ __forceinline__ u128 mx_apply(mx x, u128 v) {
-  return u128_shr(mul64x128_shr64(x.m, v.lo, v.hi), x.e);
+// x times a 128-bit value v at scale 2^124 is mx_prod(x, v) * 2^(-123 - x.e)
+// (truncated; below 2^124)
+__device__ __forceinline__ u128 mx_prod(mx x, u128 v) { return mul64x128_shr64(x.m, v.lo, v.hi); }
+
+// Floating 128-bit accumulator: value v * 2^(-123 - E) with v < 2^126, so a
+// sum of items keeps about 125 significant bits relative to its own size,
+// whatever the mass of the enumerated range.
+struct facc { u128 v; int E; int pad; };
+__device__ __forceinline__ void facc_add(facc& a, u128 P, int e) {
+  if (!(P.lo | P.hi)) return;
+  if (!(a.v.lo | a.v.hi)) { a.v = P; a.E = e; return; }
+  if (e >= a.E) {
+    const u128 q = u128_shr(P, e - a.E);
+    u128_add(a.v, q.lo, q.hi);
+  } else {
+    a.v = u128_shr(a.v, a.E - e);
+    a.E = e;
+    u128_add(a.v, P.lo, P.hi);
+  }
+  if (a.v.hi >> 62) { a.v = u128_shr(a.v, 1); a.E -= 1; }
 }
+__device__ __forceinline__ dd facc_dd(const facc& a) { return u128_dd_scaled(a.v, 123 + a.E); }
 
 // N_k counts of one word, packed by lane-popcount class cl = 0..5 into
 // fields of 8, 11, 12, 12, 11 and 8 bits: wide enough for one item's sum
@@ -232,7 +250,7 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
   const u64 thw = thr_on ? P.thw[lane] : 0ull;
   const u64 t_start = bs_timer();
   u64 n_walk = 0, n_full = 0, n_dead = 0;
-  u128 accR = u128{0ull, 0ull};   // this warp's R, scale 2^123 (the same in every lane)
+  facc accR = facc{u128{0ull, 0ull}, 0, 0};   // this warp's R (the same in every lane)
   u32 a[BS_M];
   bs_init_arcs(a, lane);
 
@@ -254,8 +272,8 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
       if (pr == 2) {
         ++n_full;
         for (int j = lane; j <= BS_TOP; j += 32) atomicAdd(&s_nbins[pc_pre + j], P.binom[j]);
-        const u128 c = mx_apply(bs_prefix_mass(P, ptab, prefix), u128{0ull, 1ull << 60});
-        u128_add(accR, c.lo, c.hi);
+        const mx w = bs_prefix_mass(P, ptab, prefix);
+        facc_add(accR, mx_prod(w, u128{0ull, 1ull << 60}), w.e);
         continue;
       }
     }
@@ -298,12 +316,12 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
     // item total: exact warp sum of T x thread mass (scale 2^124), times the
     // prefix mass, once per item
     const u128 S = warp_sum_u128(mul64x128_shr64(thw, T.lo, T.hi));
-    const u128 c = mx_apply(bs_prefix_mass(P, ptab, prefix), S);
-    u128_add(accR, c.lo, c.hi);
+    const mx w = bs_prefix_mass(P, ptab, prefix);
+    facc_add(accR, mx_prod(w, S), w.e);
   }
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
-    wacc[0] = u128_dd_scaled(accR, 123);
+    wacc[0] = facc_dd(accR);
   }
   __syncthreads();
   bs_write_partials(W, s_wacc, s_nbins);
@@ -327,9 +345,9 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
 // Per item every quantity is first summed exactly over the warp in 128-bit
 // integers with fixed-point per-lane weights; then the lane that owns an arc
 // (lanes k and k - 32 own internal arc k) scales it by the item's prefix
-// mass (integer floating point) and adds it to that arc's two 128-bit
-// accumulators (scale 2^123) in shared memory.  Walk masses are 128-bit
-// (scale 2^127).
+// mass (integer floating point) and adds it to that arc's two floating
+// 128-bit accumulators in shared memory.  Walk masses are 128-bit (scale
+// 2^127).
 struct BsGradParams {
   u64 thw_ex[5][32];    // thread-pattern masses without thread arc i (2^63)
   u64 lw_ex[5][32];     // lane-pattern masses without lane arc i (2^63)
@@ -383,17 +401,17 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   u64* s_bins = s_tt + 4 * 256;                             // [L + 1][NTHR]
   u128* s_A = (u128*)(s_bins + (BS_L + 1) * BS_NTHR);       // [BS_OUT][NTHR]
   u128* s_red = s_A + (BS_OUT > 0 ? BS_OUT : 1) * BS_NTHR;  // [warps][64] reduced values
-  u128* s_acc = s_red + (BS_NTHR / 32) * 64;                // [warps][1 + 2M]: R, then A_k, B_k
+  facc* s_acc = (facc*)(s_red + (BS_NTHR / 32) * 64);       // [warps][1 + 2M]: R, then A_k, B_k
   dd* s_wacc = (dd*)(s_acc + (BS_NTHR / 32) * (1 + 2 * BS_M));  // [warps][1 + M]
   u64* s_nbins = (u64*)(s_wacc + (BS_NTHR / 32) * (1 + BS_M));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
   for (int i = tid; i < 4 * 256; i += BS_NTHR) s_tt[i] = thr_tab[i];
   for (int i = tid; i < (1 << BS_L); i += BS_NTHR) s_wm[i] = ((const ulonglong2*)wmid128)[i];
-  for (int i = tid; i < (BS_NTHR / 32) * (1 + 2 * BS_M); i += BS_NTHR) s_acc[i] = u128{0ull, 0ull};
+  for (int i = tid; i < (BS_NTHR / 32) * (1 + 2 * BS_M); i += BS_NTHR) s_acc[i] = facc{u128{0ull, 0ull}, 0, 0};
   for (int i = tid; i <= BS_M; i += BS_NTHR) s_nbins[i] = 0ull;
   __syncthreads();
-  u128* acc = s_acc + warp * (1 + 2 * BS_M);
+  facc* acc = s_acc + warp * (1 + 2 * BS_M);
   u128* red = s_red + warp * 64;
   u64* bins = s_bins + tid;
   u128* A = s_A + tid;
@@ -520,9 +538,8 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     // ---- per-arc scaling on the owning lanes (internal arcs lane, lane + 32)
     const mx wpre = bs_prefix_mass(P, ptab, prefix);
     if (lane == 0) {
-      const u128 c = mx_apply(wpre, S);
-      u128 r0 = acc[0];
-      u128_add(r0, c.lo, c.hi);
+      facc r0 = acc[0];
+      facc_add(r0, mx_prod(wpre, S), wpre.e);
       acc[0] = r0;
     }
 #pragma unroll
@@ -551,11 +568,10 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
       } else {
         continue;   // every state of the item connected: no internal arc matters
       }
-      u128* ak = acc + 1 + 2 * k;
-      const u128 cx = mx_apply(f, X), cy = mx_apply(f, Y);
-      u128 va = ak[0], vb = ak[1];
-      u128_add(va, cx.lo, cx.hi);
-      u128_add(vb, cy.lo, cy.hi);
+      facc* ak = acc + 1 + 2 * k;
+      facc va = ak[0], vb = ak[1];
+      facc_add(va, mx_prod(f, X), f.e);
+      facc_add(vb, mx_prod(f, Y), f.e);
       ak[0] = va;
       ak[1] = vb;
     }
@@ -568,9 +584,9 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   // by p and 1 - p here
   __syncwarp();
   dd* wacc = s_wacc + warp * (1 + BS_M);
-  if (lane == 0) wacc[0] = u128_dd_scaled(acc[0], 123);
+  if (lane == 0) wacc[0] = facc_dd(acc[0]);
   for (int k = lane; k < BS_M; k += 32) {
-    const dd av = u128_dd_scaled(acc[1 + 2 * k], 123), bv = u128_dd_scaled(acc[2 + 2 * k], 123);
+    const dd av = facc_dd(acc[1 + 2 * k]), bv = facc_dd(acc[2 + 2 * k]);
     dd v;
     if (k >= BS_TOP) v = dd_add(av, dd_neg(bv));
     else if (k >= BS_WALK0) v = dd_add(dd_mul(av, Q.inv_p[k]), dd_neg(dd_mul(bv, Q.inv_q[k])));
@@ -595,7 +611,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
 // through L1); per item and p-vector the result is added exactly into a
 // 160-bit accumulator of five 64-bit limbs with integer atomics.
 static const char* kBsBatchTemplate = R"PBAT(
-#define BSB_LIMBS 4
+#define BSB_LIMBS 8
 #define BSB_KC 16
 struct BGraph {
   u64 task_begin, n_tasks;
@@ -606,13 +622,24 @@ struct BGraph {
   u64 binom[64];
 };
 
-// add a value at scale 2^123 to the limbs, 32 bits per 64-bit limb (the
-// upper halves absorb the carries)
-__device__ __forceinline__ void bsb_limb_add(u64* limbs, u128 v) {
-  const u64 c[4] = {v.lo & 0xffffffffull, v.lo >> 32, v.hi & 0xffffffffull, v.hi >> 32};
+// add P * 2^(-123 - e) (P < 2^124, e >= 0) to the limbs: a 256-bit fixed
+// point number at scale 2^250, 32 bits per 64-bit limb (the upper halves
+// absorb the carries)
+__device__ __forceinline__ void bsb_limb_add(u64* limbs, u128 P, int e) {
+  int s = 127 - e;
+  if (s < 0) {
+    P = u128_shr(P, -s);
+    s = 0;
+  }
+  if (!(P.lo | P.hi)) return;
+  const int c0 = s >> 5, r = s & 31;
+  const u64 q0 = P.lo << r;
+  const u64 q1 = r ? ((P.hi << r) | (P.lo >> (64 - r))) : P.hi;
+  const u64 q2 = r ? (P.hi >> (64 - r)) : 0ull;
+  const u64 c[5] = {q0 & 0xffffffffull, q0 >> 32, q1 & 0xffffffffull, q1 >> 32, q2};
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (c[i]) atomicAdd(&limbs[i], c[i]);
+  for (int i = 0; i < 5; ++i)
+    if (c[i] && c0 + i < BSB_LIMBS) atomicAdd(&limbs[c0 + i], c[i]);
 }
 
 __device__ __forceinline__ mx bsb_prefix_mass(const BGraph& B, const mx* __restrict__ pt, int k, u64 prefix) {
@@ -634,9 +661,10 @@ __device__ __noinline__ void bsb_full(const BGraph& B, u64 prefix, int lane, int
                                       u64* limbs, u64* nk) {
   const int pc_pre = __popcll((long long)prefix);
   for (int j = lane; j <= B.top; j += 32) atomicAdd(&nk[B.nk_off + pc_pre + j], B.binom[j]);
-  for (int k = lane; k < K; k += 32)
-    bsb_limb_add(limbs + ((size_t)B.gidx * K + k) * BSB_LIMBS,
-                 mx_apply(bsb_prefix_mass(B, pt, k, prefix), u128{0ull, 1ull << 60}));
+  for (int k = lane; k < K; k += 32) {
+    const mx w = bsb_prefix_mass(B, pt, k, prefix);
+    bsb_limb_add(limbs + ((size_t)B.gidx * K + k) * BSB_LIMBS, mx_prod(w, u128{0ull, 1ull << 60}), w.e);
+  }
 }
 
 // Everything of an item past connectivity, shared by every network: cw holds
@@ -724,9 +752,10 @@ __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefi
       const u128 got = shfl_xor_u128(T[0], 1);
       u128_add(T[0], got.lo, got.hi);
     }
-    if (!(lane & 1) && idx < kc)
-      bsb_limb_add(limbs + ((size_t)B.gidx * K + k0 + idx) * BSB_LIMBS,
-                   mx_apply(bsb_prefix_mass(B, pt, k0 + idx, prefix), T[0]));
+    if (!(lane & 1) && idx < kc) {
+      const mx w = bsb_prefix_mass(B, pt, k0 + idx, prefix);
+      bsb_limb_add(limbs + ((size_t)B.gidx * K + k0 + idx) * BSB_LIMBS, mx_prod(w, T[0]), w.e);
+    }
   }
 }
 
