@@ -28,6 +28,7 @@
 #include <mutex>
 #include <queue>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pbat.h"
@@ -405,6 +406,19 @@ struct BsLaunch {
   int per_sm = 1;
 };
 
+// out[v] = product over x < n of (bit x of v ? p : 1 - p) of arc arcs[x], for
+// every v < 2^n, built by doubling: two double-double products per entry.
+static void product_table(const double* p, const int* arcs, int n, dd* out) {
+  out[0] = dd_make(1.0);
+  for (int x = 0; x < n; ++x) {
+    const dd w0 = arc_w(p, arcs[x], 0), w1 = arc_w(p, arcs[x], 1);
+    for (int v = (1 << x) - 1; v >= 0; --v) {
+      out[v + (1 << x)] = dd_mul(out[v], w1);
+      out[v] = dd_mul(out[v], w0);
+    }
+  }
+}
+
 static unsigned long long fixed_u64(dd v, int scale) {
   // round((hi + lo) * 2^scale) for 0 <= v, result < 2^64
   uint128_host r = scaled_round_u(v.hi, scale);
@@ -415,15 +429,24 @@ static unsigned long long fixed_u64(dd v, int scale) {
   return (unsigned long long)r;
 }
 
+static const int kNkShift[6] = {0, 8, 19, 31, 43, 54};
+
+// packed N_k counts of a word whose every lane state is connected
+static unsigned long long full_counts(int ell) {
+  unsigned long long n = 0;
+  for (int j = 0; j < (1 << ell); ++j) n += 1ull << kNkShift[__builtin_popcount((unsigned)j)];
+  return n;
+}
+
 static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
-  char defs[512];
+  char defs[640];
   const unsigned lane_mask = bp.ell >= 5 ? 0xffffffffu : ((1u << (1 << bp.ell)) - 1u);
   snprintf(defs, sizeof defs,
            "#define BS_M %d\n#define BS_ELL %d\n#define BS_TB %d\n#define BS_L %d\n#define BS_D %d\n"
            "#define BS_NTHR %d\n#define BS_WALK0 %d\n#define BS_TOP %d\n#define BS_NCORE %d\n"
-           "#define BS_LANE_MASK 0x%08xu\n#define BS_GRAD %d\n",
+           "#define BS_LANE_MASK 0x%08xu\n#define BS_FULL_COUNTS 0x%016llxull\n#define BS_GRAD %d\n",
            g.m, bp.ell, bp.tb, bp.L, bp.d, nthr, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, bp.ncore,
-           lane_mask, bp.grad ? 1 : 0);
+           lane_mask, full_counts(bp.ell), bp.grad ? 1 : 0);
   const std::string tmpl = kBsTemplate;
   const size_t cut = tmpl.find("//@@GENERATED@@");
   return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tmpl.substr(cut);
@@ -525,20 +548,21 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     const int bits = bp.d / P.nlev + (l < bp.d % P.nlev ? 1 : 0);
     P.lev_bits[l] = bits;
     P.lev_off[l] = (int)bl.ptab.size();
-    for (int v = 0; v < (1 << bits); ++v) {
-      dd w = dd_make(1.0);
-      for (int x = 0; x < bits; ++x) w = dd_mul(w, arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
-      bl.ptab.push_back(to_mx(w));
-    }
+    std::vector<dd> tab((size_t)1 << bits);
+    product_table(p, bp.perm.data() + top + sh, bits, tab.data());
+    for (int v = 0; v < (1 << bits); ++v) bl.ptab.push_back(to_mx(tab[v]));
     if (grad)
-      for (int v = 0; v < (1 << bits); ++v) {
-        // products of the level's factors before and after each arc
-        dd pre[12], suf[12];
-        pre[0] = dd_make(1.0);
-        for (int x = 0; x < bits; ++x) pre[x + 1] = dd_mul(pre[x], arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
-        suf[bits] = dd_make(1.0);
-        for (int x = bits - 1; x >= 0; --x) suf[x] = dd_mul(suf[x + 1], arc_w(p, bp.perm[top + sh + x], (v >> x) & 1));
-        for (int jj = 0; jj < bits; ++jj) bl.ptab_ex[((size_t)(sh + jj) << 11) + v] = to_mx(dd_mul(pre[jj], suf[jj + 1]));
+      for (int jj = 0; jj < bits; ++jj) {
+        // the level's product without arc jj: a table over the other arcs,
+        // indexed by v with bit jj removed
+        int others[12];
+        for (int x = 0, n = 0; x < bits; ++x)
+          if (x != jj) others[n++] = bp.perm[top + sh + x];
+        product_table(p, others, bits - 1, tab.data());
+        for (int v = 0; v < (1 << bits); ++v) {
+          const int u = (v & ((1 << jj) - 1)) | ((v >> (jj + 1)) << jj);
+          bl.ptab_ex[((size_t)(sh + jj) << 11) + v] = to_mx(tab[u]);
+        }
       }
     sh += bits;
   }
@@ -546,16 +570,10 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   // lane tables: byte position b, value v -> lane mass (scale 2^62) and the
   // counts of its set lanes by lane popcount class, packed in fields of
   // 8, 11, 12, 12, 11, 8 bits
-  static const int kNkShift[6] = {0, 8, 19, 31, 43, 54};
   bl.lane_tab.assign(4 * 256 * 2, 0ull);
   dd lw[32];
-  for (int j = 0; j < 32; ++j) {
-    lw[j] = dd{0.0, 0.0};
-    if (j >= (1 << bp.ell)) continue;
-    dd w = dd_make(1.0);
-    for (int i = 0; i < bp.ell; ++i) w = dd_mul(w, arc_w(p, bp.perm[i], (j >> i) & 1));
-    lw[j] = w;
-  }
+  for (int j = 0; j < 32; ++j) lw[j] = dd{0.0, 0.0};
+  product_table(p, bp.perm.data(), bp.ell, lw);
   for (int b = 0; b < 4; ++b)
     for (int v = 0; v < 256; ++v) {
       dd s = dd{0.0, 0.0};
@@ -574,13 +592,11 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   const int L_in = std::min(bp.L, 2), L_out = bp.L - L_in;
   if (!grad) {
     bl.wmid.resize((size_t)1 << bp.L);
-    for (int gi = 0; gi < (1 << bp.L); ++gi) {
-      dd w = dd_make(1.0);
-      for (int b = 0; b < bp.L; ++b) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + bp.tb + b], (gi >> b) & 1));
-      bl.wmid[gi] = fixed_u64(w, 63);
-    }
+    std::vector<dd> wt((size_t)1 << bp.L);
+    product_table(p, bp.perm.data() + bp.ell + bp.tb, bp.L, wt.data());
+    for (int gi = 0; gi < (1 << bp.L); ++gi) bl.wmid[gi] = fixed_u64(wt[gi], 63);
     bl.smem = (size_t)(4 * 256 * 2 + (1 << bp.L) + (bp.L + 1) * bl.nthr) * 8 +
-              (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
+              (size_t)(bl.nthr / 32) * 24 + (size_t)(m + 1) * 8;
   } else {
     // fused kernel: thread-pattern masses, 128-bit walk masses, fixed-point
     // excluded-arc masses, reciprocals of the walk arcs' p and 1 - p
@@ -594,10 +610,10 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
         bl.thr_tab[b * 256 + v] = fixed_u64(s, 62);
       }
     bl.wmid128.resize((size_t)2 << bp.L);
+    std::vector<dd> wt((size_t)1 << bp.L);
+    product_table(p, bp.perm.data() + bp.ell + bp.tb, bp.L, wt.data());
     for (int gi = 0; gi < (1 << bp.L); ++gi) {
-      dd w = dd_make(1.0);
-      for (int b = 0; b < bp.L; ++b) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + bp.tb + b], (gi >> b) & 1));
-      const u128 f = to_fixed127(w);
+      const u128 f = to_fixed127(wt[gi]);
       bl.wmid128[2 * gi] = f.lo;
       bl.wmid128[2 * gi + 1] = f.hi;
     }
@@ -623,8 +639,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     }
     bl.smem = (size_t)(4 * 256 * 2 + 2 * (1 << bp.L) + 4 * 256 + (bp.L + 1) * bl.nthr) * 8 +
               (size_t)std::max(L_out, 1) * bl.nthr * 16 + (size_t)(bl.nthr / 32) * 64 * 16 +
-              (size_t)(bl.nthr / 32) * (1 + 2 * m) * 24 +
-              (size_t)(bl.nthr / 32) * (1 + m) * sizeof(dd) + (size_t)(m + 1) * 8;
+              (size_t)(bl.nthr / 32) * (1 + 2 * m) * 24 + (size_t)(m + 1) * 8;
   }
   if (bl.smem > (size_t)dev.smem_optin)
     return fail(PBAT_ERANGE, "bit-sliced kernel needs %zu B of shared memory", bl.smem);
@@ -673,6 +688,26 @@ const std::vector<unsigned long long>& bs_thr_tab(const BsLaunch& bl) { return b
 const std::vector<MxHost>& bs_ptab(const BsLaunch& bl) { return bl.ptab; }
 const std::vector<MxHost>& bs_ptab_ex(const BsLaunch& bl) { return bl.ptab_ex; }
 bool bs_grad(const BsLaunch& bl) { return bl.plan.grad; }
+
+// The fused kernel's result holds R, then A_k and B_k for every internal arc
+// k: the gradient is A - B for prefix arcs (mass without the arc, working
+// minus failed), A / p - B / (1 - p) for walk arcs (their masses carry the
+// arc's own factor) and A for lane and thread arcs (exact pair differences).
+void bs_finish_grad(const BsLaunch& bl, const dd* acc, int m, double* g_internal) {
+  const BsPlan& bp = bl.plan;
+  const int walk0 = bp.ell + bp.tb, top = walk0 + bp.L;
+  for (int k = 0; k < m; ++k) {
+    const dd a = acc[1 + 2 * k], b = acc[2 + 2 * k];
+    dd v;
+    if (k >= top)
+      v = dd_sub(a, b);
+    else if (k >= walk0)
+      v = dd_sub(dd_mul(a, bl.Q.inv_p[k]), dd_mul(b, bl.Q.inv_q[k]));
+    else
+      v = a;
+    g_internal[k] = v.hi + v.lo;
+  }
+}
 BsLaunch* bs_new() { return new BsLaunch(); }
 void bs_delete(BsLaunch* b) { delete b; }
 void bs_describe(const BsLaunch& bl, int* out6) {
@@ -692,7 +727,10 @@ struct BGraphHost {
   int gidx, m, nlev, prune;
   int lev_bits[6], lev_off[6];
   int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, tb;
-  int L, top, pad0, pad1;
+  int L, top;
+  unsigned lane_mask;
+  int pad0;
+  unsigned long long full_counts;
   unsigned long long binom[64];
 };
 
@@ -863,6 +901,8 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
     b.tb = bp.tb;
     b.L = bp.L;
     b.top = bp.ell + bp.tb + bp.L;
+    b.lane_mask = bp.ell >= 5 ? 0xffffffffu : ((1u << (1 << bp.ell)) - 1u);
+    b.full_counts = full_counts(bp.ell);
   }
   E.total = begin;
   E.n_lt = lt; E.n_nt = nt; E.n_wm = wm; E.n_pt = pt; E.n_thw = th;
@@ -910,12 +950,14 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
     poff[i] = acc;
     acc += (size_t)K * graphs[i].n_arcs;
   }
-  for (int r = 0; r < E.G; ++r) {
+  // networks write disjoint table regions: build them on several host threads
+  const int nthreads = std::max(1, std::min({E.G, 16, (int)std::thread::hardware_concurrency()}));
+  auto build_range = [&](int r0, int r1) {
+  for (int r = r0; r < r1; ++r) {
     const BGraphHost& b = E.bg[r];
     const int i = b.gidx, m = b.m;
     const BsPlan& bp = E.plans[i];
     const int top = bp.ell + bp.tb + bp.L;
-    static const int kNkShift[6] = {0, 8, 19, 31, 43, 54};
     for (int v = 0; v < 1024; ++v) {  // packed N counts by lane class (same for every p-vector)
       const int by = v >> 8, val = v & 255;
       unsigned long long n = 0;
@@ -933,47 +975,43 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
     }
     for (int k = 0; k < K; ++k) {
       const double* pv = p + poff[i] + (size_t)k * m;
-      dd lw[32];
-      for (int j = 0; j < 32; ++j) {
-        lw[j] = dd{0.0, 0.0};
-        if (j >= (1 << bp.ell)) continue;
-        dd w = dd_make(1.0);
-        for (int a = 0; a < bp.ell; ++a) w = dd_mul(w, arc_w(pv, bp.perm[a], (j >> a) & 1));
-        lw[j] = w;
-      }
-      for (int v = 0; v < 1024; ++v) {
-        const int by = v >> 8, val = v & 255;
-        dd s = dd{0.0, 0.0};
-        for (int x = 0; x < 8; ++x)
-          if ((val >> x) & 1) s = dd_add(s, lw[8 * by + x]);
-        lt[b.lt_off + (size_t)v * Kp + k] = fixed_u64(s, 62);
-      }
-      for (int gi = 0; gi < (1 << bp.L); ++gi) {
-        dd w = dd_make(1.0);
-        for (int a = 0; a < bp.L; ++a) w = dd_mul(w, arc_w(pv, bp.perm[bp.ell + bp.tb + a], (gi >> a) & 1));
-        wm[b.wm_off + (size_t)gi * Kp + k] = fixed_u64(w, 63);
-      }
-      for (int t = 0; t < 32; ++t) {
-        unsigned long long f = 0;
-        if (t < (1 << bp.tb)) {
-          dd w = dd_make(1.0);
-          for (int a = 0; a < bp.tb; ++a) w = dd_mul(w, arc_w(pv, bp.perm[bp.ell + a], (t >> a) & 1));
-          f = fixed_u64(w, 63);
+      dd lw[32], tw[32];
+      for (int j = 0; j < 32; ++j) lw[j] = tw[j] = dd{0.0, 0.0};
+      product_table(pv, bp.perm.data(), bp.ell, lw);
+      for (int by = 0; by < 4; ++by) {  // byte sums by lowest set bit: one addition each
+        dd sb[256];
+        sb[0] = dd{0.0, 0.0};
+        lt[b.lt_off + (size_t)(by * 256) * Kp + k] = 0;
+        for (int val = 1; val < 256; ++val) {
+          sb[val] = dd_add(sb[val & (val - 1)], lw[8 * by + __builtin_ctz((unsigned)val)]);
+          lt[b.lt_off + (size_t)(by * 256 + val) * Kp + k] = fixed_u64(sb[val], 62);
         }
-        th[b.thw_off + (size_t)t * Kp + k] = f;
       }
+      dd wtab[32];
+      product_table(pv, bp.perm.data() + bp.ell + bp.tb, bp.L, wtab);
+      for (int gi = 0; gi < (1 << bp.L); ++gi) wm[b.wm_off + (size_t)gi * Kp + k] = fixed_u64(wtab[gi], 63);
+      product_table(pv, bp.perm.data() + bp.ell, bp.tb, tw);
+      for (int t = 0; t < 32; ++t)
+        th[b.thw_off + (size_t)t * Kp + k] = t < (1 << bp.tb) ? fixed_u64(tw[t], 63) : 0ull;
       MxHost* ptk = pt + b.pt_off + (size_t)k * b.pt_size;
       if (b.nlev == 0) ptk[0] = to_mx(dd_make(1.0));
       for (int l = 0, sh = 0; l < b.nlev; ++l) {
-        for (int v = 0; v < (1 << b.lev_bits[l]); ++v) {
-          dd w = dd_make(1.0);
-          for (int x = 0; x < b.lev_bits[l]; ++x) w = dd_mul(w, arc_w(pv, bp.perm[top + sh + x], (v >> x) & 1));
-          ptk[b.lev_off[l] + v] = to_mx(w);
-        }
+        dd tab[1 << 11];
+        product_table(pv, bp.perm.data() + top + sh, b.lev_bits[l], tab);
+        for (int v = 0; v < (1 << b.lev_bits[l]); ++v) ptk[b.lev_off[l] + v] = to_mx(tab[v]);
         sh += b.lev_bits[l];
       }
     }
   }
+  };
+  if (nthreads == 1) {
+    build_range(0, E.G);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t)
+    pool.emplace_back(build_range, E.G * t / nthreads, E.G * (t + 1) / nthreads);
+  for (auto& th_ : pool) th_.join();
 }
 
 static int bsb_enqueue(BsBatch& E, cudaStream_t st, unsigned long long budget_ns) {

@@ -133,7 +133,29 @@ __device__ __forceinline__ void facc_add(facc& a, u128 P, int e) {
   }
   if (a.v.hi >> 62) { a.v = u128_shr(a.v, 1); a.E -= 1; }
 }
-__device__ __forceinline__ dd facc_dd(const facc& a) { return u128_dd_scaled(a.v, 123 + a.E); }
+// mant (leading 1 at bit 52) * 2^(e - 52), assembled from its bits
+__device__ __forceinline__ double bs_bits_double(u64 mant, int e) {
+  if (e < -1022 || e > 1023) return ldexp((double)mant, e - 52);   // outside the normal range
+  return __longlong_as_double((long long)(((u64)(e + 1023) << 52) | (mant & 0xfffffffffffffull)));
+}
+// the accumulator as a double-double (truncated to 106 bits) with integer
+// operations only
+__device__ __forceinline__ dd facc_to_dd(const facc& a) {
+  u64 hi = a.v.hi, lo = a.v.lo;
+  if (!(hi | lo)) return dd{0.0, 0.0};
+  const int z = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  if (z >= 64) { hi = lo << (z - 64); lo = 0ull; }
+  else if (z > 0) { hi = (hi << z) | (lo >> (64 - z)); lo <<= z; }
+  const int e = 4 - z - a.E;               // weight of the leading bit: 2^e
+  const double dh = bs_bits_double(hi >> 11, e);
+  const u64 rh = hi & 0x7ffull, rl = lo;   // the 75 bits below the head
+  if (!(rh | rl)) return dd{dh, 0.0};
+  const int z2 = rh ? __clzll((long long)rh) : 64 + __clzll((long long)rl);
+  u64 nh;
+  if (z2 >= 64) nh = rl << (z2 - 64);
+  else nh = (rh << z2) | (z2 ? (rl >> (64 - z2)) : 0ull);
+  return dd{dh, bs_bits_double(nh >> 11, e - z2)};
+}
 
 // N_k counts of one word, packed by lane-popcount class cl = 0..5 into
 // fields of 8, 11, 12, 12, 11 and 8 bits: wide enough for one item's sum
@@ -215,14 +237,17 @@ __device__ __forceinline__ void bs_flush_bins(u64* bins, u64* s_nbins, int base)
   }
 }
 
-// per-block partials for the fixed-order reduction
-__device__ __forceinline__ void bs_write_partials(const BsWork& W, const dd* s_wacc, const u64* s_nbins) {
-  for (int i = threadIdx.x; i <= BS_M; i += BS_NTHR) {
-    dd s = dd{0.0, 0.0};
-    for (int w = 0; w < BS_NTHR / 32; ++w) s = dd_add(s, s_wacc[w * (1 + BS_M) + i]);
-    W.part_acc[(size_t)blockIdx.x * (1 + BS_M) + i] = s;
-    W.part_n[(size_t)blockIdx.x * (BS_M + 1) + i] = s_nbins[i];
+// Per-block partials for the fixed-order reduction: entry i combines the
+// warps' floating accumulators s_acc[w * stride + i] in integer arithmetic and
+// becomes one double-double; then the block's N_k counts.
+__device__ __forceinline__ void bs_write_partials(const BsWork& W, const facc* s_acc, int stride, int n_acc,
+                                                  const u64* s_nbins) {
+  for (int i = threadIdx.x; i < n_acc; i += BS_NTHR) {
+    facc t = s_acc[i];
+    for (int w = 1; w < BS_NTHR / 32; ++w) facc_add(t, s_acc[w * stride + i].v, s_acc[w * stride + i].E);
+    W.part_acc[(size_t)blockIdx.x * n_acc + i] = facc_to_dd(t);
   }
+  for (int i = threadIdx.x; i <= BS_M; i += BS_NTHR) W.part_n[(size_t)blockIdx.x * (BS_M + 1) + i] = s_nbins[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -235,15 +260,13 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
   ulonglong2* s_lt = (ulonglong2*)smem;                     // [4][256] {lane mass 2^62, packed counts}
   u64* s_wmid = (u64*)(s_lt + 4 * 256);                     // [2^L], scale 2^63
   u64* s_bins = s_wmid + (1 << BS_L);                       // [L + 1][NTHR]
-  dd* s_wacc = (dd*)(s_bins + (BS_L + 1) * BS_NTHR);        // [warps][1 + M]
-  u64* s_nbins = (u64*)(s_wacc + (BS_NTHR / 32) * (1 + BS_M));
+  facc* s_acc = (facc*)(s_bins + (BS_L + 1) * BS_NTHR);     // [warps]: each warp's R
+  u64* s_nbins = (u64*)(s_acc + BS_NTHR / 32);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
   for (int i = tid; i < (1 << BS_L); i += BS_NTHR) s_wmid[i] = wmid_tab[i];
-  for (int i = tid; i < (BS_NTHR / 32) * (1 + BS_M); i += BS_NTHR) s_wacc[i] = dd{0.0, 0.0};
   for (int i = tid; i <= BS_M; i += BS_NTHR) s_nbins[i] = 0ull;
   __syncthreads();
-  dd* wacc = s_wacc + warp * (1 + BS_M);
   u64* bins = s_bins + tid;
   const bool thr_on = lane < (1 << BS_TB);
   const int pc_thr = __popc(lane & ((1 << BS_TB) - 1));
@@ -300,7 +323,12 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
 #pragma unroll
         for (int b = 0; b < BS_IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
         const u32 c = bs_var(e, w) & BS_LANE_MASK;
-        if (c) {
+        if (c == BS_LANE_MASK) {
+          // every lane state connected: the lane mass is exactly 1
+          const u64 wm = s_wmid[(gout << BS_IN) | (u32)r];
+          u128_add(T, wm << 62, wm >> 2);
+          bins[(pco + __popc(r)) * BS_NTHR] += BS_FULL_COUNTS;
+        } else if (c) {
           const u32 g = (gout << BS_IN) | (u32)r;
           const int pc = pco + __popc(r);
           const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
@@ -321,10 +349,10 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
   }
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
-    wacc[0] = facc_dd(accR);
+    s_acc[warp] = accR;
   }
   __syncthreads();
-  bs_write_partials(W, s_wacc, s_nbins);
+  bs_write_partials(W, s_acc, 1, 1, s_nbins);
 }
 
 #if BS_GRAD
@@ -402,8 +430,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   u128* s_A = (u128*)(s_bins + (BS_L + 1) * BS_NTHR);       // [BS_OUT][NTHR]
   u128* s_red = s_A + (BS_OUT > 0 ? BS_OUT : 1) * BS_NTHR;  // [warps][64] reduced values
   facc* s_acc = (facc*)(s_red + (BS_NTHR / 32) * 64);       // [warps][1 + 2M]: R, then A_k, B_k
-  dd* s_wacc = (dd*)(s_acc + (BS_NTHR / 32) * (1 + 2 * BS_M));  // [warps][1 + M]
-  u64* s_nbins = (u64*)(s_wacc + (BS_NTHR / 32) * (1 + BS_M));
+  u64* s_nbins = (u64*)(s_acc + (BS_NTHR / 32) * (1 + 2 * BS_M));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
   for (int i = tid; i < 4 * 256; i += BS_NTHR) s_tt[i] = thr_tab[i];
@@ -481,9 +508,20 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
           for (int b = 0; b < BS_IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
           const u32 g = (gout << BS_IN) | (u32)r;
           const u32 c = bs_var(e, w) & BS_LANE_MASK;
-          const u32 ct = bs_transpose32(c, tr);
+          // words that are all connected or all cut in every lane add the
+          // same amount to every lane pattern: no lane-arc pair differs
+          const bool mixed = __any_sync(0xffffffffu, c != 0u && c != BS_LANE_MASK);
+          const u32 ct = mixed ? bs_transpose32(c, tr) : 0u;
           const ulonglong2 wv = s_wm[g];
-          if (c) {
+          if (c == BS_LANE_MASK) {
+            // lane mass exactly 1: the walk mass at scale 2^125
+            const u128 x = u128{(wv.x >> 2) | (wv.y << 62), wv.y >> 2};
+            u128_add(T, x.lo, x.hi);
+#pragma unroll
+            for (int b = 0; b < BS_IN; ++b)
+              if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
+            bins[(pco + __popc(r)) * BS_NTHR] += BS_FULL_COUNTS;
+          } else if (c) {
             const int pc = pco + __popc(r);
             const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
             const ulonglong2 t2 = s_lt[2 * 256 + ((c >> 16) & 0xffu)], t3 = s_lt[3 * 256 + (c >> 24)];
@@ -580,21 +618,11 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
   }
-  // ---- once per warp: the accumulators as double-double; walk arcs divide
-  // by p and 1 - p here
-  __syncwarp();
-  dd* wacc = s_wacc + warp * (1 + BS_M);
-  if (lane == 0) wacc[0] = facc_dd(acc[0]);
-  for (int k = lane; k < BS_M; k += 32) {
-    const dd av = facc_dd(acc[1 + 2 * k]), bv = facc_dd(acc[2 + 2 * k]);
-    dd v;
-    if (k >= BS_TOP) v = dd_add(av, dd_neg(bv));
-    else if (k >= BS_WALK0) v = dd_add(dd_mul(av, Q.inv_p[k]), dd_neg(dd_mul(bv, Q.inv_q[k])));
-    else v = av;
-    wacc[1 + k] = v;
-  }
+  // ---- per block: R, then A_k and B_k of every arc; the host forms the
+  // gradient (A - B for prefix arcs, A / p - B / (1 - p) for walk arcs, A
+  // for lane and thread arcs)
   __syncthreads();
-  bs_write_partials(W, s_wacc, s_nbins);
+  bs_write_partials(W, s_acc, 1 + 2 * BS_M, 1 + 2 * BS_M, s_nbins);
 }
 #endif
 )PBAT";
@@ -618,7 +646,10 @@ struct BGraph {
   int gidx, m, nlev, prune;
   int lev_bits[6], lev_off[6];
   int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, tb;
-  int L, top, pad0, pad1;
+  int L, top;
+  u32 lane_mask;
+  int pad0;
+  u64 full_counts;
   u64 binom[64];
 };
 
@@ -686,8 +717,9 @@ __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefi
   for (int g = 0; g < nw; ++g) {
     const u32 c = cw[g * BSB_NTHR];
     if (!c) continue;
-    bins[__popc(g) * BSB_NTHR] += __ldg(ntg + (c & 0xffu)) + __ldg(ntg + 256 + ((c >> 8) & 0xffu)) +
-                                  __ldg(ntg + 512 + ((c >> 16) & 0xffu)) + __ldg(ntg + 768 + (c >> 24));
+    bins[__popc(g) * BSB_NTHR] += c == B.lane_mask ? B.full_counts
+        : __ldg(ntg + (c & 0xffu)) + __ldg(ntg + 256 + ((c >> 8) & 0xffu)) +
+          __ldg(ntg + 512 + ((c >> 16) & 0xffu)) + __ldg(ntg + 768 + (c >> 24));
   }
   const bool thr_on = lane < (1 << B.tb);
   if (thr_on) {
@@ -713,12 +745,24 @@ __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefi
     for (int g = 0; g < nw; ++g) {
       const u32 c = cw[g * BSB_NTHR];
       if (!c) continue;
+      const ulonglong2* wv = (const ulonglong2*)(wmg + (size_t)g * Kp + k0);
+      if (c == B.lane_mask) {
+        // every lane state connected: lane mass exactly 1, the walk mass at
+        // scale 2^125
+#pragma unroll
+        for (int h = 0; h < BSB_KC / 2; ++h) {
+          if (2 * h >= kc) break;
+          const ulonglong2 ww = __ldg(wv + h);
+          u128_add(T[2 * h], ww.x << 62, ww.x >> 2);
+          u128_add(T[2 * h + 1], ww.y << 62, ww.y >> 2);
+        }
+        continue;
+      }
       // tables are padded to an even Kp, so pairs of p-vectors load as 16 bytes
       const ulonglong2* l0 = (const ulonglong2*)(ltg + (size_t)(0 * 256 + (c & 0xffu)) * Kp + k0);
       const ulonglong2* l1 = (const ulonglong2*)(ltg + (size_t)(1 * 256 + ((c >> 8) & 0xffu)) * Kp + k0);
       const ulonglong2* l2 = (const ulonglong2*)(ltg + (size_t)(2 * 256 + ((c >> 16) & 0xffu)) * Kp + k0);
       const ulonglong2* l3 = (const ulonglong2*)(ltg + (size_t)(3 * 256 + (c >> 24)) * Kp + k0);
-      const ulonglong2* wv = (const ulonglong2*)(wmg + (size_t)g * Kp + k0);
 #pragma unroll
       for (int h = 0; h < BSB_KC / 2; ++h) {
         if (2 * h >= kc) break;

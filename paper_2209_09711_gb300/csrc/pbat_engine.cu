@@ -34,9 +34,10 @@ const void* frontier_kernel_ptr(bool grad, bool wide);
 cudaError_t launch_frontier(bool grad, bool wide, int grid, int nthr, size_t smem,
                             cudaStream_t st, const FrontierParams& P, const u128* wmid,
                             const DevWork& W);
-cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int m);
+cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int n_acc, int n_cnt);
 
 struct BsLaunch;
+void bs_finish_grad(const BsLaunch& bl, const dd* acc, int m, double* g_internal);
 BsLaunch* bs_new();
 void bs_delete(BsLaunch* b);
 int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
@@ -361,6 +362,7 @@ struct Job {
   DeviceInfo dev;
   Scratch* scr = nullptr;
   int grid = 0;
+  int n_acc = 0;   // double-double sums per block and in the result
   DevWork W{};
   u128* d_wmid = nullptr;
   // host mirror in pinned memory
@@ -611,15 +613,20 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   grid = std::max(1LL, std::min(grid, need));
   J->grid = (int)grid;
   const int m = g.m;
+  // accumulators per block: the frontier kernel and the bit-sliced R kernel
+  // write R and one value per arc (zeros for R only) or R alone; the fused
+  // bit-sliced kernel writes R and two sums per arc
+  J->n_acc = J->bs ? (bs_grad(*J->bs) ? 1 + 2 * m : 1) : 1 + m;
+  const int n_acc = J->n_acc;
 
   // device scratch layout
   size_t off = 0;
   const size_t o_counter = off; off = up16(off + 8);
   const size_t o_status = off; off = up16(off + 4);
   const size_t o_stats = off; off = up16(off + 3 * 8);
-  const size_t o_part_acc = off; off = up16(off + (size_t)grid * (1 + m) * sizeof(dd));
+  const size_t o_part_acc = off; off = up16(off + (size_t)grid * n_acc * sizeof(dd));
   const size_t o_part_n = off; off = up16(off + (size_t)grid * (m + 1) * 8);
-  const size_t o_out_acc = off; off = up16(off + (size_t)(1 + m) * sizeof(dd));
+  const size_t o_out_acc = off; off = up16(off + (size_t)n_acc * sizeof(dd));
   const size_t o_out_n = off; off = up16(off + (size_t)(m + 1) * 8);
   const size_t o_wmid = off; off = up16(off + wmid.size() * sizeof(u128));
   size_t o_lane = 0, o_thr = 0, o_wmid64 = 0, o_ptab = 0, o_ptabx = 0, o_tab_end = 0;
@@ -634,7 +641,7 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t dbytes = off;
   // host (pinned) layout: results + staging of the walk table
   size_t hoff = 0;
-  const size_t h_acc = hoff; hoff = up16(hoff + (size_t)(1 + m) * sizeof(dd));
+  const size_t h_acc = hoff; hoff = up16(hoff + (size_t)n_acc * sizeof(dd));
   const size_t h_n = hoff; hoff = up16(hoff + (size_t)(m + 1) * 8);
   const size_t h_status = hoff; hoff = up16(hoff + 4);
   const size_t h_stats = hoff; hoff = up16(hoff + 3 * 8);
@@ -720,7 +727,7 @@ int job_launch(Job* J, cudaStream_t st) {
     PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].second, st));
     ++J->n_pending;
   }
-  PBAT_CUDA(launch_reduce(st, J->W, J->grid, J->g.m));
+  PBAT_CUDA(launch_reduce(st, J->W, J->grid, J->n_acc, J->g.m + 1));
   return PBAT_OK;
 }
 
@@ -730,7 +737,7 @@ void job_destroy(Job* J);
 int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* dRdp_out,
              pbat_options* opt) {
   const int m = J->g.m;
-  PBAT_CUDA(cudaMemcpyAsync(J->h_acc, J->W.out_acc, (size_t)(1 + m) * sizeof(dd),
+  PBAT_CUDA(cudaMemcpyAsync(J->h_acc, J->W.out_acc, (size_t)J->n_acc * sizeof(dd),
                             cudaMemcpyDeviceToHost, st));
   PBAT_CUDA(cudaMemcpyAsync(J->h_n, J->W.out_n, (size_t)(m + 1) * 8, cudaMemcpyDeviceToHost, st));
   PBAT_CUDA(cudaMemcpyAsync(J->h_status, J->W.status, 4, cudaMemcpyDeviceToHost, st));
@@ -744,7 +751,7 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
     opt->stats[0] = J->h_stats[0] * item;
     opt->stats[1] = (J->h_stats[1] + J->h_stats[2]) * item;
     opt->stats[2] = J->wmid_bytes;
-    opt->stats[3] = (1 + m) * sizeof(dd) + (m + 1) * 8 + 4 + 24;
+    opt->stats[3] = J->n_acc * sizeof(dd) + (m + 1) * 8 + 4 + 24;
     double ns = 0.0;
     for (size_t i = 0; i < J->n_pending; ++i) {
       float ms = 0.f;
@@ -775,11 +782,18 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
   *R_out = R;
   if (Nk_out)
     for (int k = 0; k <= m; ++k) Nk_out[k] = J->h_n[k];
-  if (dRdp_out)
-    for (int k = 0; k < m; ++k) {
-      const dd v = J->h_acc[1 + k];
-      dRdp_out[J->perm[k]] = v.hi + v.lo;
+  if (dRdp_out) {
+    if (J->bs) {
+      std::vector<double> gi(m);
+      bs_finish_grad(*J->bs, J->h_acc, m, gi.data());
+      for (int k = 0; k < m; ++k) dRdp_out[J->perm[k]] = gi[k];
+    } else {
+      for (int k = 0; k < m; ++k) {
+        const dd v = J->h_acc[1 + k];
+        dRdp_out[J->perm[k]] = v.hi + v.lo;
+      }
     }
+  }
   return PBAT_OK;
 }
 

@@ -300,15 +300,17 @@ __global__ void __launch_bounds__(256) frontier_kernel(const __grid_constant__ F
 // depend on scheduling.
 constexpr int kReduceThreads = 256;
 
-__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevWork W, int nblocks, int m) {
+// Output i sums entry i of every block's partials (n_acc double-double
+// sums and n_cnt counts per block) in a fixed order.
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevWork W, int nblocks, int n_acc, int n_cnt) {
   __shared__ dd s_acc[kReduceThreads];
   __shared__ unsigned long long s_n[kReduceThreads];
   const int i = blockIdx.x, t = threadIdx.x;
   dd s = dd{0.0, 0.0};
   unsigned long long c = 0ull;
   for (int b = t; b < nblocks; b += kReduceThreads) {
-    s = dd_add(s, W.part_acc[(size_t)b * (1 + m) + i]);
-    c += W.part_n[(size_t)b * (m + 1) + i];
+    if (i < n_acc) s = dd_add(s, W.part_acc[(size_t)b * n_acc + i]);
+    if (i < n_cnt) c += W.part_n[(size_t)b * n_cnt + i];
   }
   s_acc[t] = s;
   s_n[t] = c;
@@ -321,8 +323,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevWork W, int n
     __syncthreads();
   }
   if (t == 0) {
-    W.out_acc[i] = s_acc[0];
-    W.out_n[i] = s_n[0];
+    if (i < n_acc) W.out_acc[i] = s_acc[0];
+    if (i < n_cnt) W.out_n[i] = s_n[0];
   }
 }
 
@@ -362,8 +364,8 @@ cudaError_t launch_frontier(bool grad, bool wide, int grid, int nthr, size_t sme
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int m) {
-  reduce_kernel<<<m + 1, kReduceThreads, 0, st>>>(W, nblocks, m);
+cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int n_acc, int n_cnt) {
+  reduce_kernel<<<n_acc > n_cnt ? n_acc : n_cnt, kReduceThreads, 0, st>>>(W, nblocks, n_acc, n_cnt);
   return cudaGetLastError();
 }
 

@@ -37,7 +37,7 @@ const void* frontier_kernel_ptr(bool grad, bool wide);
 cudaError_t launch_frontier(bool grad, bool wide, int grid, int nthr, size_t smem,
                             cudaStream_t st, const FrontierParams& P, const u128* wmid,
                             const DevWork& W);
-cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int m);
+cudaError_t launch_reduce(cudaStream_t st, const DevWork& W, int nblocks, int n_acc, int n_cnt);
 
 constexpr size_t kNoAllocScratchBytes = (size_t)512 << 10;  // 512 KiB
 constexpr int kNoAllocMaxWalkBits = 12;                     // walk table <= 64 KiB
@@ -215,7 +215,7 @@ static int run_noalloc(const GraphIn& g, const double* p, const pbat_options* op
   if ((e = cudaMemcpyAsync((void*)d_wmid, wmid, wmid_bytes, cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemsetAsync(base + kNaCounter, 0, 64, st)) ||
       (e = launch_frontier(false, wide, grid, nthr, smem, st, P, d_wmid, W)) ||
-      (e = launch_reduce(st, W, grid, m)))
+      (e = launch_reduce(st, W, grid, 1 + m, m + 1)))
     return fail(PBAT_ECUDA, "enqueue failed: %s", cudaGetErrorString(e));
   dd acc[1 + kMaxArcs];
   unsigned long long nk[kMaxArcs + 1];

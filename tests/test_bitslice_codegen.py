@@ -29,7 +29,7 @@ def _parse(src):
     inv = inv[:inv.index("\n}\n")]
     var = src[src.index("u32 bs_var"):]
     var = var[:var.index("\n}\n")]
-    return perm, {k: int(v.rstrip("u"), 0) for k, v in defs.items()}, inv, var
+    return perm, {k: int(v.rstrip("ul"), 0) for k, v in defs.items()}, inv, var
 
 
 def _run(body, env):
