@@ -638,8 +638,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
       bl.Q.inv_q[k] = dd_recip_dd(dd_one_minus(pk));
     }
     bl.smem = (size_t)(4 * 256 * 2 + 2 * (1 << bp.L) + 4 * 256 + (bp.L + 1) * bl.nthr) * 8 +
-              (size_t)std::max(L_out, 1) * bl.nthr * 16 + (size_t)(bl.nthr / 32) * 64 * 16 +
-              (size_t)(bl.nthr / 32) * (1 + 2 * m) * 24 + (size_t)(m + 1) * 8;
+              (size_t)std::max(L_out, 1) * bl.nthr * 16 + (size_t)(m + 1) * 8;
   }
   if (bl.smem > (size_t)dev.smem_optin)
     return fail(PBAT_ERANGE, "bit-sliced kernel needs %zu B of shared memory", bl.smem);
@@ -861,7 +860,7 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
                       const DeviceInfo& dev, const std::vector<unsigned long long>& items) {
   int rc;
   E.bg.resize(G);
-  E.Kp = K + (K & 1);
+  E.Kp = (K + 15) & ~15;   // whole chunks of 16 p-vectors per table row
   const int Kp = E.Kp;
   unsigned long long begin = 0;
   size_t lt = 0, nt = 0, wm = 0, pt = 0, th = 0;

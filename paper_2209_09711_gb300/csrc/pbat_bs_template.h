@@ -171,9 +171,11 @@ struct BsParams {
   u64 thw[32];           // thread-pattern masses, fixed point 2^63
   u64 binom[64];
 };
+struct facc;
 struct BsWork {
   u64* counter; u32* status; u64* stats;
   dd* part_acc; u64* part_n; dd* out_acc; u64* out_n;
+  facc* wacc;   // fused kernel: per warp, R and the two sums of every arc
 };
 
 __device__ __forceinline__ u64 bs_timer() {
@@ -213,15 +215,17 @@ __device__ __forceinline__ void bs_init_arcs(u32* a, int lane) {
   for (int b = 0; b < BS_L; ++b) a[BS_WALK0 + b] = 0u;
 }
 
-// 0: walk the item, 1: every state disconnected, 2: every state connected
+// 0: walk the item, 1: every state disconnected, 2: every state connected.
+// One bit-sliced evaluation answers both extremes: bit 0 has every arc below
+// the prefix working, bit 1 every such arc failed (the prefix arcs are the
+// same in every bit).
 __device__ __forceinline__ int bs_prune(const u32* a) {
   u32 u[BS_M];
 #pragma unroll
-  for (int k = 0; k < BS_M; ++k) u[k] = k < BS_TOP ? ~0u : a[k];
-  if (bs_uniform(u) == 0u) return 1;
-#pragma unroll
-  for (int k = 0; k < BS_M; ++k) u[k] = k < BS_TOP ? 0u : a[k];
-  return bs_uniform(u) != 0u ? 2 : 0;
+  for (int k = 0; k < BS_M; ++k) u[k] = k < BS_TOP ? 1u : a[k];
+  const u32 ext = bs_uniform(u);
+  if (!(ext & 1u)) return 1;
+  return (ext & 2u) ? 2 : 0;
 }
 
 __device__ __forceinline__ void bs_flush_bins(u64* bins, u64* s_nbins, int base) {
@@ -417,6 +421,8 @@ __device__ __forceinline__ u32 bs_transpose32(u32 x, const BsTr& t) {
   return x;
 }
 
+static_assert(BS_TOP <= 32, "lane k owns internal arc k");
+
 extern "C" __global__ void __launch_bounds__(BS_NTHR)
 bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGradParams Q,
                const u64* __restrict__ lane_tab, const u64* __restrict__ thr_tab,
@@ -428,18 +434,17 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   u64* s_tt = (u64*)(s_wm + (1 << BS_L));                   // [4][256] thread-pattern masses (2^62)
   u64* s_bins = s_tt + 4 * 256;                             // [L + 1][NTHR]
   u128* s_A = (u128*)(s_bins + (BS_L + 1) * BS_NTHR);       // [BS_OUT][NTHR]
-  u128* s_red = s_A + (BS_OUT > 0 ? BS_OUT : 1) * BS_NTHR;  // [warps][64] reduced values
-  facc* s_acc = (facc*)(s_red + (BS_NTHR / 32) * 64);       // [warps][1 + 2M]: R, then A_k, B_k
-  u64* s_nbins = (u64*)(s_acc + (BS_NTHR / 32) * (1 + 2 * BS_M));
+  u64* s_nbins = (u64*)(s_A + (BS_OUT > 0 ? BS_OUT : 1) * BS_NTHR);
+  // per warp, in global scratch: R, then A_k and B_k of every arc k
+  facc* g_acc = W.wacc + (size_t)blockIdx.x * (BS_NTHR / 32) * (1 + 2 * BS_M);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
   for (int i = tid; i < 4 * 256; i += BS_NTHR) s_tt[i] = thr_tab[i];
   for (int i = tid; i < (1 << BS_L); i += BS_NTHR) s_wm[i] = ((const ulonglong2*)wmid128)[i];
-  for (int i = tid; i < (BS_NTHR / 32) * (1 + 2 * BS_M); i += BS_NTHR) s_acc[i] = facc{u128{0ull, 0ull}, 0, 0};
+  for (int i = tid; i < (BS_NTHR / 32) * (1 + 2 * BS_M); i += BS_NTHR) g_acc[i] = facc{u128{0ull, 0ull}, 0, 0};
   for (int i = tid; i <= BS_M; i += BS_NTHR) s_nbins[i] = 0ull;
   __syncthreads();
-  facc* acc = s_acc + warp * (1 + 2 * BS_M);
-  u128* red = s_red + warp * 64;
+  facc* acc = g_acc + warp * (1 + 2 * BS_M);
   u64* bins = s_bins + tid;
   u128* A = s_A + tid;
   const BsTr tr = bs_tr_init(lane);
@@ -469,6 +474,9 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
       if (pr == 1) { ++n_dead; continue; }
     }
     u128 S;      // sum over the warp of T x thread mass, scale 2^124
+    // warp sums of the internal arc this lane owns (internal arcs are below
+    // 32): the exact pair difference, or for a walk arc A and T - A
+    u128 myX = u128{0ull, 0ull}, myY = u128{0ull, 0ull};
     if (pr == 2) {
       ++n_full;
       for (int j = lane; j <= BS_TOP; j += 32) atomicAdd(&s_nbins[pc_pre + j], P.binom[j]);
@@ -552,7 +560,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
         const u128 d2 = u128_sub(T2, o);
         const u128 v = ((lane >> i) & 1) ? mul64x128_shr64(Q.lw_ex[i][lane], d2.lo, d2.hi) : u128{0ull, 0ull};
         const u128 sv = warp_sum_u128(v);
-        if (lane == 0) red[i] = sv;
+        if (lane == i) myX = sv;
       }
 #pragma unroll
       for (int i = 0; i < BS_TB; ++i) {
@@ -561,7 +569,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
         const u128 v = (((lane >> i) & 1) && thr_on) ? mul64x128_shr64(Q.thw_ex[i][lane], d1.lo, d1.hi)
                                                      : u128{0ull, 0ull};
         const u128 sv = warp_sum_u128(v);
-        if (lane == 0) red[BS_ELL + i] = sv;
+        if (lane == BS_ELL + i) myX = sv;
       }
 #pragma unroll
       for (int b = 0; b < BS_L; ++b) {
@@ -569,9 +577,8 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
         const u128 sa = warp_sum_u128(mul64x128_shr64(thw, Ab.lo, Ab.hi));
         const u128 z = u128_sub(T, Ab);
         const u128 sz = warp_sum_u128(mul64x128_shr64(thw, z.lo, z.hi));
-        if (lane == 0) { red[BS_WALK0 + b] = sa; red[32 + ((BS_WALK0 + b) & 31)] = sz; }
+        if (lane == BS_WALK0 + b) { myX = sa; myY = sz; }
       }
-      __syncwarp();
     }
     // ---- per-arc scaling on the owning lanes (internal arcs lane, lane + 32)
     const mx wpre = bs_prefix_mass(P, ptab, prefix);
@@ -601,8 +608,8 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
         }
         if ((prefix >> j) & 1ull) X = S; else Y = S;
       } else if (pr != 2) {
-        X = red[k];
-        if (k >= BS_WALK0) Y = red[32 + (k & 31)];
+        X = myX;
+        Y = myY;
       } else {
         continue;   // every state of the item connected: no internal arc matters
       }
@@ -622,7 +629,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   // gradient (A - B for prefix arcs, A / p - B / (1 - p) for walk arcs, A
   // for lane and thread arcs)
   __syncthreads();
-  bs_write_partials(W, s_acc, 1 + 2 * BS_M, 1 + 2 * BS_M, s_nbins);
+  bs_write_partials(W, g_acc, 1 + 2 * BS_M, 1 + 2 * BS_M, s_nbins);
 }
 #endif
 )PBAT";
@@ -745,27 +752,26 @@ __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefi
     for (int g = 0; g < nw; ++g) {
       const u32 c = cw[g * BSB_NTHR];
       if (!c) continue;
+      // table rows hold whole chunks of 16 p-vectors (zero past K), so all
+      // loads of a word are unconditional and in flight together
       const ulonglong2* wv = (const ulonglong2*)(wmg + (size_t)g * Kp + k0);
       if (c == B.lane_mask) {
         // every lane state connected: lane mass exactly 1, the walk mass at
         // scale 2^125
 #pragma unroll
         for (int h = 0; h < BSB_KC / 2; ++h) {
-          if (2 * h >= kc) break;
           const ulonglong2 ww = __ldg(wv + h);
           u128_add(T[2 * h], ww.x << 62, ww.x >> 2);
           u128_add(T[2 * h + 1], ww.y << 62, ww.y >> 2);
         }
         continue;
       }
-      // tables are padded to an even Kp, so pairs of p-vectors load as 16 bytes
       const ulonglong2* l0 = (const ulonglong2*)(ltg + (size_t)(0 * 256 + (c & 0xffu)) * Kp + k0);
       const ulonglong2* l1 = (const ulonglong2*)(ltg + (size_t)(1 * 256 + ((c >> 8) & 0xffu)) * Kp + k0);
       const ulonglong2* l2 = (const ulonglong2*)(ltg + (size_t)(2 * 256 + ((c >> 16) & 0xffu)) * Kp + k0);
       const ulonglong2* l3 = (const ulonglong2*)(ltg + (size_t)(3 * 256 + (c >> 24)) * Kp + k0);
 #pragma unroll
       for (int h = 0; h < BSB_KC / 2; ++h) {
-        if (2 * h >= kc) break;
         const ulonglong2 a0 = __ldg(l0 + h), a1 = __ldg(l1 + h), a2 = __ldg(l2 + h), a3 = __ldg(l3 + h);
         const ulonglong2 ww = __ldg(wv + h);
         const u64 sx = a0.x + a1.x + a2.x + a3.x, sy = a0.y + a1.y + a2.y + a3.y;

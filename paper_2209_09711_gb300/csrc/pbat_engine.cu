@@ -628,6 +628,8 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t o_part_n = off; off = up16(off + (size_t)grid * (m + 1) * 8);
   const size_t o_out_acc = off; off = up16(off + (size_t)n_acc * sizeof(dd));
   const size_t o_out_n = off; off = up16(off + (size_t)(m + 1) * 8);
+  const size_t wacc_bytes = (J->bs && bs_grad(*J->bs)) ? (size_t)grid * (nthr / 32) * (1 + 2 * m) * 24 : 0;
+  const size_t o_wacc = off; off = up16(off + wacc_bytes);
   const size_t o_wmid = off; off = up16(off + wmid.size() * sizeof(u128));
   size_t o_lane = 0, o_thr = 0, o_wmid64 = 0, o_ptab = 0, o_ptabx = 0, o_tab_end = 0;
   if (J->bs) {
@@ -662,6 +664,7 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   J->W.part_n = (unsigned long long*)(d + o_part_n);
   J->W.out_acc = (dd*)(d + o_out_acc);
   J->W.out_n = (unsigned long long*)(d + o_out_n);
+  J->W.wacc = wacc_bytes ? (void*)(d + o_wacc) : nullptr;
   J->d_wmid = (u128*)(d + o_wmid);
   J->h_acc = (dd*)(h + h_acc);
   J->h_n = (unsigned long long*)(h + h_n);

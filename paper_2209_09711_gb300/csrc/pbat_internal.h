@@ -43,10 +43,12 @@ struct DevWork {
   unsigned long long* counter;  // work-item ticket
   unsigned int* status;         // bit 0: deadline hit
   unsigned long long* stats;    // [0] walked items, [1] full items, [2] dead items
-  dd* part_acc;                 // [grid][1 + m]: R then dR/dp per internal arc
+  dd* part_acc;                 // [grid][n_acc]: R, then per internal arc dR/dp (frontier)
+                                //   or the two sums A, B (fused bit-sliced kernel)
   unsigned long long* part_n;   // [grid][m + 1]
-  dd* out_acc;                  // [1 + m]
+  dd* out_acc;                  // [n_acc]
   unsigned long long* out_n;    // [m + 1]
+  void* wacc;                   // fused bit-sliced kernel: per-warp accumulators (24 B each)
 };
 
 }  // namespace pbat
