@@ -50,7 +50,8 @@ DEFAULT_WORKLOAD = "grid-3x6"
 # the timed launch is the one the instruction counts below were taken from.
 SHAPES = {
     "grid-3x6": {"fused": (6, 128), "r_only": (6, 128)},
-    "random-directed-n20-m34": {"fused": (8, 256), "r_only": (10, 192)},
+    "random-directed-n20-m34": {"fused": (10, 256), "r_only": (10, 192)},
+    "random-undirected-n24-m40": {"fused": (10, 128), "r_only": (8, 128)},
 }
 
 # Warp instructions executed per state (smsp__inst_executed.sum of one launch
