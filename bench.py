@@ -55,12 +55,26 @@ SHAPES = {
 }
 
 # Warp instructions executed per state (smsp__inst_executed.sum of one launch
-# / 2^m, from ncu) -- the per-unit figure of the issue-rate roofline -- and
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum), keyed
-# by (kernel, workload, L, threads per block).  Source: the summaries under
-# profiles/.
-INST_PER_STATE = {}
-DRAM_BYTES_PER_LAUNCH = {}
+# / 2^m) -- the per-unit figure of the issue-rate roofline -- and DRAM bytes
+# per launch (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# (kernel, workload, L, threads per block); from one ncu --set full capture
+# of the same launch (the --probe command with the same shape).
+INST_PER_STATE = {
+    ("bs_kernel_grad", "grid-3x6", 6, 128): 0.100509,
+    ("bs_kernel", "grid-3x6", 6, 128): 0.054033,
+    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 0.050369,
+    ("bs_kernel", "random-directed-n20-m34", 10, 192): 0.022860,
+    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 0.095397,
+    ("bs_kernel", "random-undirected-n24-m40", 8, 128): 0.065276,
+}
+DRAM_BYTES_PER_LAUNCH = {
+    ("bs_kernel_grad", "grid-3x6", 6, 128): 474112,
+    ("bs_kernel", "grid-3x6", 6, 128): 78080,
+    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 189184,
+    ("bs_kernel", "random-directed-n20-m34", 10, 192): 59136,
+    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 1345536,
+    ("bs_kernel", "random-undirected-n24-m40", 8, 128): 192256,
+}
 
 SM_COUNT = 152
 ISSUE_PER_SM_CLK = 4          # warp instructions per clock per SM (4 schedulers)
