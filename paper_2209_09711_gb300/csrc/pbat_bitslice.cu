@@ -735,8 +735,7 @@ struct BGraphHost {
 
 constexpr int kBsbThreads = 128;
 constexpr int kBsbMaxWalk = 5;  // 2^L connectivity words per thread staged in shared memory
-constexpr int kBsbLimbs = 8;    // 32-bit chunks of a value at scale 2^250, in 64-bit atomics
-constexpr int kBsbScale = 250;
+constexpr int kBsbLimbs = 8;    // 32-bit chunks of a 256-bit value at scale 2^250, in 64-bit atomics
 constexpr int kBsbMaxGraphs = 256;
 
 struct BsBatch {
@@ -841,13 +840,17 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
       "    if (task >= total) break;\n"
       "    int lo = 0, hi = G - 1;\n"
       "    while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (graphs[mid].task_begin <= task) lo = mid; else hi = mid - 1; }\n"
-      "    const BGraph& B = graphs[lo];\n"
-      "    const u64 prefix = task - B.task_begin;\n"
+      "    const BGraph* __restrict__ Bp = graphs + lo;\n"
+      "    const u64 prefix = task - Bp->task_begin;\n"
+      "    const int prune = Bp->prune;\n"
+      "    int st = 0;\n"
       "    switch (lo) {\n";
   for (int r = 0; r < G; ++r)
-    kern += "      case " + std::to_string(r) + ": bsb_item<G" + std::to_string(r) +
-            ">(B, prefix, lane, K, Kp, lt, nt, wm, pt, thw, limbs, nk, bins, cw); break;\n";
-  kern += "    }\n    __syncwarp();\n  }\n}\n";
+    kern += "      case " + std::to_string(r) + ": st = bsb_conn<G" + std::to_string(r) +
+            ">(prefix, lane, prune, cw); break;\n";
+  kern += "    }\n"
+          "    if (st) bsb_finish(Bp, st, prefix, lane, K, Kp, lt, nt, wm, pt, thw, limbs, nk, bins, cw);\n"
+          "    __syncwarp();\n  }\n}\n";
   std::string bt = kBsBatchTemplate;
   const size_t cut = bt.find("//@@BATCH_KERNEL@@");
   src += bt.substr(0, cut) + kern;
@@ -1030,18 +1033,8 @@ static int bsb_enqueue(BsBatch& E, cudaStream_t st, unsigned long long budget_ns
 }
 
 static double bsb_limbs_value(const unsigned long long* limbs) {
-  long long carry = 0;
-  uint32_t chunk[kBsbLimbs + 2];
-  for (int i = 0; i < kBsbLimbs; ++i) {
-    const __int128 v = (__int128)(long long)limbs[i] + carry;
-    chunk[i] = (uint32_t)(v & 0xffffffff);
-    carry = (long long)(v >> 32);
-  }
-  chunk[kBsbLimbs] = (uint32_t)(carry & 0xffffffff);
-  chunk[kBsbLimbs + 1] = (uint32_t)((carry >> 32) & 0xffffffff);
-  dd s = dd{0.0, 0.0};
-  for (int i = kBsbLimbs + 1; i >= 0; --i) s = dd_add(s, dd_make(ldexp((double)chunk[i], 32 * i - kBsbScale)));
-  return s.hi + s.lo;
+  const dd v = limbs256_to_dd(limbs);
+  return v.hi + v.lo;
 }
 
 // Source of the batched module (diagnostic; no device needed).

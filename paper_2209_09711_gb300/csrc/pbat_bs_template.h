@@ -33,25 +33,7 @@ typedef unsigned long long u64;
 #define BS_IN (BS_L >= 2 ? 2 : BS_L)
 #define BS_OUT (BS_L - BS_IN)
 
-struct dd { double hi, lo; };
-__device__ __forceinline__ dd two_sum(double a, double b) {
-  double s = a + b; double bb = s - a; double e = (a - (s - bb)) + (b - bb); return dd{s, e};
-}
-__device__ __forceinline__ dd fast_two_sum(double a, double b) {
-  double s = a + b; double e = b - (s - a); return dd{s, e};
-}
-__device__ __forceinline__ dd two_prod(double a, double b) {
-  double p = a * b; double e = fma(a, b, -p); return dd{p, e};
-}
-__device__ __forceinline__ dd dd_add(dd a, dd b) {
-  dd s = two_sum(a.hi, b.hi); dd t = two_sum(a.lo, b.lo);
-  s.lo += t.hi; s = fast_two_sum(s.hi, s.lo); s.lo += t.lo; return fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
-__device__ __forceinline__ dd dd_mul(dd a, dd b) {
-  dd p = two_prod(a.hi, b.hi); p.lo += a.hi * b.lo + a.lo * b.hi; return fast_two_sum(p.hi, p.lo);
-}
-__device__ __forceinline__ dd dd_ldexp(dd a, int e) { return dd{ldexp(a.hi, e), ldexp(a.lo, e)}; }
+struct dd { double hi, lo; };   // host-side double-double (only carried, never computed here)
 
 struct u128 { u64 lo, hi; };
 __device__ __forceinline__ void u128_add(u128& a, u64 blo, u64 bhi) {
@@ -61,12 +43,6 @@ __device__ __forceinline__ u128 u128_sub(u128 a, u128 b) {
   u128 r;
   asm("sub.cc.u64 %0, %2, %4;\n\tsubc.u64 %1, %3, %5;" : "=l"(r.lo), "=l"(r.hi) : "l"(a.lo), "l"(a.hi), "l"(b.lo), "l"(b.hi));
   return r;
-}
-__device__ __forceinline__ dd u128_to_dd(u128 v) {
-  double h = __ull2double_rd(v.hi);
-  u64 hr = v.hi - (u64)h;
-  dd r = two_sum(ldexp(h, 64), ldexp((double)hr, 64));
-  return dd_add(r, two_sum(ldexp((double)(v.lo >> 32), 32), (double)(v.lo & 0xffffffffull)));
 }
 // (a * b) >> 64 for a 64-bit a and a 128-bit b (the lowest 64 bits dropped)
 __device__ __forceinline__ u128 mul64x128_shr64(u64 a, u64 blo, u64 bhi) {
@@ -99,8 +75,6 @@ __device__ __forceinline__ u128 u128_shr(u128 v, int s) {
   if (s >= 64) return u128{v.hi >> (s - 64), 0ull};
   return u128{(v.lo >> s) | (v.hi << (64 - s)), v.hi >> s};
 }
-// exact 128-bit value as double-double times 2^-e
-__device__ __forceinline__ dd u128_dd_scaled(u128 v, int e) { return dd_ldexp(u128_to_dd(v), -e); }
 
 // Products of arc reliabilities (the prefix masses) as integer floating
 // point: value m * 2^(-63 - e), m in [2^63, 2^64) or m = 0, e >= 0.  A
@@ -133,28 +107,24 @@ __device__ __forceinline__ void facc_add(facc& a, u128 P, int e) {
   }
   if (a.v.hi >> 62) { a.v = u128_shr(a.v, 1); a.E -= 1; }
 }
-// mant (leading 1 at bit 52) * 2^(e - 52), assembled from its bits
-__device__ __forceinline__ double bs_bits_double(u64 mant, int e) {
-  if (e < -1022 || e > 1023) return ldexp((double)mant, e - 52);   // outside the normal range
-  return __longlong_as_double((long long)(((u64)(e + 1023) << 52) | (mant & 0xfffffffffffffull)));
-}
-// the accumulator as a double-double (truncated to 106 bits) with integer
-// operations only
-__device__ __forceinline__ dd facc_to_dd(const facc& a) {
-  u64 hi = a.v.hi, lo = a.v.lo;
-  if (!(hi | lo)) return dd{0.0, 0.0};
-  const int z = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
-  if (z >= 64) { hi = lo << (z - 64); lo = 0ull; }
-  else if (z > 0) { hi = (hi << z) | (lo >> (64 - z)); lo <<= z; }
-  const int e = 4 - z - a.E;               // weight of the leading bit: 2^e
-  const double dh = bs_bits_double(hi >> 11, e);
-  const u64 rh = hi & 0x7ffull, rl = lo;   // the 75 bits below the head
-  if (!(rh | rl)) return dd{dh, 0.0};
-  const int z2 = rh ? __clzll((long long)rh) : 64 + __clzll((long long)rl);
-  u64 nh;
-  if (z2 >= 64) nh = rl << (z2 - 64);
-  else nh = (rh << z2) | (z2 ? (rl >> (64 - z2)) : 0ull);
-  return dd{dh, bs_bits_double(nh >> 11, e - z2)};
+
+// add v * 2^(s - 250) to a 256-bit fixed-point number held as 32-bit chunks
+// in eight 64-bit limbs (the upper halves absorb the carries); v < 2^127 and
+// s <= 129 keep it below 2^256
+__device__ __forceinline__ void bs_limb_add(u64* limbs, u128 v, int s) {
+  if (s < 0) {
+    v = u128_shr(v, -s);
+    s = 0;
+  }
+  if (!(v.lo | v.hi)) return;
+  const int c0 = s >> 5, r = s & 31;
+  const u64 q0 = v.lo << r;
+  const u64 q1 = r ? ((v.hi << r) | (v.lo >> (64 - r))) : v.hi;
+  const u64 q2 = r ? (v.hi >> (64 - r)) : 0ull;
+  const u64 c[5] = {q0 & 0xffffffffull, q0 >> 32, q1 & 0xffffffffull, q1 >> 32, q2};
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    if (c[i] && c0 + i < 8) atomicAdd(&limbs[c0 + i], c[i]);
 }
 
 // N_k counts of one word, packed by lane-popcount class cl = 0..5 into
@@ -175,7 +145,8 @@ struct facc;
 struct BsWork {
   u64* counter; u32* status; u64* stats;
   dd* part_acc; u64* part_n; dd* out_acc; u64* out_n;
-  facc* wacc;   // fused kernel: per warp, R and the two sums of every arc
+  facc* wacc;       // fused kernel: per warp, R and the two sums of every arc
+  u64* out_limbs;   // [n_acc][8]: 256-bit fixed point at scale 2^250, 32 bits per limb
 };
 
 __device__ __forceinline__ u64 bs_timer() {
@@ -241,17 +212,20 @@ __device__ __forceinline__ void bs_flush_bins(u64* bins, u64* s_nbins, int base)
   }
 }
 
-// Per-block partials for the fixed-order reduction: entry i combines the
-// warps' floating accumulators s_acc[w * stride + i] in integer arithmetic and
-// becomes one double-double; then the block's N_k counts.
-__device__ __forceinline__ void bs_write_partials(const BsWork& W, const facc* s_acc, int stride, int n_acc,
-                                                  const u64* s_nbins) {
+// End of a block: entry i combines the warps' floating accumulators
+// s_acc[w * stride + i] in integer arithmetic and adds the sum to the result
+// with integer atomics (every sum is non-negative, and integer addition is
+// exact, so the order of the blocks does not matter); then the block's N_k
+// counts.  The host converts the result once.
+__device__ __forceinline__ void bs_write_out(const BsWork& W, const facc* s_acc, int stride, int n_acc,
+                                             const u64* s_nbins) {
   for (int i = threadIdx.x; i < n_acc; i += BS_NTHR) {
     facc t = s_acc[i];
     for (int w = 1; w < BS_NTHR / 32; ++w) facc_add(t, s_acc[w * stride + i].v, s_acc[w * stride + i].E);
-    W.part_acc[(size_t)blockIdx.x * n_acc + i] = facc_to_dd(t);
+    bs_limb_add(W.out_limbs + 8 * i, t.v, 127 - t.E);   // v * 2^(-123 - E) at scale 2^250
   }
-  for (int i = threadIdx.x; i <= BS_M; i += BS_NTHR) W.part_n[(size_t)blockIdx.x * (BS_M + 1) + i] = s_nbins[i];
+  for (int i = threadIdx.x; i <= BS_M; i += BS_NTHR)
+    if (s_nbins[i]) atomicAdd(&W.out_n[i], s_nbins[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -356,7 +330,7 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
     s_acc[warp] = accR;
   }
   __syncthreads();
-  bs_write_partials(W, s_acc, 1, 1, s_nbins);
+  bs_write_out(W, s_acc, 1, 1, s_nbins);
 }
 
 #if BS_GRAD
@@ -629,7 +603,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   // gradient (A - B for prefix arcs, A / p - B / (1 - p) for walk arcs, A
   // for lane and thread arcs)
   __syncthreads();
-  bs_write_partials(W, g_acc, 1 + 2 * BS_M, 1 + 2 * BS_M, s_nbins);
+  bs_write_out(W, g_acc, 1 + 2 * BS_M, 1 + 2 * BS_M, s_nbins);
 }
 #endif
 )PBAT";
@@ -660,78 +634,124 @@ struct BGraph {
   u64 binom[64];
 };
 
-// add P * 2^(-123 - e) (P < 2^124, e >= 0) to the limbs: a 256-bit fixed
-// point number at scale 2^250, 32 bits per 64-bit limb (the upper halves
-// absorb the carries)
-__device__ __forceinline__ void bsb_limb_add(u64* limbs, u128 P, int e) {
-  int s = 127 - e;
-  if (s < 0) {
-    P = u128_shr(P, -s);
-    s = 0;
-  }
-  if (!(P.lo | P.hi)) return;
-  const int c0 = s >> 5, r = s & 31;
-  const u64 q0 = P.lo << r;
-  const u64 q1 = r ? ((P.hi << r) | (P.lo >> (64 - r))) : P.hi;
-  const u64 q2 = r ? (P.hi >> (64 - r)) : 0ull;
-  const u64 c[5] = {q0 & 0xffffffffull, q0 >> 32, q1 & 0xffffffffull, q1 >> 32, q2};
-#pragma unroll
-  for (int i = 0; i < 5; ++i)
-    if (c[i] && c0 + i < BSB_LIMBS) atomicAdd(&limbs[c0 + i], c[i]);
-}
+// add P * 2^(-123 - e) (P < 2^124, e >= 0) to the 256-bit limbs (scale 2^250)
+__device__ __forceinline__ void bsb_limb_add(u64* limbs, u128 P, int e) { bs_limb_add(limbs, P, 127 - e); }
 
-__device__ __forceinline__ mx bsb_prefix_mass(const BGraph& B, const mx* __restrict__ pt, int k, u64 prefix) {
+// prefix mass of one p-vector: product over the levels of its table t
+__device__ __forceinline__ mx bsb_prefix_mass(const mx* __restrict__ t, int nlev, const int (&lev_bits)[6],
+                                              const int (&lev_off)[6], u64 prefix) {
   mx w = mx{1ull << 63, 0, 0};
   int sh = 0;
-  const mx* t = pt + B.pt_off + (size_t)k * B.pt_size;
-  for (int l = 0; l < B.nlev; ++l) {
-    const u64 v = (prefix >> sh) & ((1ull << B.lev_bits[l]) - 1ull);
-    const mx f = t[B.lev_off[l] + v];
+#pragma unroll
+  for (int l = 0; l < 6; ++l) {
+    if (l >= nlev) break;
+    const u64 v = (prefix >> sh) & ((1ull << lev_bits[l]) - 1ull);
+    const ulonglong2 q = __ldg((const ulonglong2*)(t + lev_off[l] + v));
+    const mx f = mx{q.x, (int)(u32)q.y, 0};
     w = l ? mx_mul(w, f) : f;
-    sh += B.lev_bits[l];
+    sh += lev_bits[l];
   }
   return w;
 }
 
-// An item whose every state connects s to t (monotone prune): its counts are
-// binomials and its mass, per p-vector, is the prefix mass.
-__device__ __noinline__ void bsb_full(const BGraph& B, u64 prefix, int lane, int K, const mx* __restrict__ pt,
-                                      u64* limbs, u64* nk) {
-  const int pc_pre = __popcll((long long)prefix);
-  for (int j = lane; j <= B.top; j += 32) atomicAdd(&nk[B.nk_off + pc_pre + j], B.binom[j]);
-  for (int k = lane; k < K; k += 32) {
-    const mx w = bsb_prefix_mass(B, pt, k, prefix);
-    bsb_limb_add(limbs + ((size_t)B.gidx * K + k) * BSB_LIMBS, mx_prod(w, u128{0ull, 1ull << 60}), w.e);
-  }
+template <class G>
+__device__ __forceinline__ u32 bsb_uniform(const u32* a) {
+  u32 e[G::NCORE > 0 ? G::NCORE : 1];
+  G::inv(a, e);
+  u32 w[G::L > 0 ? G::L : 1];
+#pragma unroll
+  for (int b = 0; b < G::L; ++b) w[b] = a[G::WALK0 + b];
+  return G::var(e, w);
 }
 
-// Everything of an item past connectivity, shared by every network: cw holds
-// this thread's 2^L connectivity words (stride BSB_NTHR), word g for walk
-// state g.  Counts N_k once, then sums the exact fixed-point mass of every
-// p-vector, BSB_KC of them at a time (Eq. 1 restricted to the item): per
-// thread in registers, then over the warp by a reduce-scatter that leaves
-// p-vector kk's item total on lanes 2 idx(kk) and 2 idx(kk) + 1, so that the
-// prefix scaling and the limb additions run on 16 lanes at once.
-__device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefix, int lane, int K, int Kp,
-                                       const u64* __restrict__ lt, const u64* __restrict__ nt,
-                                       const u64* __restrict__ wm, const mx* __restrict__ pt,
-                                       const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins) {
+// The per-network part of one item: its state words, the monotone prune,
+// and the connectivity word of every walk state into cw (stride BSB_NTHR).
+// Returns 0 when every state of the item is cut, 1 when every state is
+// connected, 2 when cw holds the item's words.
+template <class G>
+__device__ __forceinline__ int bsb_conn(u64 prefix, int lane, int prune, u32* cw) {
+  u32 a[G::M];
+#pragma unroll
+  for (int i = 0; i < G::ELL; ++i)
+    a[i] = i == 0 ? 0xAAAAAAAAu : i == 1 ? 0xCCCCCCCCu : i == 2 ? 0xF0F0F0F0u : i == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+#pragma unroll
+  for (int i = 0; i < G::TB; ++i) a[G::ELL + i] = 0u - (u32)((lane >> i) & 1);
+#pragma unroll
+  for (int b = 0; b < G::L; ++b) a[G::WALK0 + b] = 0u;
+#pragma unroll
+  for (int j = 0; j < G::D; ++j) a[G::TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
+  if (prune) {
+    // one evaluation for both extremes: bit 0 has every arc below the prefix
+    // up, the other bits have them all down (the prefix arcs are the same in
+    // every bit)
+    u32 u[G::M];
+#pragma unroll
+    for (int k = 0; k < G::M; ++k) u[k] = k < G::TOP ? 1u : a[k];
+    const u32 ext = bsb_uniform<G>(u);
+    if (!(ext & 1u)) return 0;
+    if (ext & 2u) return 1;
+  }
+  u32 e[G::NCORE > 0 ? G::NCORE : 1];
+  G::inv(a, e);
+#pragma unroll 1
+  for (u32 g = 0; g < (1u << G::L); ++g) {
+    u32 w[G::L > 0 ? G::L : 1];
+#pragma unroll
+    for (int b = 0; b < G::L; ++b) w[b] = 0u - ((g >> b) & 1u);
+    cw[g * BSB_NTHR] = G::var(e, w) & G::LANE_MASK;
+  }
+  return 2;
+}
+// Everything of an item past connectivity, shared by every network (inlined
+// once, in the kernel body): counts N_k, then sums the exact fixed-point
+// mass of every p-vector, BSB_KC of them at a time (Eq. 1 restricted to the
+// item) -- per thread in registers, then over the warp by a reduce-scatter
+// that leaves p-vector kk's item total on lanes 2 idx(kk) and 2 idx(kk) + 1,
+// so that the prefix scaling and the limb additions run on 16 lanes at once.
+// The network's constants are read once into registers.
+__device__ __forceinline__ void bsb_finish(const BGraph* __restrict__ Bp, int st, u64 prefix, int lane, int K,
+                                           int Kp, const u64* __restrict__ lt, const u64* __restrict__ nt,
+                                           const u64* __restrict__ wm, const mx* __restrict__ pt,
+                                           const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins,
+                                           const u32* cw) {
   constexpr int nsh[6] = BS_NK_SHIFTS, nwd[6] = BS_NK_WIDTHS;
-  const int nw = 1 << B.L;
+  const int gidx = Bp->gidx, L = Bp->L, tb = Bp->tb, nlev = Bp->nlev, top = Bp->top;
+  const int lt_off = Bp->lt_off, nt_off = Bp->nt_off, wm_off = Bp->wm_off, pt_off = Bp->pt_off;
+  const int pt_size = Bp->pt_size, thw_off = Bp->thw_off, nk_off = Bp->nk_off;
+  const u32 lane_mask = Bp->lane_mask;
+  const u64 full_counts = Bp->full_counts;
+  int lev_bits[6], lev_off[6];
+#pragma unroll
+  for (int l = 0; l < 6; ++l) {
+    lev_bits[l] = Bp->lev_bits[l];
+    lev_off[l] = Bp->lev_off[l];
+  }
   const int pc_pre = __popcll((long long)prefix);
-  for (int r = 0; r <= B.L; ++r) bins[r * BSB_NTHR] = 0ull;
-  const u64* ntg = nt + B.nt_off;
+  u64* glimbs = limbs + (size_t)gidx * K * BSB_LIMBS;
+  const mx* gpt = pt + pt_off;
+  if (st == 1) {
+    // every state connected: binomial counts, and per p-vector the prefix mass
+    for (int j = lane; j <= top; j += 32) atomicAdd(&nk[nk_off + pc_pre + j], __ldg(&Bp->binom[j]));
+    for (int k = lane; k < K; k += 32) {
+      const mx w = bsb_prefix_mass(gpt + (size_t)k * pt_size, nlev, lev_bits, lev_off, prefix);
+      bsb_limb_add(glimbs + (size_t)k * BSB_LIMBS, mx_prod(w, u128{0ull, 1ull << 60}), w.e);
+    }
+    return;
+  }
+  const int nw = 1 << L;
+  for (int r = 0; r <= L; ++r) bins[r * BSB_NTHR] = 0ull;
+  const u64* ntg = nt + nt_off;
   for (int g = 0; g < nw; ++g) {
     const u32 c = cw[g * BSB_NTHR];
     if (!c) continue;
-    bins[__popc(g) * BSB_NTHR] += c == B.lane_mask ? B.full_counts
+    bins[__popc(g) * BSB_NTHR] += c == lane_mask ? full_counts
         : __ldg(ntg + (c & 0xffu)) + __ldg(ntg + 256 + ((c >> 8) & 0xffu)) +
           __ldg(ntg + 512 + ((c >> 16) & 0xffu)) + __ldg(ntg + 768 + (c >> 24));
   }
-  const bool thr_on = lane < (1 << B.tb);
+  const bool thr_on = lane < (1 << tb);
   if (thr_on) {
-    const int base = B.nk_off + pc_pre + __popc(lane);
-    for (int r = 0; r <= B.L; ++r) {
+    const int base = nk_off + pc_pre + __popc(lane);
+    for (int r = 0; r <= L; ++r) {
       const u64 n = bins[r * BSB_NTHR];
 #pragma unroll
       for (int cl = 0; cl < 6; ++cl) {
@@ -740,8 +760,9 @@ __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefi
       }
     }
   }
-  const u64* ltg = lt + B.lt_off;
-  const u64* wmg = wm + B.wm_off;
+  const u64* ltg = lt + lt_off;
+  const u64* wmg = wm + wm_off;
+  const u64* thg = thw + thw_off + (size_t)lane * Kp;
   // p-vector whose total this lane holds after the reduce-scatter
   const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
   for (int k0 = 0; k0 < K; k0 += BSB_KC) {
@@ -755,7 +776,7 @@ __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefi
       // table rows hold whole chunks of 16 p-vectors (zero past K), so all
       // loads of a word are unconditional and in flight together
       const ulonglong2* wv = (const ulonglong2*)(wmg + (size_t)g * Kp + k0);
-      if (c == B.lane_mask) {
+      if (c == lane_mask) {
         // every lane state connected: lane mass exactly 1, the walk mass at
         // scale 2^125
 #pragma unroll
@@ -782,12 +803,12 @@ __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefi
     // thread-pattern masses (scale 2^124 after this), then the reduce-scatter
 #pragma unroll
     for (int kk = 0; kk < BSB_KC; ++kk) {
-      const u64 tw = (thr_on && kk < kc) ? __ldg(thw + B.thw_off + (size_t)lane * Kp + k0 + kk) : 0ull;
+      const u64 tw = (thr_on && kk < kc) ? __ldg(thg + k0 + kk) : 0ull;
       T[kk] = mul64x128_shr64(tw, T[kk].lo, T[kk].hi);
     }
 #pragma unroll
-    for (int st = 0; st < 4; ++st) {
-      const int o = 16 >> st, n = 8 >> st;
+    for (int st2 = 0; st2 < 4; ++st2) {
+      const int o = 16 >> st2, n = 8 >> st2;
       const bool up = lane & o;
 #pragma unroll
       for (int i = 0; i < n; ++i) {
@@ -803,63 +824,10 @@ __device__ __noinline__ void bsb_accum(const BGraph& B, const u32* cw, u64 prefi
       u128_add(T[0], got.lo, got.hi);
     }
     if (!(lane & 1) && idx < kc) {
-      const mx w = bsb_prefix_mass(B, pt, k0 + idx, prefix);
-      bsb_limb_add(limbs + ((size_t)B.gidx * K + k0 + idx) * BSB_LIMBS, mx_prod(w, T[0]), w.e);
+      const mx w = bsb_prefix_mass(gpt + (size_t)(k0 + idx) * pt_size, nlev, lev_bits, lev_off, prefix);
+      bsb_limb_add(glimbs + (size_t)(k0 + idx) * BSB_LIMBS, mx_prod(w, T[0]), w.e);
     }
   }
-}
-
-template <class G>
-__device__ __forceinline__ u32 bsb_uniform(const u32* a) {
-  u32 e[G::NCORE > 0 ? G::NCORE : 1];
-  G::inv(a, e);
-  u32 w[G::L > 0 ? G::L : 1];
-#pragma unroll
-  for (int b = 0; b < G::L; ++b) w[b] = a[G::WALK0 + b];
-  return G::var(e, w);
-}
-
-// The per-network part of one item: its state words, the monotone prune, and
-// the connectivity word of every walk state into cw.
-template <class G>
-__device__ void bsb_item(const BGraph& B, u64 prefix, int lane, int K, int Kp,
-                         const u64* __restrict__ lt, const u64* __restrict__ nt,
-                         const u64* __restrict__ wm, const mx* __restrict__ pt,
-                         const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins, u32* cw) {
-  u32 a[G::M];
-#pragma unroll
-  for (int i = 0; i < G::ELL; ++i)
-    a[i] = i == 0 ? 0xAAAAAAAAu : i == 1 ? 0xCCCCCCCCu : i == 2 ? 0xF0F0F0F0u : i == 3 ? 0xFF00FF00u : 0xFFFF0000u;
-#pragma unroll
-  for (int i = 0; i < G::TB; ++i) a[G::ELL + i] = 0u - (u32)((lane >> i) & 1);
-#pragma unroll
-  for (int b = 0; b < G::L; ++b) a[G::WALK0 + b] = 0u;
-#pragma unroll
-  for (int j = 0; j < G::D; ++j) a[G::TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
-  if (B.prune) {
-    // one evaluation for both extremes: bit 0 has every arc below the prefix
-    // up, the other bits have them all down (the prefix arcs are the same in
-    // every bit)
-    u32 u[G::M];
-#pragma unroll
-    for (int k = 0; k < G::M; ++k) u[k] = k < G::TOP ? 1u : a[k];
-    const u32 ext = bsb_uniform<G>(u);
-    if (!(ext & 1u)) return;
-    if (ext & 2u) {
-      bsb_full(B, prefix, lane, K, pt, limbs, nk);
-      return;
-    }
-  }
-  u32 e[G::NCORE > 0 ? G::NCORE : 1];
-  G::inv(a, e);
-#pragma unroll 1
-  for (u32 g = 0; g < (1u << G::L); ++g) {
-    u32 w[G::L > 0 ? G::L : 1];
-#pragma unroll
-    for (int b = 0; b < G::L; ++b) w[b] = 0u - ((g >> b) & 1u);
-    cw[g * BSB_NTHR] = G::var(e, w) & G::LANE_MASK;
-  }
-  bsb_accum(B, cw, prefix, lane, K, Kp, lt, nt, wm, pt, thw, limbs, nk, bins);
 }
 //@@BATCH_KERNEL@@
 )PBAT";

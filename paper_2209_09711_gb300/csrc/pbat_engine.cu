@@ -362,7 +362,9 @@ struct Job {
   DeviceInfo dev;
   Scratch* scr = nullptr;
   int grid = 0;
-  int n_acc = 0;   // double-double sums per block and in the result
+  int n_acc = 0;   // accumulated sums: R, then per arc one (frontier) or two (fused bit-sliced)
+  size_t reset_bytes = 64;
+  unsigned long long* h_limbs = nullptr;
   DevWork W{};
   u128* d_wmid = nullptr;
   // host mirror in pinned memory
@@ -621,13 +623,19 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
 
   // device scratch layout
   size_t off = 0;
+  // counter, status, stats and the results sit together: one memset per launch
   const size_t o_counter = off; off = up16(off + 8);
   const size_t o_status = off; off = up16(off + 4);
   const size_t o_stats = off; off = up16(off + 3 * 8);
-  const size_t o_part_acc = off; off = up16(off + (size_t)grid * n_acc * sizeof(dd));
-  const size_t o_part_n = off; off = up16(off + (size_t)grid * (m + 1) * 8);
-  const size_t o_out_acc = off; off = up16(off + (size_t)n_acc * sizeof(dd));
   const size_t o_out_n = off; off = up16(off + (size_t)(m + 1) * 8);
+  const size_t limbs_bytes = J->bs ? (size_t)n_acc * 8 * 8 : 0;
+  const size_t o_out_limbs = off; off = up16(off + limbs_bytes);
+  J->reset_bytes = off;
+  // the frontier kernel: per-block partials and the fixed-order reduction
+  const size_t part_bytes = J->bs ? 0 : (size_t)grid * n_acc * sizeof(dd);
+  const size_t o_part_acc = off; off = up16(off + part_bytes);
+  const size_t o_part_n = off; off = up16(off + (J->bs ? 0 : (size_t)grid * (m + 1) * 8));
+  const size_t o_out_acc = off; off = up16(off + (size_t)n_acc * sizeof(dd));
   const size_t wacc_bytes = (J->bs && bs_grad(*J->bs)) ? (size_t)grid * (nthr / 32) * (1 + 2 * m) * 24 : 0;
   const size_t o_wacc = off; off = up16(off + wacc_bytes);
   const size_t o_wmid = off; off = up16(off + wmid.size() * sizeof(u128));
@@ -644,6 +652,7 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   // host (pinned) layout: results + staging of the walk table
   size_t hoff = 0;
   const size_t h_acc = hoff; hoff = up16(hoff + (size_t)n_acc * sizeof(dd));
+  const size_t h_limbs = hoff; hoff = up16(hoff + limbs_bytes);
   const size_t h_n = hoff; hoff = up16(hoff + (size_t)(m + 1) * 8);
   const size_t h_status = hoff; hoff = up16(hoff + 4);
   const size_t h_stats = hoff; hoff = up16(hoff + 3 * 8);
@@ -664,9 +673,11 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   J->W.part_n = (unsigned long long*)(d + o_part_n);
   J->W.out_acc = (dd*)(d + o_out_acc);
   J->W.out_n = (unsigned long long*)(d + o_out_n);
+  J->W.out_limbs = limbs_bytes ? (unsigned long long*)(d + o_out_limbs) : nullptr;
   J->W.wacc = wacc_bytes ? (void*)(d + o_wacc) : nullptr;
   J->d_wmid = (u128*)(d + o_wmid);
   J->h_acc = (dd*)(h + h_acc);
+  J->h_limbs = (unsigned long long*)(h + h_limbs);
   J->h_n = (unsigned long long*)(h + h_n);
   J->h_status = (unsigned int*)(h + h_status);
   J->h_stats = (unsigned long long*)(h + h_stats);
@@ -708,7 +719,7 @@ int job_upload(Job* J, cudaStream_t st) {
 
 // Launch the enumeration and the reduction (asynchronous).
 int job_launch(Job* J, cudaStream_t st) {
-  PBAT_CUDA(cudaMemsetAsync(J->W.counter, 0, 64, st));  // counter, status, stats
+  PBAT_CUDA(cudaMemsetAsync(J->W.counter, 0, J->reset_bytes, st));  // counter, status, stats, results
   const bool timed = J->n_pending < 65536;
   if (timed && J->n_pending == J->evs.size()) {
     cudaEvent_t a, b;
@@ -730,7 +741,7 @@ int job_launch(Job* J, cudaStream_t st) {
     PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].second, st));
     ++J->n_pending;
   }
-  PBAT_CUDA(launch_reduce(st, J->W, J->grid, J->n_acc, J->g.m + 1));
+  if (!J->bs) PBAT_CUDA(launch_reduce(st, J->W, J->grid, J->n_acc, J->g.m + 1));
   return PBAT_OK;
 }
 
@@ -740,8 +751,11 @@ void job_destroy(Job* J);
 int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* dRdp_out,
              pbat_options* opt) {
   const int m = J->g.m;
-  PBAT_CUDA(cudaMemcpyAsync(J->h_acc, J->W.out_acc, (size_t)J->n_acc * sizeof(dd),
-                            cudaMemcpyDeviceToHost, st));
+  if (J->bs)
+    PBAT_CUDA(cudaMemcpyAsync(J->h_limbs, J->W.out_limbs, (size_t)J->n_acc * 64, cudaMemcpyDeviceToHost, st));
+  else
+    PBAT_CUDA(cudaMemcpyAsync(J->h_acc, J->W.out_acc, (size_t)J->n_acc * sizeof(dd),
+                              cudaMemcpyDeviceToHost, st));
   PBAT_CUDA(cudaMemcpyAsync(J->h_n, J->W.out_n, (size_t)(m + 1) * 8, cudaMemcpyDeviceToHost, st));
   PBAT_CUDA(cudaMemcpyAsync(J->h_status, J->W.status, 4, cudaMemcpyDeviceToHost, st));
   PBAT_CUDA(cudaMemcpyAsync(J->h_stats, J->W.stats, 24, cudaMemcpyDeviceToHost, st));
@@ -749,12 +763,14 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
   if (*J->h_status & 1u)
     return fail(PBAT_ETIMEOUT, "time budget of %.3f s ran out on the device",
                 J->opt_copy.time_budget_s);
+  if (J->bs)
+    for (int i = 0; i < J->n_acc; ++i) J->h_acc[i] = limbs256_to_dd(J->h_limbs + 8 * i);
   if (opt) {
     const unsigned long long item = J->item_states;
     opt->stats[0] = J->h_stats[0] * item;
     opt->stats[1] = (J->h_stats[1] + J->h_stats[2]) * item;
     opt->stats[2] = J->wmid_bytes;
-    opt->stats[3] = J->n_acc * sizeof(dd) + (m + 1) * 8 + 4 + 24;
+    opt->stats[3] = J->n_acc * (J->bs ? 64 : sizeof(dd)) + (m + 1) * 8 + 4 + 24;
     double ns = 0.0;
     for (size_t i = 0; i < J->n_pending; ++i) {
       float ms = 0.f;

@@ -124,6 +124,23 @@ inline MxHost to_mx(dd v) {
   return out;
 }
 
+// A non-negative 256-bit fixed-point number at scale 2^250, held as 32-bit
+// chunks in eight 64-bit limbs whose upper halves carry, as a double-double.
+inline dd limbs256_to_dd(const unsigned long long* limbs) {
+  uint32_t chunk[10];
+  uint128_host carry = 0;
+  for (int i = 0; i < 8; ++i) {
+    const uint128_host v = (uint128_host)limbs[i] + carry;
+    chunk[i] = (uint32_t)(v & 0xffffffffu);
+    carry = v >> 32;
+  }
+  chunk[8] = (uint32_t)(carry & 0xffffffffu);
+  chunk[9] = (uint32_t)(carry >> 32);
+  dd s = dd{0.0, 0.0};
+  for (int i = 9; i >= 0; --i) s = dd_add(s, dd_make(ldexp((double)chunk[i], 32 * i - 250)));
+  return s;
+}
+
 inline dd dd_recip(double x) {
   // Newton step on 1/x in double-double: y1 = y0 + y0 * (1 - x y0)
   const double y0 = 1.0 / x;

@@ -49,6 +49,7 @@ struct DevWork {
   dd* out_acc;                  // [n_acc]
   unsigned long long* out_n;    // [m + 1]
   void* wacc;                   // fused bit-sliced kernel: per-warp accumulators (24 B each)
+  unsigned long long* out_limbs;  // bit-sliced kernels: [n_acc][8] 256-bit fixed point, scale 2^250
 };
 
 }  // namespace pbat

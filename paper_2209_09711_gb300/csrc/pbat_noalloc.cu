@@ -209,6 +209,7 @@ static int run_noalloc(const GraphIn& g, const double* p, const pbat_options* op
   W.part_acc = (dd*)(base + part_off);
   W.part_n = (unsigned long long*)(base + part_off + (size_t)grid * per_block_acc);
   W.wacc = nullptr;   // the frontier kernel keeps its accumulators in registers
+  W.out_limbs = nullptr;
   const u128* d_wmid = (const u128*)(base + kNaWmid);
 
   cudaStream_t st = (cudaStream_t)stream;
