@@ -829,6 +829,10 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
       "  const int lane = threadIdx.x & 31;\n"
       "  u64* bins = s_bins + threadIdx.x;\n"
       "  u32* cw = (u32*)(s_bins + (BSB_LMAX + 1) * BSB_NTHR) + threadIdx.x;\n"
+      "  u64* nkw = s_bins + (BSB_LMAX + 1) * BSB_NTHR + (((size_t)1 << BSB_LMAX) * BSB_NTHR) / 2 +\n"
+      "             (threadIdx.x >> 5) * 65;\n"
+      "  for (int i = lane; i < 65; i += 32) nkw[i] = 0ull;\n"
+      "  int cur = -1;   // network whose counts nkw holds\n"
       "  const u64 t0 = bs_timer();\n"
       "  for (;;) {\n"
       "    u64 task = 0;\n"
@@ -841,6 +845,11 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
       "    int lo = 0, hi = G - 1;\n"
       "    while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (graphs[mid].task_begin <= task) lo = mid; else hi = mid - 1; }\n"
       "    const BGraph* __restrict__ Bp = graphs + lo;\n"
+      "    if (lo != cur) {\n"
+      "      __syncwarp();\n"
+      "      if (cur >= 0) bsb_flush_counts(graphs + cur, nkw, nk, lane);\n"
+      "      cur = lo;\n"
+      "    }\n"
       "    const u64 prefix = task - Bp->task_begin;\n"
       "    const int prune = Bp->prune;\n"
       "    int st = 0;\n"
@@ -849,8 +858,10 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
     kern += "      case " + std::to_string(r) + ": st = bsb_conn<G" + std::to_string(r) +
             ">(prefix, lane, prune, cw); break;\n";
   kern += "    }\n"
-          "    if (st) bsb_finish(Bp, st, prefix, lane, K, Kp, lt, nt, wm, pt, thw, limbs, nk, bins, cw);\n"
-          "    __syncwarp();\n  }\n}\n";
+          "    if (st) bsb_finish(Bp, st, prefix, lane, K, Kp, lt, nt, wm, pt, thw, limbs, nkw, bins, cw);\n"
+          "    __syncwarp();\n  }\n"
+          "  __syncwarp();\n"
+          "  if (cur >= 0) bsb_flush_counts(graphs + cur, nkw, nk, lane);\n}\n";
   std::string bt = kBsBatchTemplate;
   const size_t cut = bt.find("//@@BATCH_KERNEL@@");
   src += bt.substr(0, cut) + kern;
@@ -923,7 +934,8 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   E.o_end = off;
   if ((rc = scratch_acquire(dev.device, E.o_end, E.o_end, &E.scr))) return rc;
   memcpy((char*)E.scr->hmem + E.o_graphs, E.bg.data(), sizeof(BGraphHost) * G);
-  E.smem = (size_t)(E.lmax + 1) * kBsbThreads * 8 + ((size_t)1 << E.lmax) * kBsbThreads * 4;
+  E.smem = (size_t)(E.lmax + 1) * kBsbThreads * 8 + ((size_t)1 << E.lmax) * kBsbThreads * 4 +
+           (size_t)(kBsbThreads / 32) * 65 * 8;
   cudaError_t e = cudaFuncSetAttribute((const void*)E.jit.kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E.smem);
   if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));

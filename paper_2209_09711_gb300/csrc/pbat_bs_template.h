@@ -709,15 +709,29 @@ __device__ __forceinline__ int bsb_conn(u64 prefix, int lane, int prune, u32* cw
 // that leaves p-vector kk's item total on lanes 2 idx(kk) and 2 idx(kk) + 1,
 // so that the prefix scaling and the limb additions run on 16 lanes at once.
 // The network's constants are read once into registers.
+// add the warp's counts of network B (k = 0..m) to the global N_k, then clear
+__device__ __forceinline__ void bsb_flush_counts(const BGraph* __restrict__ B, u64* nkw, u64* nk, int lane) {
+  const int m = B->m, off = B->nk_off;
+  for (int i = lane; i <= m; i += 32) {
+    const u64 v = nkw[i];
+    if (v) atomicAdd(&nk[off + i], v);
+    nkw[i] = 0ull;
+  }
+  __syncwarp();
+}
+
+// N_k counts go to the warp's own array nkw (indexed by k within the
+// network), which the kernel flushes to global memory when the warp moves
+// to another network and at the end.
 __device__ __forceinline__ void bsb_finish(const BGraph* __restrict__ Bp, int st, u64 prefix, int lane, int K,
                                            int Kp, const u64* __restrict__ lt, const u64* __restrict__ nt,
                                            const u64* __restrict__ wm, const mx* __restrict__ pt,
-                                           const u64* __restrict__ thw, u64* limbs, u64* nk, u64* bins,
+                                           const u64* __restrict__ thw, u64* limbs, u64* nkw, u64* bins,
                                            const u32* cw) {
   constexpr int nsh[6] = BS_NK_SHIFTS, nwd[6] = BS_NK_WIDTHS;
   const int gidx = Bp->gidx, L = Bp->L, tb = Bp->tb, nlev = Bp->nlev, top = Bp->top;
   const int lt_off = Bp->lt_off, nt_off = Bp->nt_off, wm_off = Bp->wm_off, pt_off = Bp->pt_off;
-  const int pt_size = Bp->pt_size, thw_off = Bp->thw_off, nk_off = Bp->nk_off;
+  const int pt_size = Bp->pt_size, thw_off = Bp->thw_off;
   const u32 lane_mask = Bp->lane_mask;
   const u64 full_counts = Bp->full_counts;
   int lev_bits[6], lev_off[6];
@@ -731,7 +745,7 @@ __device__ __forceinline__ void bsb_finish(const BGraph* __restrict__ Bp, int st
   const mx* gpt = pt + pt_off;
   if (st == 1) {
     // every state connected: binomial counts, and per p-vector the prefix mass
-    for (int j = lane; j <= top; j += 32) atomicAdd(&nk[nk_off + pc_pre + j], __ldg(&Bp->binom[j]));
+    for (int j = lane; j <= top; j += 32) nkw[pc_pre + j] += __ldg(&Bp->binom[j]);
     for (int k = lane; k < K; k += 32) {
       const mx w = bsb_prefix_mass(gpt + (size_t)k * pt_size, nlev, lev_bits, lev_off, prefix);
       bsb_limb_add(glimbs + (size_t)k * BSB_LIMBS, mx_prod(w, u128{0ull, 1ull << 60}), w.e);
@@ -749,15 +763,24 @@ __device__ __forceinline__ void bsb_finish(const BGraph* __restrict__ Bp, int st
           __ldg(ntg + 512 + ((c >> 16) & 0xffu)) + __ldg(ntg + 768 + (c >> 24));
   }
   const bool thr_on = lane < (1 << tb);
-  if (thr_on) {
-    const int base = nk_off + pc_pre + __popc(lane);
-    for (int r = 0; r <= L; ++r) {
+  {
+    // this thread's counts by r + cl (walk popcount + lane class), then
+    // shared atomics at k = prefix + thread + r + cl
+    u64 c11[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) c11[i] = 0ull;
+#pragma unroll
+    for (int r = 0; r <= 5; ++r) {
+      if (r > L) break;
       const u64 n = bins[r * BSB_NTHR];
 #pragma unroll
-      for (int cl = 0; cl < 6; ++cl) {
-        const u64 v = (n >> nsh[cl]) & ((1ull << nwd[cl]) - 1ull);
-        if (v) atomicAdd(&nk[base + r + cl], v);
-      }
+      for (int cl = 0; cl < 6; ++cl) c11[r + cl] += (n >> nsh[cl]) & ((1ull << nwd[cl]) - 1ull);
+    }
+    if (thr_on) {
+      const int base = pc_pre + __popc(lane);
+#pragma unroll
+      for (int i = 0; i < 11; ++i)
+        if (c11[i]) atomicAdd(&nkw[base + i], c11[i]);
     }
   }
   const u64* ltg = lt + lt_off;
