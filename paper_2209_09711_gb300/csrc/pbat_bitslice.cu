@@ -41,9 +41,9 @@ namespace pbat {
 // Host mirror of BsParams in the kernel source (same field order and types).
 struct BsParamsHost {
   unsigned long long task_lo, n_tasks, budget_ns;
-  int prune, nlev;
-  int lev_bits[6];
-  int lev_off[6];
+  int prune, nlev, ex_shift, pad;
+  int lev_bits[10];
+  int lev_off[10];
   unsigned long long thw[32];
   unsigned long long binom[64];
 };
@@ -539,11 +539,16 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   }
   P.task_lo = lo;
   P.n_tasks = hi - lo;
-  // prefix masses: the d prefix arcs in levels of at most 11 bits; each
-  // entry is the exact double-double product over one level's arcs
-  P.nlev = (bp.d + 10) / 11;
+  // prefix masses: the d prefix arcs in levels of at most 6 bits (fused
+  // kernel: the per-arc excluded tables stay small) or 8 bits (R only); each
+  // entry is the double-double product over the level's arcs, rounded to
+  // the kernels' integer floating point, and a level product on the device
+  // is one integer multiply
+  const int max_bits = grad ? 6 : 8;
+  P.nlev = (bp.d + max_bits - 1) / max_bits;
+  P.ex_shift = max_bits;
   bl.ptab.clear();
-  bl.ptab_ex.assign(grad ? (size_t)bp.d << 11 : 0, MxHost{0, 0, 0});
+  bl.ptab_ex.assign(grad ? (size_t)bp.d << max_bits : 0, MxHost{0, 0, 0});
   for (int l = 0, sh = 0; l < P.nlev; ++l) {
     const int bits = bp.d / P.nlev + (l < bp.d % P.nlev ? 1 : 0);
     P.lev_bits[l] = bits;
@@ -561,7 +566,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
         product_table(p, others, bits - 1, tab.data());
         for (int v = 0; v < (1 << bits); ++v) {
           const int u = (v & ((1 << jj) - 1)) | ((v >> (jj + 1)) << jj);
-          bl.ptab_ex[((size_t)(sh + jj) << 11) + v] = to_mx(tab[u]);
+          bl.ptab_ex[((size_t)(sh + jj) << max_bits) + v] = to_mx(tab[u]);
         }
       }
     sh += bits;

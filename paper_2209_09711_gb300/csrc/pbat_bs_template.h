@@ -136,8 +136,9 @@ __device__ __forceinline__ void bs_limb_add(u64* limbs, u128 v, int s) {
 struct BsParams {
   u64 task_lo, n_tasks, budget_ns;
   int prune, nlev;       // prefix-mass table levels
-  int lev_bits[6];       // prefix bits per level (low level first)
-  int lev_off[6];        // first entry of each level in the prefix table
+  int ex_shift, pad;     // log2 of the excluded-arc table's row length
+  int lev_bits[10];      // prefix bits per level (low level first)
+  int lev_off[10];       // first entry of each level in the prefix table
   u64 thw[32];           // thread-pattern masses, fixed point 2^63
   u64 binom[64];
 };
@@ -576,7 +577,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
         int s2 = 0;
         for (int q = 0; q < P.nlev; ++q) {
           const u64 bits = (prefix >> s2) & ((1ull << P.lev_bits[q]) - 1ull);
-          const mx t = q == l ? ptab_ex[((size_t)j << 11) + bits] : ptab[P.lev_off[q] + bits];
+          const mx t = q == l ? ptab_ex[((size_t)j << P.ex_shift) + bits] : ptab[P.lev_off[q] + bits];
           f = q ? mx_mul(f, t) : t;
           s2 += P.lev_bits[q];
         }

@@ -717,18 +717,48 @@ int job_upload(Job* J, cudaStream_t st) {
   return PBAT_OK;
 }
 
-// Launch the enumeration and the reduction (asynchronous).
+// Timing event pairs are pooled per device: a one-shot call would otherwise
+// create and destroy two events every time.
+static std::mutex g_ev_mu;
+static std::map<int, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> g_ev_pool;
+
+static int event_pair_acquire(int device, std::pair<cudaEvent_t, cudaEvent_t>* out) {
+  {
+    std::lock_guard<std::mutex> lk(g_ev_mu);
+    auto& v = g_ev_pool[device];
+    if (!v.empty()) {
+      *out = v.back();
+      v.pop_back();
+      return PBAT_OK;
+    }
+  }
+  cudaEvent_t a, b;
+  PBAT_CUDA(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return fail(PBAT_ECUDA, "cudaEventCreate failed");
+  }
+  *out = {a, b};
+  return PBAT_OK;
+}
+
+static void event_pairs_release(int device, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& evs) {
+  std::lock_guard<std::mutex> lk(g_ev_mu);
+  auto& v = g_ev_pool[device];
+  for (auto& e : evs) v.push_back(e);
+  evs.clear();
+}
+
+// Launch the enumeration (and, for the frontier kernel, the reduction);
+// asynchronous.
 int job_launch(Job* J, cudaStream_t st) {
   PBAT_CUDA(cudaMemsetAsync(J->W.counter, 0, J->reset_bytes, st));  // counter, status, stats, results
   const bool timed = J->n_pending < 65536;
   if (timed && J->n_pending == J->evs.size()) {
-    cudaEvent_t a, b;
-    PBAT_CUDA(cudaEventCreate(&a));
-    if (cudaEventCreate(&b) != cudaSuccess) {
-      cudaEventDestroy(a);
-      return fail(PBAT_ECUDA, "cudaEventCreate failed");
-    }
-    J->evs.emplace_back(a, b);
+    std::pair<cudaEvent_t, cudaEvent_t> e;
+    const int rc = event_pair_acquire(J->dev.device, &e);
+    if (rc) return rc;
+    J->evs.push_back(e);
   }
   if (timed) PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].first, st));
   if (J->bs)
@@ -819,10 +849,7 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
 void job_destroy(Job* J) {
   if (!J) return;
   if (J->bs) bs_delete(J->bs);
-  for (auto& e : J->evs) {
-    cudaEventDestroy(e.first);
-    cudaEventDestroy(e.second);
-  }
+  event_pairs_release(J->dev.device, J->evs);
   scratch_release(J->scr);
   delete J;
 }
