@@ -476,6 +476,8 @@ int bs_source_for(const GraphIn& g, const double* p, bool grad, const pbat_optio
 struct BsCached {
   BsPlan plan;
   JitEntry jit;
+  size_t smem = 0;   // shared memory the kernel attribute was set for
+  int per_sm = 0;    // resident blocks per SM at that size
 };
 static std::mutex g_bsplan_mu;
 static std::map<std::string, BsCached> g_bsplan;
@@ -513,7 +515,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     const std::string src = bs_source(g, bl.plan, bl.nthr);
     if ((rc = jit_compile(src, dev, grad ? "bs_kernel_grad" : "bs_kernel", &bl.jit))) return rc;
     std::lock_guard<std::mutex> lk(g_bsplan_mu);
-    g_bsplan[key] = BsCached{bl.plan, bl.jit};
+    g_bsplan[key] = BsCached{bl.plan, bl.jit, 0, 0};
   }
   const BsPlan& bp = bl.plan;
   const int m = g.m, top = bp.ell + bp.tb + bp.L;
@@ -647,6 +649,16 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   }
   if (bl.smem > (size_t)dev.smem_optin)
     return fail(PBAT_ERANGE, "bit-sliced kernel needs %zu B of shared memory", bl.smem);
+  {
+    // the shared-memory attribute and the occupancy of a cached kernel are
+    // known after its first preparation
+    std::lock_guard<std::mutex> lk(g_bsplan_mu);
+    auto it = g_bsplan.find(key);
+    if (it != g_bsplan.end() && it->second.per_sm > 0 && it->second.smem == bl.smem) {
+      bl.per_sm = it->second.per_sm;
+      return PBAT_OK;
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute((const void*)bl.jit.kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bl.smem);
   if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
@@ -658,6 +670,12 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     per_sm = 1;
   }
   bl.per_sm = per_sm;
+  std::lock_guard<std::mutex> lk(g_bsplan_mu);
+  auto it = g_bsplan.find(key);
+  if (it != g_bsplan.end()) {
+    it->second.smem = bl.smem;
+    it->second.per_sm = per_sm;
+  }
   return PBAT_OK;
 }
 

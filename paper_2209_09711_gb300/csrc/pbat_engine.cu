@@ -365,6 +365,7 @@ struct Job {
   int n_acc = 0;   // accumulated sums: R, then per arc one (frontier) or two (fused bit-sliced)
   size_t reset_bytes = 64;
   unsigned long long* h_limbs = nullptr;
+  char* h_region = nullptr;   // host mirror of the device result region
   DevWork W{};
   u128* d_wmid = nullptr;
   // host mirror in pinned memory
@@ -500,19 +501,26 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
   }
   const int lmax = std::min(10, std::max(0, g.m - o.range_bits - 10));
   std::vector<int> Ls;
-  for (int L = std::max(0, lmax - 6); L <= lmax; L += 2) Ls.push_back(L);
-  if (Ls.empty() || Ls.back() != lmax) Ls.push_back(lmax);
+  for (int L = std::max(0, lmax - 6); L <= lmax; ++L) Ls.push_back(L);
+  // above 2^34 states the candidates run on the first equal-division block
+  // of 2^34 states (same per-state work, a fraction of the time)
+  const int sub = o.range_bits == 0 ? std::max(0, (int)log2_states(g, o) - 34) : 0;
   cudaStream_t st;
   PBAT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   double best_ms = 1e300;
   int best_L = -1, best_nt = 128;
   for (int L : Ls)
-    for (int nt : {128, 192, 256}) {
+    for (int nt : {64, 128, 192, 256}) {
       pbat_options t = o;
       t.autotune = 0;
       t.walk_bits = L;
       t.block_threads = nt;
       t.time_budget_s = 0;
+      if (sub) {
+        t.range_bits = sub;
+        t.range_lo = 0;
+        t.range_hi = 1;
+      }
       Job* J = nullptr;
       if (job_create(g, p, grad, &t, &J) != PBAT_OK) {
         clear_error();
@@ -650,12 +658,12 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   }
   const size_t dbytes = off;
   // host (pinned) layout: results + staging of the walk table
+  // the first reset_bytes mirror the device's result region (one copy back)
   size_t hoff = 0;
+  const size_t h_region = hoff; hoff = up16(hoff + J->reset_bytes);
+  const size_t h_status = h_region + o_status, h_stats = h_region + o_stats;
+  const size_t h_n = h_region + o_out_n, h_limbs = h_region + o_out_limbs;
   const size_t h_acc = hoff; hoff = up16(hoff + (size_t)n_acc * sizeof(dd));
-  const size_t h_limbs = hoff; hoff = up16(hoff + limbs_bytes);
-  const size_t h_n = hoff; hoff = up16(hoff + (size_t)(m + 1) * 8);
-  const size_t h_status = hoff; hoff = up16(hoff + 4);
-  const size_t h_stats = hoff; hoff = up16(hoff + 3 * 8);
   const size_t h_wmid = hoff; hoff = up16(hoff + wmid.size() * sizeof(u128));
   size_t h_lane = 0;
   if (J->bs) {
@@ -676,6 +684,7 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   J->W.out_limbs = limbs_bytes ? (unsigned long long*)(d + o_out_limbs) : nullptr;
   J->W.wacc = wacc_bytes ? (void*)(d + o_wacc) : nullptr;
   J->d_wmid = (u128*)(d + o_wmid);
+  J->h_region = h + h_region;
   J->h_acc = (dd*)(h + h_acc);
   J->h_limbs = (unsigned long long*)(h + h_limbs);
   J->h_n = (unsigned long long*)(h + h_n);
@@ -781,14 +790,12 @@ void job_destroy(Job* J);
 int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* dRdp_out,
              pbat_options* opt) {
   const int m = J->g.m;
-  if (J->bs)
-    PBAT_CUDA(cudaMemcpyAsync(J->h_limbs, J->W.out_limbs, (size_t)J->n_acc * 64, cudaMemcpyDeviceToHost, st));
-  else
+  // one copy of counter, status, statistics, N_k and (bit-sliced) the
+  // fixed-point results; the frontier kernel's sums come from the reduce
+  if (!J->bs)
     PBAT_CUDA(cudaMemcpyAsync(J->h_acc, J->W.out_acc, (size_t)J->n_acc * sizeof(dd),
                               cudaMemcpyDeviceToHost, st));
-  PBAT_CUDA(cudaMemcpyAsync(J->h_n, J->W.out_n, (size_t)(m + 1) * 8, cudaMemcpyDeviceToHost, st));
-  PBAT_CUDA(cudaMemcpyAsync(J->h_status, J->W.status, 4, cudaMemcpyDeviceToHost, st));
-  PBAT_CUDA(cudaMemcpyAsync(J->h_stats, J->W.stats, 24, cudaMemcpyDeviceToHost, st));
+  PBAT_CUDA(cudaMemcpyAsync(J->h_region, J->W.counter, J->reset_bytes, cudaMemcpyDeviceToHost, st));
   PBAT_CUDA(cudaStreamSynchronize(st));
   if (*J->h_status & 1u)
     return fail(PBAT_ETIMEOUT, "time budget of %.3f s ran out on the device",
@@ -800,7 +807,7 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
     opt->stats[0] = J->h_stats[0] * item;
     opt->stats[1] = (J->h_stats[1] + J->h_stats[2]) * item;
     opt->stats[2] = J->wmid_bytes;
-    opt->stats[3] = J->n_acc * (J->bs ? 64 : sizeof(dd)) + (m + 1) * 8 + 4 + 24;
+    opt->stats[3] = J->reset_bytes + (J->bs ? 0 : J->n_acc * sizeof(dd));
     double ns = 0.0;
     for (size_t i = 0; i < J->n_pending; ++i) {
       float ms = 0.f;
