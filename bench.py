@@ -49,7 +49,7 @@ DEFAULT_WORKLOAD = "grid-3x6"
 # these workloads on GB300; the bench pins them (unless --autotune) so that
 # the timed launch is the one the instruction counts below were taken from.
 SHAPES = {
-    "grid-3x6": {"fused": (6, 128), "r_only": (6, 128)},
+    "grid-3x6": {"fused": (5, 128), "r_only": (5, 64)},
     "random-directed-n20-m34": {"fused": (10, 256), "r_only": (10, 192)},
     "random-undirected-n24-m40": {"fused": (10, 128), "r_only": (8, 128)},
 }

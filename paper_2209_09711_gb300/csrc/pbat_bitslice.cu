@@ -581,21 +581,22 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   dd lw[32];
   for (int j = 0; j < 32; ++j) lw[j] = dd{0.0, 0.0};
   product_table(p, bp.perm.data(), bp.ell, lw);
-  for (int b = 0; b < 4; ++b)
-    for (int v = 0; v < 256; ++v) {
-      dd s = dd{0.0, 0.0};
-      unsigned long long n = 0;
-      for (int k = 0; k < 8; ++k) {
-        if (!((v >> k) & 1)) continue;
-        const int j = 8 * b + k;
-        if (j >= (1 << bp.ell)) continue;
-        s = dd_add(s, lw[j]);
-        n += 1ull << kNkShift[__builtin_popcount((unsigned)j)];
-      }
+  for (int b = 0; b < 4; ++b) {
+    // subset sums by the lowest set bit: one addition per entry
+    dd sb[256];
+    unsigned long long nb[256];
+    sb[0] = dd{0.0, 0.0};
+    nb[0] = 0;
+    for (int v = 1; v < 256; ++v) {
+      const int j = 8 * b + __builtin_ctz((unsigned)v), u = v & (v - 1);
+      const bool on = j < (1 << bp.ell);
+      sb[v] = on ? dd_add(sb[u], lw[j]) : sb[u];
+      nb[v] = nb[u] + (on ? 1ull << kNkShift[__builtin_popcount((unsigned)j)] : 0ull);
       unsigned long long* e = &bl.lane_tab[(b * 256 + v) * 2];
-      e[0] = fixed_u64(s, 62);
-      e[1] = n;
+      e[0] = fixed_u64(sb[v], 62);
+      e[1] = nb[v];
     }
+  }
   const int L_in = std::min(bp.L, 2), L_out = bp.L - L_in;
   if (!grad) {
     bl.wmid.resize((size_t)1 << bp.L);
@@ -609,13 +610,14 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     // excluded-arc masses, reciprocals of the walk arcs' p and 1 - p
     memset(&bl.Q, 0, sizeof bl.Q);
     bl.thr_tab.assign(4 * 256, 0ull);
-    for (int b = 0; b < 4; ++b)
-      for (int v = 0; v < 256; ++v) {
-        dd s = dd{0.0, 0.0};
-        for (int k = 0; k < 8; ++k)
-          if ((v >> k) & 1) s = dd_add(s, tw[8 * b + k]);
-        bl.thr_tab[b * 256 + v] = fixed_u64(s, 62);
+    for (int b = 0; b < 4; ++b) {
+      dd sb[256];
+      sb[0] = dd{0.0, 0.0};
+      for (int v = 1; v < 256; ++v) {
+        sb[v] = dd_add(sb[v & (v - 1)], tw[8 * b + __builtin_ctz((unsigned)v)]);
+        bl.thr_tab[b * 256 + v] = fixed_u64(sb[v], 62);
       }
+    }
     bl.wmid128.resize((size_t)2 << bp.L);
     std::vector<dd> wt((size_t)1 << bp.L);
     product_table(p, bp.perm.data() + bp.ell + bp.tb, bp.L, wt.data());

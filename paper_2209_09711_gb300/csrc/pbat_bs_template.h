@@ -398,6 +398,26 @@ __device__ __forceinline__ u32 bs_transpose32(u32 x, const BsTr& t) {
 
 static_assert(BS_TOP <= 32, "lane k owns internal arc k");
 
+// The prefix factor of internal arc k for this item: for a prefix arc the
+// item's prefix mass without that arc's own factor (its level's entry from
+// the excluded-arc table), otherwise the whole prefix mass.
+__device__ __forceinline__ mx bs_arc_factor(const BsParams& P, const mx* __restrict__ ptab,
+                                            const mx* __restrict__ ptab_ex, u64 prefix, int k, mx wpre) {
+  if (k < BS_TOP) return wpre;
+  const int j = k - BS_TOP;
+  int l = 0, sh = 0;
+  while (sh + P.lev_bits[l] <= j) { sh += P.lev_bits[l]; ++l; }
+  mx f = wpre;
+  int s2 = 0;
+  for (int q = 0; q < P.nlev; ++q) {
+    const u64 bits = (prefix >> s2) & ((1ull << P.lev_bits[q]) - 1ull);
+    const mx t = q == l ? ptab_ex[((size_t)j << P.ex_shift) + bits] : ptab[P.lev_off[q] + bits];
+    f = q ? mx_mul(f, t) : t;
+    s2 += P.lev_bits[q];
+  }
+  return f;
+}
+
 extern "C" __global__ void __launch_bounds__(BS_NTHR)
 bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGradParams Q,
                const u64* __restrict__ lane_tab, const u64* __restrict__ thr_tab,
@@ -428,6 +448,9 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   const u64 thw = thr_on ? P.thw[lane] : 0ull;
   const u64 t_start = bs_timer();
   u64 n_walk = 0, n_full = 0, n_dead = 0;
+  // this lane's accumulators: R (lane 0) and the two sums of internal arc
+  // `lane` in registers; arc lane + 32 (a prefix arc) in the global slots
+  facc accR = facc{u128{0ull, 0ull}, 0, 0}, accA = accR, accB = accR;
   u32 a[BS_M];
   bs_init_arcs(a, lane);
 
@@ -440,6 +463,10 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     task = __shfl_sync(0xffffffffu, task, 0);
     if (task >= P.n_tasks) break;
     const u64 prefix = P.task_lo + task;
+    // the item's prefix factors first: their table loads overlap the walk
+    const mx wpre = bs_prefix_mass(P, ptab, prefix);
+    const mx f0 = bs_arc_factor(P, ptab, ptab_ex, prefix, lane, wpre);
+    const mx f1 = lane + 32 < BS_M ? bs_arc_factor(P, ptab, ptab_ex, prefix, lane + 32, wpre) : wpre;
 #pragma unroll
     for (int j = 0; j < BS_D; ++j) a[BS_TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
     const int pc_pre = __popcll((long long)prefix);
@@ -556,42 +583,29 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
       }
     }
     // ---- per-arc scaling on the owning lanes (internal arcs lane, lane + 32)
-    const mx wpre = bs_prefix_mass(P, ptab, prefix);
-    if (lane == 0) {
-      facc r0 = acc[0];
-      facc_add(r0, mx_prod(wpre, S), wpre.e);
-      acc[0] = r0;
-    }
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int k = lane + 32 * half;
-      if (k >= BS_M) continue;
+    facc_add(accR, mx_prod(wpre, S), wpre.e);
+    {
+      // arc `lane`: a prefix arc goes into A when it works in this item and
+      // into B when it fails (the item's mass without its factor); an
+      // internal arc of a fully connected item has no pair that differs
       u128 X = u128{0ull, 0ull}, Y = u128{0ull, 0ull};
-      mx f = wpre;
-      if (k >= BS_TOP) {
-        // prefix arc: the item's mass without this arc's factor, into A
-        // when the arc works in this item and into B when it fails
-        const int j = k - BS_TOP;
-        int l = 0, sh = 0;
-        while (sh + P.lev_bits[l] <= j) { sh += P.lev_bits[l]; ++l; }
-        int s2 = 0;
-        for (int q = 0; q < P.nlev; ++q) {
-          const u64 bits = (prefix >> s2) & ((1ull << P.lev_bits[q]) - 1ull);
-          const mx t = q == l ? ptab_ex[((size_t)j << P.ex_shift) + bits] : ptab[P.lev_off[q] + bits];
-          f = q ? mx_mul(f, t) : t;
-          s2 += P.lev_bits[q];
+      if (lane >= BS_TOP) {
+        if (lane < BS_M) {
+          if ((prefix >> (lane - BS_TOP)) & 1ull) X = S; else Y = S;
         }
-        if ((prefix >> j) & 1ull) X = S; else Y = S;
       } else if (pr != 2) {
         X = myX;
         Y = myY;
-      } else {
-        continue;   // every state of the item connected: no internal arc matters
       }
-      facc* ak = acc + 1 + 2 * k;
+      facc_add(accA, mx_prod(f0, X), f0.e);
+      facc_add(accB, mx_prod(f0, Y), f0.e);
+    }
+    if (lane + 32 < BS_M) {
+      const int j = lane + 32 - BS_TOP;
+      facc* ak = acc + 1 + 2 * (lane + 32);
       facc va = ak[0], vb = ak[1];
-      facc_add(va, mx_prod(f, X), f.e);
-      facc_add(vb, mx_prod(f, Y), f.e);
+      if ((prefix >> j) & 1ull) facc_add(va, mx_prod(f1, S), f1.e);
+      else facc_add(vb, mx_prod(f1, S), f1.e);
       ak[0] = va;
       ak[1] = vb;
     }
@@ -599,6 +613,11 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   }
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
+    acc[0] = accR;
+  }
+  if (lane < BS_M) {
+    acc[1 + 2 * lane] = accA;
+    acc[2 + 2 * lane] = accB;
   }
   // ---- per block: R, then A_k and B_k of every arc; the host forms the
   // gradient (A - B for prefix arcs, A / p - B / (1 - p) for walk arcs, A

@@ -502,9 +502,9 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
   const int lmax = std::min(10, std::max(0, g.m - o.range_bits - 10));
   std::vector<int> Ls;
   for (int L = std::max(0, lmax - 6); L <= lmax; ++L) Ls.push_back(L);
-  // above 2^34 states the candidates run on the first equal-division block
-  // of 2^34 states (same per-state work, a fraction of the time)
-  const int sub = o.range_bits == 0 ? std::max(0, (int)log2_states(g, o) - 34) : 0;
+  // above 2^37 states the candidates run on the first equal-division block
+  // of 2^37 states (same per-state work, a fraction of the time)
+  const int sub = o.range_bits == 0 ? std::max(0, (int)log2_states(g, o) - 37) : 0;
   cudaStream_t st;
   PBAT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   double best_ms = 1e300;

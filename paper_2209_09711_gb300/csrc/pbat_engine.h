@@ -2,6 +2,7 @@
 #pragma once
 #include <stddef.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <vector>
 
@@ -67,15 +68,29 @@ int device_info(DeviceInfo& out);
 // ---- host numeric helpers (fixed point, double-double) ----
 typedef unsigned __int128 uint128_host;
 
+// x = M * 2^ex2 with an integer M < 2^53, read from the bits of a finite x > 0
+inline void double_parts(double x, uint64_t& M, int& ex2) {
+  uint64_t bits;
+  memcpy(&bits, &x, sizeof bits);
+  const int bexp = (int)((bits >> 52) & 0x7ff);
+  M = bits & ((1ull << 52) - 1);
+  if (bexp) {
+    M |= 1ull << 52;
+    ex2 = bexp - 1075;
+  } else {
+    ex2 = -1074;
+  }
+}
+
 // round(x * 2^e) for a finite double x >= 0 whose result is below 2^128
 inline uint128_host scaled_round_u(double x, int e) {
-  if (x <= 0.0) return 0;
-  int ex;
-  const double mant = frexp(x, &ex);  // x = mant * 2^ex, mant in [0.5, 1)
-  const uint64_t M = (uint64_t)ldexp(mant, 53);
-  const int sh = ex - 53 + e;
+  if (!(x > 0.0)) return 0;
+  uint64_t M;
+  int ex2;
+  double_parts(x, M, ex2);
+  const int sh = ex2 + e;
   if (sh >= 0) return (uint128_host)M << sh;
-  if (-sh >= 64) return (-sh == 64 && M >= ((uint64_t)1 << 63)) ? 1 : 0;
+  if (-sh >= 64) return 0;   // below one half (M < 2^53)
   const uint64_t half = (uint64_t)1 << (-sh - 1);
   return (uint128_host)((M + half) >> (-sh));
 }
@@ -100,8 +115,10 @@ struct MxHost {
 inline MxHost to_mx(dd v) {
   MxHost out{0, 0, 0};
   if (!(v.hi > 0.0)) return out;
-  int k;
-  frexp(v.hi, &k);
+  uint64_t M;
+  int ex2;
+  double_parts(v.hi, M, ex2);
+  const int k = ex2 + 64 - __builtin_clzll(M);   // v.hi in [2^(k-1), 2^k)
   int e = 1 - k;
   uint128_host r = scaled_round_u(v.hi, 64 - k);
   if (v.lo > 0)
