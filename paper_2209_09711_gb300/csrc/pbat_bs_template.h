@@ -448,9 +448,13 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   const u64 thw = thr_on ? P.thw[lane] : 0ull;
   const u64 t_start = bs_timer();
   u64 n_walk = 0, n_full = 0, n_dead = 0;
-  // this lane's accumulators: R (lane 0) and the two sums of internal arc
-  // `lane` in registers; arc lane + 32 (a prefix arc) in the global slots
+#if BS_ACC_REG
+  // short items: this lane's accumulators -- R and the two sums of internal
+  // arc `lane` -- in registers, so an item costs no global round trip; arc
+  // lane + 32 (a prefix arc) stays in the global slots.  Long items keep
+  // them all in the global slots: registers are worth more to the walk.
   facc accR = facc{u128{0ull, 0ull}, 0, 0}, accA = accR, accB = accR;
+#endif
   u32 a[BS_M];
   bs_init_arcs(a, lane);
 
@@ -463,10 +467,12 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     task = __shfl_sync(0xffffffffu, task, 0);
     if (task >= P.n_tasks) break;
     const u64 prefix = P.task_lo + task;
+#if BS_ACC_REG
     // the item's prefix factors first: their table loads overlap the walk
     const mx wpre = bs_prefix_mass(P, ptab, prefix);
     const mx f0 = bs_arc_factor(P, ptab, ptab_ex, prefix, lane, wpre);
     const mx f1 = lane + 32 < BS_M ? bs_arc_factor(P, ptab, ptab_ex, prefix, lane + 32, wpre) : wpre;
+#endif
 #pragma unroll
     for (int j = 0; j < BS_D; ++j) a[BS_TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
     const int pc_pre = __popcll((long long)prefix);
@@ -583,7 +589,18 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
       }
     }
     // ---- per-arc scaling on the owning lanes (internal arcs lane, lane + 32)
-    facc_add(accR, mx_prod(wpre, S), wpre.e);
+#if !BS_ACC_REG
+    const mx wpre = bs_prefix_mass(P, ptab, prefix);
+    const mx f0 = bs_arc_factor(P, ptab, ptab_ex, prefix, lane, wpre);
+    const mx f1 = lane + 32 < BS_M ? bs_arc_factor(P, ptab, ptab_ex, prefix, lane + 32, wpre) : wpre;
+    facc accR, accA, accB;
+    if (lane == 0) accR = acc[0];
+    if (lane < BS_M) {
+      accA = acc[1 + 2 * lane];
+      accB = acc[2 + 2 * lane];
+    }
+#endif
+    if (lane == 0) facc_add(accR, mx_prod(wpre, S), wpre.e);
     {
       // arc `lane`: a prefix arc goes into A when it works in this item and
       // into B when it fails (the item's mass without its factor); an
@@ -600,6 +617,13 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
       facc_add(accA, mx_prod(f0, X), f0.e);
       facc_add(accB, mx_prod(f0, Y), f0.e);
     }
+#if !BS_ACC_REG
+    if (lane == 0) acc[0] = accR;
+    if (lane < BS_M) {
+      acc[1 + 2 * lane] = accA;
+      acc[2 + 2 * lane] = accB;
+    }
+#endif
     if (lane + 32 < BS_M) {
       const int j = lane + 32 - BS_TOP;
       facc* ak = acc + 1 + 2 * (lane + 32);
@@ -613,12 +637,14 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   }
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
-    acc[0] = accR;
   }
+#if BS_ACC_REG
+  if (lane == 0) acc[0] = accR;
   if (lane < BS_M) {
     acc[1 + 2 * lane] = accA;
     acc[2 + 2 * lane] = accB;
   }
+#endif
   // ---- per block: R, then A_k and B_k of every arc; the host forms the
   // gradient (A - B for prefix arcs, A / p - B / (1 - p) for walk arcs, A
   // for lane and thread arcs)
