@@ -438,6 +438,14 @@ static unsigned long long full_counts(int ell) {
   return n;
 }
 
+// The fused kernel keeps each lane's accumulators in registers when the
+// item is short (the per-item global update would be a large share of it)
+// or the per-word connectivity program is small (registers to spare); on
+// GB300: 3x6 grid (L = 5) 70.5 -> 66.7 us, 34-arc directed network (12
+// operations per word) 1.54 -> 1.43 ms, but the 40-arc network (260
+// operations per word) 144.7 -> 157.6 ms, so that one keeps global slots.
+static bool acc_in_registers(const BsPlan& bp) { return bp.L <= 6 || bp.ops_var <= 128; }
+
 static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
   char defs[640];
   const unsigned lane_mask = bp.ell >= 5 ? 0xffffffffu : ((1u << (1 << bp.ell)) - 1u);
@@ -447,7 +455,7 @@ static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
            "#define BS_LANE_MASK 0x%08xu\n#define BS_FULL_COUNTS 0x%016llxull\n#define BS_GRAD %d\n"
            "#define BS_ACC_REG %d\n",
            g.m, bp.ell, bp.tb, bp.L, bp.d, nthr, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, bp.ncore,
-           lane_mask, full_counts(bp.ell), bp.grad ? 1 : 0, bp.L <= 6 ? 1 : 0);
+           lane_mask, full_counts(bp.ell), bp.grad ? 1 : 0, acc_in_registers(bp) ? 1 : 0);
   const std::string tmpl = kBsTemplate;
   const size_t cut = tmpl.find("//@@GENERATED@@");
   return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tmpl.substr(cut);
