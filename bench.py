@@ -60,20 +60,20 @@ SHAPES = {
 # (kernel, workload, L, threads per block); from one ncu --set full capture
 # of the same launch (the --probe command with the same shape).
 INST_PER_STATE = {
-    ("bs_kernel_grad", "grid-3x6", 6, 128): 0.100509,
-    ("bs_kernel", "grid-3x6", 6, 128): 0.054033,
-    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 0.050369,
-    ("bs_kernel", "random-directed-n20-m34", 10, 192): 0.022860,
-    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 0.095397,
-    ("bs_kernel", "random-undirected-n24-m40", 8, 128): 0.065276,
+    ("bs_kernel_grad", "grid-3x6", 5, 128): 0.143722,
+    ("bs_kernel", "grid-3x6", 5, 64): 0.067235,
+    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 0.048997,
+    ("bs_kernel", "random-directed-n20-m34", 10, 192): 0.022853,
+    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 0.098792,
+    ("bs_kernel", "random-undirected-n24-m40", 8, 128): 0.065173,
 }
 DRAM_BYTES_PER_LAUNCH = {
-    ("bs_kernel_grad", "grid-3x6", 6, 128): 474112,
-    ("bs_kernel", "grid-3x6", 6, 128): 78080,
-    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 189184,
-    ("bs_kernel", "random-directed-n20-m34", 10, 192): 59136,
-    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 1345536,
-    ("bs_kernel", "random-undirected-n24-m40", 8, 128): 192256,
+    ("bs_kernel_grad", "grid-3x6", 5, 128): 108544,
+    ("bs_kernel", "grid-3x6", 5, 64): 43520,
+    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 402176,
+    ("bs_kernel", "random-directed-n20-m34", 10, 192): 58368,
+    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 803839,
+    ("bs_kernel", "random-undirected-n24-m40", 8, 128): 66304,
 }
 
 SM_COUNT = 152
