@@ -81,6 +81,13 @@ ISSUE_PER_SM_CLK = 4          # warp instructions per clock per SM (4 schedulers
 SM_MAX_MHZ = 2070.0
 
 
+def workload_config(name: str, net, ws: int, l2: str) -> dict:
+    """The workload as both arms name it in their JSON lines."""
+    return {"workload": name, "n": net.n, "m": net.m, "states": 2**net.m,
+            "outputs": "R, N_k, dR/dp", "directed": bool(net.directed),
+            "parallelism": f"replicas x{ws}", "l2": l2}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -152,7 +159,7 @@ def run_reference(a):
         "ms_per_step": 1000.0 * statistics.mean(walls), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f80/f128 long double",
         "data": "synthetic",
-        "config": {"workload": name, "n": net.n, "m": net.m, "states": 2**net.m},
+        "config": workload_config(name, net, 1, "not applicable: host oracle"),
         "cpu_baseline": {"value": value, "unit": "states/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "states/s", "h2d_bytes_per_step": 0,
@@ -348,10 +355,8 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_f, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u128", "data": "synthetic",
-        "config": {"workload": a.workload, "n": net.n, "m": m, "states": states,
-                   "outputs": "R, N_k, dR/dp", "directed": bool(net.directed),
-                   "l2": "flushed between steps (256 MiB write, outside the timed events)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": workload_config(a.workload, net, ws,
+                                  "flushed between steps (256 MiB write, outside the timed events)"),
         "roofline": roof,
         "fused_shape": shape,
         "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r,
