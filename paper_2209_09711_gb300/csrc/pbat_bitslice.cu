@@ -758,7 +758,7 @@ namespace pbat {
 struct BGraphHost {
   unsigned long long task_begin, n_tasks;
   int gidx, m, nlev, prune;
-  int lev_bits[6], lev_off[6];
+  int lev_bits[8], lev_off[8];
   int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, tb;
   int L, top;
   unsigned lane_mask;
@@ -930,7 +930,7 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
     b.gidx = i;
     b.m = graphs[i].n_arcs;
     b.prune = o.prune ? 1 : 0;
-    b.nlev = (bp.d + 10) / 11;
+    b.nlev = (bp.d + 6) / 7;   // levels of at most 7 bits: small per-p-vector tables
     int off = 0;
     for (int l = 0; l < b.nlev; ++l) {
       b.lev_bits[l] = bp.d / b.nlev + (l < bp.d % b.nlev ? 1 : 0);
@@ -1044,7 +1044,7 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
       MxHost* ptk = pt + b.pt_off + (size_t)k * b.pt_size;
       if (b.nlev == 0) ptk[0] = to_mx(dd_make(1.0));
       for (int l = 0, sh = 0; l < b.nlev; ++l) {
-        dd tab[1 << 11];
+        dd tab[1 << 7];
         product_table(pv, bp.perm.data() + top + sh, b.lev_bits[l], tab);
         for (int v = 0; v < (1 << b.lev_bits[l]); ++v) ptk[b.lev_off[l] + v] = to_mx(tab[v]);
         sh += b.lev_bits[l];

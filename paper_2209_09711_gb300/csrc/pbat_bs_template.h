@@ -671,7 +671,7 @@ static const char* kBsBatchTemplate = R"PBAT(
 struct BGraph {
   u64 task_begin, n_tasks;
   int gidx, m, nlev, prune;
-  int lev_bits[6], lev_off[6];
+  int lev_bits[8], lev_off[8];
   int lt_off, nt_off, wm_off, pt_off, pt_size, thw_off, nk_off, tb;
   int L, top;
   u32 lane_mask;
@@ -684,12 +684,12 @@ struct BGraph {
 __device__ __forceinline__ void bsb_limb_add(u64* limbs, u128 P, int e) { bs_limb_add(limbs, P, 127 - e); }
 
 // prefix mass of one p-vector: product over the levels of its table t
-__device__ __forceinline__ mx bsb_prefix_mass(const mx* __restrict__ t, int nlev, const int (&lev_bits)[6],
-                                              const int (&lev_off)[6], u64 prefix) {
+__device__ __forceinline__ mx bsb_prefix_mass(const mx* __restrict__ t, int nlev, const int (&lev_bits)[8],
+                                              const int (&lev_off)[8], u64 prefix) {
   mx w = mx{1ull << 63, 0, 0};
   int sh = 0;
 #pragma unroll
-  for (int l = 0; l < 6; ++l) {
+  for (int l = 0; l < 8; ++l) {
     if (l >= nlev) break;
     const u64 v = (prefix >> sh) & ((1ull << lev_bits[l]) - 1ull);
     const ulonglong2 q = __ldg((const ulonglong2*)(t + lev_off[l] + v));
@@ -780,9 +780,9 @@ __device__ __forceinline__ void bsb_finish(const BGraph* __restrict__ Bp, int st
   const int pt_size = Bp->pt_size, thw_off = Bp->thw_off;
   const u32 lane_mask = Bp->lane_mask;
   const u64 full_counts = Bp->full_counts;
-  int lev_bits[6], lev_off[6];
+  int lev_bits[8], lev_off[8];
 #pragma unroll
-  for (int l = 0; l < 6; ++l) {
+  for (int l = 0; l < 8; ++l) {
     lev_bits[l] = Bp->lev_bits[l];
     lev_off[l] = Bp->lev_off[l];
   }

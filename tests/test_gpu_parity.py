@@ -195,6 +195,26 @@ def test_directed_34_sampled(pb):
     assert np.max(np.abs(g - full.grad)) <= 1e-13
 
 
+def test_fused_accumulator_placements_against_oracle(pb):
+    """The fused kernel keeps a lane's accumulators in registers for short
+    walks or small connectivity programs and in global slots otherwise: both,
+    with the bit-sliced kernel forced, on sampled 2^19-state divisions of a
+    dense seeded network (16 nodes, 38 arcs: its program at walk 9 is over
+    128 operations per word), against the oracle."""
+    tail, head, rng = synth.random_connected_undirected(16, 38, 4243)
+    net = synth.Network(16, tail, head, synth.uniform_p(rng, 38, 0.85, 0.99), 0, 15, False, "dense-16-38")
+    bits = 19
+    for walk in (4, 9):
+        src = pb.kernel_source(net, pb.options(walk_bits=walk, range_bits=bits), grad=True)
+        want = "1" if walk <= 6 else "0"
+        assert f"#define BS_ACC_REG {want}" in src
+        for d in (7, (1 << bits) - 2):
+            r = run(pb, net, grad=True, algo=pb.ALGO_BITSLICE, walk_bits=walk,
+                    range_bits=bits, range_lo=d, range_hi=d + 1)
+            ref = oracle.enumerate_states(net, prefix_bits=bits, prefix_lo=d, prefix_hi=d + 1, grad=True)
+            check(r, ref, True, f"walk {walk} division {d}")
+
+
 def test_random_40_sampled(pb):
     net = synth.workload_random_24_40()
     _sampled(pb, net, 26, [0, 20_000_000, (1 << 26) - 1], True)
