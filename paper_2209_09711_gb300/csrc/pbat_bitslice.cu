@@ -446,6 +446,14 @@ static unsigned long long full_counts(int ell) {
 // operations per word) 144.7 -> 157.6 ms, so that one keeps global slots.
 static bool acc_in_registers(const BsPlan& bp) { return bp.L <= 6 || bp.ops_var <= 128; }
 
+// Walk arcs unrolled per step (2^in_bits words with compile-time walk words):
+// three give more independent words to the R kernel (GB300: 40-arc network
+// 106.5 -> 87.8 ms, 34-arc directed 541 -> 495 us) and to the fused kernel
+// when its accumulators are in registers (34-arc 1437 -> 1385 us), but the
+// fused kernel with a large program loses registers to them (40-arc 147.4 ->
+// 154 ms) and keeps two.
+static int walk_unroll_bits(const BsPlan& bp) { return !bp.grad || acc_in_registers(bp) ? 3 : 2; }
+
 static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
   char defs[640];
   const unsigned lane_mask = bp.ell >= 5 ? 0xffffffffu : ((1u << (1 << bp.ell)) - 1u);
@@ -453,9 +461,10 @@ static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
            "#define BS_M %d\n#define BS_ELL %d\n#define BS_TB %d\n#define BS_L %d\n#define BS_D %d\n"
            "#define BS_NTHR %d\n#define BS_WALK0 %d\n#define BS_TOP %d\n#define BS_NCORE %d\n"
            "#define BS_LANE_MASK 0x%08xu\n#define BS_FULL_COUNTS 0x%016llxull\n#define BS_GRAD %d\n"
-           "#define BS_ACC_REG %d\n",
+           "#define BS_ACC_REG %d\n#define BS_IN_BITS %d\n",
            g.m, bp.ell, bp.tb, bp.L, bp.d, nthr, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, bp.ncore,
-           lane_mask, full_counts(bp.ell), bp.grad ? 1 : 0, acc_in_registers(bp) ? 1 : 0);
+           lane_mask, full_counts(bp.ell), bp.grad ? 1 : 0, acc_in_registers(bp) ? 1 : 0,
+           walk_unroll_bits(bp));
   const std::string tmpl = kBsTemplate;
   const size_t cut = tmpl.find("//@@GENERATED@@");
   return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tmpl.substr(cut);
@@ -606,7 +615,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
       e[1] = nb[v];
     }
   }
-  const int L_in = std::min(bp.L, 2), L_out = bp.L - L_in;
+  const int L_in = std::min(bp.L, walk_unroll_bits(bp)), L_out = bp.L - L_in;
   if (!grad) {
     bl.wmid.resize((size_t)1 << bp.L);
     std::vector<dd> wt((size_t)1 << bp.L);

@@ -30,7 +30,7 @@ static const char* kBsTemplate = R"PBAT(
 typedef unsigned int u32;
 typedef unsigned long long u64;
 
-#define BS_IN (BS_L >= 2 ? 2 : BS_L)
+#define BS_IN (BS_L >= BS_IN_BITS ? BS_IN_BITS : BS_L)
 #define BS_OUT (BS_L - BS_IN)
 
 struct dd { double hi, lo; };   // host-side double-double (only carried, never computed here)
