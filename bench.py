@@ -60,20 +60,20 @@ SHAPES = {
 # (kernel, workload, L, threads per block); from one ncu --set full capture
 # of the same launch (the --probe command with the same shape).
 INST_PER_STATE = {
-    ("bs_kernel_grad", "grid-3x6", 5, 128): 0.143722,
-    ("bs_kernel", "grid-3x6", 5, 64): 0.067235,
-    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 0.048997,
-    ("bs_kernel", "random-directed-n20-m34", 10, 192): 0.022853,
+    ("bs_kernel_grad", "grid-3x6", 5, 128): 0.140129,
+    ("bs_kernel", "grid-3x6", 5, 64): 0.064481,
+    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 0.044515,
+    ("bs_kernel", "random-directed-n20-m34", 10, 192): 0.020959,
     ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 0.098792,
-    ("bs_kernel", "random-undirected-n24-m40", 8, 128): 0.065173,
+    ("bs_kernel", "random-undirected-n24-m40", 10, 128): 0.051793,
 }
 DRAM_BYTES_PER_LAUNCH = {
-    ("bs_kernel_grad", "grid-3x6", 5, 128): 108544,
-    ("bs_kernel", "grid-3x6", 5, 64): 43520,
-    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 402176,
-    ("bs_kernel", "random-directed-n20-m34", 10, 192): 58368,
-    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 803839,
-    ("bs_kernel", "random-undirected-n24-m40", 8, 128): 66304,
+    ("bs_kernel_grad", "grid-3x6", 5, 128): 116480,
+    ("bs_kernel", "grid-3x6", 5, 64): 45824,
+    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 665856,
+    ("bs_kernel", "random-directed-n20-m34", 10, 192): 60160,
+    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 801024,
+    ("bs_kernel", "random-undirected-n24-m40", 10, 128): 158464,
 }
 
 SM_COUNT = 152
