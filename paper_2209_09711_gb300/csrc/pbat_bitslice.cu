@@ -461,10 +461,10 @@ static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
            "#define BS_M %d\n#define BS_ELL %d\n#define BS_TB %d\n#define BS_L %d\n#define BS_D %d\n"
            "#define BS_NTHR %d\n#define BS_WALK0 %d\n#define BS_TOP %d\n#define BS_NCORE %d\n"
            "#define BS_LANE_MASK 0x%08xu\n#define BS_FULL_COUNTS 0x%016llxull\n#define BS_GRAD %d\n"
-           "#define BS_ACC_REG %d\n#define BS_IN_BITS %d\n",
+           "#define BS_ACC_REG %d\n#define BS_IN_BITS %d\n#define BS_THR_MASK 0x%08xu\n",
            g.m, bp.ell, bp.tb, bp.L, bp.d, nthr, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, bp.ncore,
            lane_mask, full_counts(bp.ell), bp.grad ? 1 : 0, acc_in_registers(bp) ? 1 : 0,
-           walk_unroll_bits(bp));
+           walk_unroll_bits(bp), bp.tb >= 5 ? 0xffffffffu : ((1u << (1 << bp.tb)) - 1u));
   const std::string tmpl = kBsTemplate;
   const size_t cut = tmpl.find("//@@GENERATED@@");
   return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tmpl.substr(cut);

@@ -548,7 +548,10 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
               if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
             bins[pc * BS_NTHR] += t0.y + t1.y + t2.y + t3.y;
           }
-          if (ct) {
+          if (ct == BS_THR_MASK) {
+            // every thread pattern connected: thread mass exactly 1
+            u128_add(T2, (wv.x >> 2) | (wv.y << 62), wv.y >> 2);
+          } else if (ct) {
             const u64 s2 = s_tt[ct & 0xffu] + s_tt[256 + ((ct >> 8) & 0xffu)] +
                            s_tt[512 + ((ct >> 16) & 0xffu)] + s_tt[768 + (ct >> 24)];
             const u128 x2 = mul64x128_shr64(s2, wv.x, wv.y);
