@@ -59,11 +59,23 @@ __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int m) {
   r.hi = __shfl_xor_sync(0xffffffffu, v.hi, m);
   return r;
 }
-// exact sum over the warp (every lane gets it): the value in five chunks of
-// at most 26 bits, whose 32-lane sums fit 31 bits, one hardware warp
-// reduction each, recombined in 128-bit arithmetic (GB300, against five
-// rounds of 128-bit shuffles: 40-arc R kernel 87.7 -> 73.0 ms, 34-arc
-// directed 490 -> 472 us)
+// exact sum over the warp (every lane gets it)
+#if defined(BS_GRAD) && BS_GRAD && !BS_ACC_REG
+// the fused kernel with a large connectivity program: five rounds of 128-bit
+// shuffles (the hardware reductions below measured 2% slower there)
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const u128 w = shfl_xor_u128(v, o);
+    u128_add(v, w.lo, w.hi);
+  }
+  return v;
+}
+#else
+// the value in five chunks of at most 26 bits, whose 32-lane sums fit 31
+// bits, one hardware warp reduction each, recombined in 128-bit arithmetic
+// (GB300, against five rounds of 128-bit shuffles: 40-arc R kernel 87.7 ->
+// 73.0 ms, 34-arc directed 490 -> 472 us)
 __device__ __forceinline__ u128 warp_sum_u128(u128 v) {
   const u32 c0 = (u32)(v.lo & 0x3ffffffull), c1 = (u32)((v.lo >> 26) & 0x3ffffffull);
   const u32 c2 = (u32)(((v.lo >> 52) | (v.hi << 12)) & 0x3ffffffull);
@@ -78,6 +90,7 @@ __device__ __forceinline__ u128 warp_sum_u128(u128 v) {
   u128_add(r, 0ull, s4 << 40);
   return r;
 }
+#endif
 
 __device__ __forceinline__ u128 u128_shr(u128 v, int s) {
   if (s <= 0) return v;
