@@ -51,7 +51,7 @@ DEFAULT_WORKLOAD = "grid-3x6"
 SHAPES = {
     "grid-3x6": {"fused": (5, 128), "r_only": (5, 64)},
     "random-directed-n20-m34": {"fused": (10, 256), "r_only": (10, 192)},
-    "random-undirected-n24-m40": {"fused": (10, 128), "r_only": (10, 256)},
+    "random-undirected-n24-m40": {"fused": (10, 160), "r_only": (10, 224)},
 }
 
 # Warp instructions executed per state (smsp__inst_executed.sum of one launch
