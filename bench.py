@@ -60,20 +60,20 @@ SHAPES = {
 # (kernel, workload, L, threads per block); from one ncu --set full capture
 # of the same launch (the --probe command with the same shape).
 INST_PER_STATE = {
-    ("bs_kernel_grad", "grid-3x6", 5, 128): 0.140129,
-    ("bs_kernel", "grid-3x6", 5, 64): 0.064481,
-    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 0.044515,
-    ("bs_kernel", "random-directed-n20-m34", 10, 192): 0.020959,
-    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 0.098792,
-    ("bs_kernel", "random-undirected-n24-m40", 10, 128): 0.051793,
+    ("bs_kernel_grad", "grid-3x6", 5, 128): 0.139708,
+    ("bs_kernel", "grid-3x6", 5, 64): 0.063786,
+    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 0.042332,
+    ("bs_kernel", "random-directed-n20-m34", 10, 192): 0.020323,
+    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 160): 0.093555,
+    ("bs_kernel", "random-undirected-n24-m40", 10, 224): 0.053999,
 }
 DRAM_BYTES_PER_LAUNCH = {
-    ("bs_kernel_grad", "grid-3x6", 5, 128): 116480,
-    ("bs_kernel", "grid-3x6", 5, 64): 45824,
-    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 665856,
-    ("bs_kernel", "random-directed-n20-m34", 10, 192): 60160,
-    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 128): 801024,
-    ("bs_kernel", "random-undirected-n24-m40", 10, 128): 158464,
+    ("bs_kernel_grad", "grid-3x6", 5, 128): 114176,
+    ("bs_kernel", "grid-3x6", 5, 64): 43264,
+    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 150784,
+    ("bs_kernel", "random-directed-n20-m34", 10, 192): 57600,
+    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 160): 1110528,
+    ("bs_kernel", "random-undirected-n24-m40", 10, 224): 279296,
 }
 
 SM_COUNT = 152
