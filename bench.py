@@ -373,7 +373,7 @@ def run_ours(a):
         "cpu_baseline": cpu,
         "e2e": {"value": ws * states / e2e_s, "unit": "states/s",
                 "h2d_bytes_per_step": int(r.stats[2]), "d2h_bytes_per_step": int(r.stats[3])},
-        "gpu_launches": 2 * a.steps,
+        "gpu_launches": int(res_f.stats[5]),
         "clocks": clocks,
         "wall_s_timed": wall_f,
     }

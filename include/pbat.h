@@ -82,7 +82,8 @@ typedef struct pbat_options {
                            prune, [2] bytes copied host -> device, [3] bytes copied
                            device -> host, [4] summed device time in ns of the
                            enumeration kernel over the launches since the last read (CUDA
-                           events on the launch stream), [5] kernels launched, [6] work
+                           events on the launch stream), [5] kernels launched (one per
+                           bit-sliced launch; the frontier kernel adds a reduce), [6] work
                            items per launch, [7] launches timed in [4] */
 } pbat_options;
 

@@ -820,7 +820,7 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
         cudaGetLastError();
     }
     opt->stats[4] = (unsigned long long)ns;
-    opt->stats[5] = 2 * J->n_pending;
+    opt->stats[5] = (J->bs ? 1 : 2) * J->n_pending;   // the frontier kernel adds its reduce
     opt->stats[6] = J->n_items;
     opt->stats[7] = J->n_pending;
   }
