@@ -150,9 +150,6 @@ __device__ __forceinline__ void bs_limb_add(u64* limbs, u128 v, int s) {
     if (c[i] && c0 + i < 8) atomicAdd(&limbs[c0 + i], c[i]);
 }
 
-// popcount of a compile-time constant (unrolled walk index)
-__host__ __device__ constexpr int bs_popc_const(int r) { return r ? (r & 1) + bs_popc_const(r >> 1) : 0; }
-
 // N_k counts of one word, packed by lane-popcount class cl = 0..5 into
 // fields of 8, 11, 12, 12, 11 and 8 bits: wide enough for one item's sum
 // over 2^L words with L <= 10 (at most C(10,5) * C(5,cl) per field).
@@ -323,11 +320,6 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
       u32 w[BS_L > 0 ? BS_L : 1];
 #pragma unroll
       for (int b = 0; b < BS_OUT; ++b) w[BS_IN + b] = 0u - ((gout >> b) & 1u);
-      // this step's counts by inner popcount, in registers: the words of an
-      // unrolled block would otherwise chain read-modify-writes of one bin
-      u64 cnt[BS_IN + 1];
-#pragma unroll
-      for (int i = 0; i <= BS_IN; ++i) cnt[i] = 0ull;
 #pragma unroll
       for (int r = 0; r < (1 << BS_IN); ++r) {
 #pragma unroll
@@ -337,20 +329,18 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
           // every lane state connected: the lane mass is exactly 1
           const u64 wm = s_wmid[(gout << BS_IN) | (u32)r];
           u128_add(T, wm << 62, wm >> 2);
-          cnt[bs_popc_const(r)] += BS_FULL_COUNTS;
+          bins[(pco + __popc(r)) * BS_NTHR] += BS_FULL_COUNTS;
         } else if (c) {
           const u32 g = (gout << BS_IN) | (u32)r;
+          const int pc = pco + __popc(r);
           const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
           const ulonglong2 t2 = s_lt[2 * 256 + ((c >> 16) & 0xffu)], t3 = s_lt[3 * 256 + (c >> 24)];
           const u64 sR = t0.x + t1.x + t2.x + t3.x;
           const u64 wm = s_wmid[g];
           u128_add(T, sR * wm, __umul64hi(sR, wm));
-          cnt[bs_popc_const(r)] += t0.y + t1.y + t2.y + t3.y;
+          bins[pc * BS_NTHR] += t0.y + t1.y + t2.y + t3.y;
         }
       }
-#pragma unroll
-      for (int i = 0; i <= BS_IN; ++i)
-        if (cnt[i]) bins[(pco + i) * BS_NTHR] += cnt[i];
     }
     if (thr_on) bs_flush_bins(bins, s_nbins, pc_pre + pc_thr);
     // item total: exact warp sum of T x thread mass (scale 2^124), times the
@@ -551,9 +541,6 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
         u32 w[BS_L > 0 ? BS_L : 1];
 #pragma unroll
         for (int b = 0; b < BS_OUT; ++b) w[BS_IN + b] = 0u - ((gout >> b) & 1u);
-        u64 cnt[BS_IN + 1];   // this step's counts by inner popcount
-#pragma unroll
-        for (int i = 0; i <= BS_IN; ++i) cnt[i] = 0ull;
 #pragma unroll
         for (int r = 0; r < (1 << BS_IN); ++r) {
 #pragma unroll
@@ -572,8 +559,9 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
 #pragma unroll
             for (int b = 0; b < BS_IN; ++b)
               if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
-            cnt[bs_popc_const(r)] += BS_FULL_COUNTS;
+            bins[(pco + __popc(r)) * BS_NTHR] += BS_FULL_COUNTS;
           } else if (c) {
+            const int pc = pco + __popc(r);
             const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
             const ulonglong2 t2 = s_lt[2 * 256 + ((c >> 16) & 0xffu)], t3 = s_lt[3 * 256 + (c >> 24)];
             const u128 x = mul64x128_shr64(t0.x + t1.x + t2.x + t3.x, wv.x, wv.y);
@@ -581,7 +569,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
 #pragma unroll
             for (int b = 0; b < BS_IN; ++b)
               if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
-            cnt[bs_popc_const(r)] += t0.y + t1.y + t2.y + t3.y;
+            bins[pc * BS_NTHR] += t0.y + t1.y + t2.y + t3.y;
           }
           if (ct == BS_THR_MASK) {
             // every thread pattern connected: thread mass exactly 1
@@ -593,9 +581,6 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
             u128_add(T2, x2.lo, x2.hi);
           }
         }
-#pragma unroll
-        for (int i = 0; i <= BS_IN; ++i)
-          if (cnt[i]) bins[(pco + i) * BS_NTHR] += cnt[i];
       }
 #pragma unroll
       for (int b = 0; b < BS_OUT; ++b)
