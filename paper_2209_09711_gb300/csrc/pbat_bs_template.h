@@ -684,13 +684,15 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
 // Batched: every network's connectivity program is a struct of static
 // functions (inv, var) with its sizes as constants; one persistent kernel
 // takes (network, prefix) items from one ticket -- networks with the most
-// items first -- and switches to that network's item function.  That
-// function only stages the item's 2^L connectivity words in shared memory;
-// one shared accumulate (compiled once, so the module's compile time barely
-// grows with the number of networks) weights each word by every p-vector,
-// 16 at a time in registers (byte tables interleaved by p-vector, read
-// through L1); per item and p-vector the result is added exactly into a
-// 160-bit accumulator of five 64-bit limbs with integer atomics.
+// items first -- and switches to that network's connectivity function
+// (bsb_conn), which only stages the item's 2^L connectivity words in shared
+// memory.  The accumulate (bsb_finish) is written once in the kernel body,
+// so the module's compile time barely grows with the number of networks: it
+// weights each word by every p-vector, 16 at a time in registers (byte
+// tables interleaved by p-vector, read through L1), and adds each item's
+// mass per p-vector exactly into a 256-bit fixed-point number (eight 32-bit
+// chunks in 64-bit limbs) with integer atomics.  N_k counts collect per warp
+// in shared memory.
 static const char* kBsBatchTemplate = R"PBAT(
 #define BSB_LIMBS 8
 #define BSB_KC 16
