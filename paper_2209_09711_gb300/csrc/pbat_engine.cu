@@ -5,10 +5,15 @@
 //   validate  -> reject what the problem statement excludes (Sec. 2.4)
 //   plan      -> choose which arcs are prefix / walk / lane arcs and how many
 //                of each (STEP 0-1: the equal division of Sec. 4.3)
-//   tables    -> fixed-point walk masses, lane masses, reciprocals
-//   launch    -> frontier kernel over all work items (STEP 2), then the
-//                fixed-order reduction of block partials (STEP 3)
-//   read back -> R, N_k and dR/dp in input arc order
+//   tables    -> fixed-point walk masses, lane masses, prefix masses,
+//                reciprocals
+//   launch    -> the bit-sliced or the frontier kernel over all work items
+//                (STEP 2); the bit-sliced kernels add their block sums into
+//                256-bit fixed-point results with integer atomics, the
+//                frontier kernel is followed by the fixed-order reduction of
+//                its block partials (STEP 3)
+//   read back -> R, N_k and dR/dp in input arc order (the fused bit-sliced
+//                kernel's per-arc sums become dR/dp here)
 #include <cuda_runtime.h>
 
 #include <algorithm>
