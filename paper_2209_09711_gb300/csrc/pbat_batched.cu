@@ -1,4 +1,8 @@
-// pbat_batched.cu -- many networks, many p-vectors, one persistent launch.
+// pbat_batched.cu -- many networks, many p-vectors, one persistent launch:
+// the entry point, and the frontier (one state per thread) variant.  The
+// default path is the bit-sliced batched module of pbat_bitslice.cu; this
+// variant runs on request (PBAT_ALGO_FRONTIER), past that module's limits,
+// and as the independent cross-check of its tests.
 //
 // The work items of every network (its prefix values, Sec. 4.3 equal
 // division) are laid end to end, networks with the most items first, and a
