@@ -1100,6 +1100,51 @@ int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o
   return bsb_source(E, G, graphs, K, o, items, out);
 }
 
+// The batch's walk length (split depth: each network's items are its
+// prefixes of d = m - 10 - L arcs): every candidate L in {3, 4, 5} builds its
+// module and runs the batch once; the fastest launch wins.  -1 keeps the
+// planner's default.
+static int bsb_tune_walk(int G, const pbat_graph* graphs, int K, const double* p,
+                         const pbat_options& o, cudaStream_t st, const DeviceInfo& dev) {
+  double best_ms = 1e300;
+  int best = -1;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    cudaGetLastError();
+    return -1;
+  }
+  for (int L = 3; L <= kBsbMaxWalk; ++L) {
+    pbat_options t = o;
+    t.walk_bits = L;
+    t.time_budget_s = 0;
+    BsBatch T;
+    if (bsb_build(T, G, graphs, K, t, dev) != PBAT_OK) {
+      if (T.scr) scratch_release(T.scr);
+      clear_error();
+      continue;
+    }
+    bsb_tables(T, graphs, p);
+    bool ok = cudaMemcpyAsync(T.scr->dmem, T.scr->hmem, T.o_upload_end, cudaMemcpyHostToDevice, st) ==
+              cudaSuccess;
+    ok = ok && cudaEventRecord(a, st) == cudaSuccess && bsb_enqueue(T, st, 0) == PBAT_OK &&
+         cudaEventRecord(b, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+    float ms = 0.f;
+    if (ok && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = L;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      clear_error();
+    }
+    scratch_release(T.scr);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
 // R (and N_k) of a batch with the bit-sliced batched kernel; returns
 // PBAT_ENOTSUP when the batch is outside its limits (the caller then uses the
 // frontier kernel).
@@ -1114,10 +1159,12 @@ int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, cons
       if (!e->busy && e->key == key) { e->busy = true; E = e; break; }
   }
   if (!E) {
+    pbat_options ob = o;
+    if (o.autotune && o.walk_bits < 0) ob.walk_bits = bsb_tune_walk(G, graphs, K, p, o, st, dev);
     std::unique_ptr<BsBatch> ne(new BsBatch());
     ne->key = key;
     ne->busy = true;
-    int rc = bsb_build(*ne, G, graphs, K, o, dev);
+    int rc = bsb_build(*ne, G, graphs, K, ob, dev);
     if (rc) {
       if (ne->scr) scratch_release(ne->scr);
       return rc;
