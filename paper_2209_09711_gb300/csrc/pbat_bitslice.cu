@@ -419,6 +419,35 @@ static void product_table(const double* p, const int* arcs, int n, dd* out) {
   }
 }
 
+// Byte-table sums from 32 pattern masses w[]: entry (b, v) is the sum of
+// w[8b + x] over the set bits x of v, rounded to 2^62 fixed point.  The
+// masses are rounded once to 2^126 and the subset sums are exact 128-bit
+// integer additions (one per entry, by the lowest set bit).
+static void byte_table_sums(const dd* w, int n_valid, unsigned long long* out, int stride) {
+  uint128_host fw[32];
+  for (int j = 0; j < 32; ++j) {
+    if (j >= n_valid) {
+      fw[j] = 0;
+      continue;
+    }
+    fw[j] = scaled_round_u(w[j].hi, 126);
+    if (w[j].lo > 0)
+      fw[j] += scaled_round_u(w[j].lo, 126);
+    else if (w[j].lo < 0)
+      fw[j] -= scaled_round_u(-w[j].lo, 126);
+  }
+  const uint128_host half = (uint128_host)1 << 63;
+  for (int b = 0; b < 4; ++b) {
+    uint128_host sb[256];
+    sb[0] = 0;
+    out[(size_t)(b * 256) * stride] = 0;
+    for (int v = 1; v < 256; ++v) {
+      sb[v] = sb[v & (v - 1)] + fw[8 * b + __builtin_ctz((unsigned)v)];
+      out[(size_t)(b * 256 + v) * stride] = (unsigned long long)((sb[v] + half) >> 64);
+    }
+  }
+}
+
 static unsigned long long fixed_u64(dd v, int scale) {
   // round((hi + lo) * 2^scale) for 0 <= v, result < 2^64
   uint128_host r = scaled_round_u(v.hi, scale);
@@ -599,20 +628,15 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
   dd lw[32];
   for (int j = 0; j < 32; ++j) lw[j] = dd{0.0, 0.0};
   product_table(p, bp.perm.data(), bp.ell, lw);
+  byte_table_sums(lw, 1 << bp.ell, bl.lane_tab.data(), 2);
   for (int b = 0; b < 4; ++b) {
-    // subset sums by the lowest set bit: one addition per entry
-    dd sb[256];
+    // counts by the lowest set bit: one addition per entry
     unsigned long long nb[256];
-    sb[0] = dd{0.0, 0.0};
     nb[0] = 0;
     for (int v = 1; v < 256; ++v) {
-      const int j = 8 * b + __builtin_ctz((unsigned)v), u = v & (v - 1);
-      const bool on = j < (1 << bp.ell);
-      sb[v] = on ? dd_add(sb[u], lw[j]) : sb[u];
-      nb[v] = nb[u] + (on ? 1ull << kNkShift[__builtin_popcount((unsigned)j)] : 0ull);
-      unsigned long long* e = &bl.lane_tab[(b * 256 + v) * 2];
-      e[0] = fixed_u64(sb[v], 62);
-      e[1] = nb[v];
+      const int j = 8 * b + __builtin_ctz((unsigned)v);
+      nb[v] = nb[v & (v - 1)] + (j < (1 << bp.ell) ? 1ull << kNkShift[__builtin_popcount((unsigned)j)] : 0ull);
+      bl.lane_tab[(b * 256 + v) * 2 + 1] = nb[v];
     }
   }
   const int L_in = std::min(bp.L, walk_unroll_bits(bp)), L_out = bp.L - L_in;
@@ -628,14 +652,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     // excluded-arc masses, reciprocals of the walk arcs' p and 1 - p
     memset(&bl.Q, 0, sizeof bl.Q);
     bl.thr_tab.assign(4 * 256, 0ull);
-    for (int b = 0; b < 4; ++b) {
-      dd sb[256];
-      sb[0] = dd{0.0, 0.0};
-      for (int v = 1; v < 256; ++v) {
-        sb[v] = dd_add(sb[v & (v - 1)], tw[8 * b + __builtin_ctz((unsigned)v)]);
-        bl.thr_tab[b * 256 + v] = fixed_u64(sb[v], 62);
-      }
-    }
+    byte_table_sums(tw, 1 << bp.tb, bl.thr_tab.data(), 1);
     bl.wmid128.resize((size_t)2 << bp.L);
     std::vector<dd> wt((size_t)1 << bp.L);
     product_table(p, bp.perm.data() + bp.ell + bp.tb, bp.L, wt.data());
@@ -644,20 +661,21 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
       bl.wmid128[2 * gi] = f.lo;
       bl.wmid128[2 * gi + 1] = f.hi;
     }
-    for (int x = 0; x < bp.tb; ++x)
-      for (int t = 0; t < (1 << bp.tb); ++t) {
-        dd w = dd_make(1.0);
-        for (int i = 0; i < bp.tb; ++i)
-          if (i != x) w = dd_mul(w, arc_w(p, bp.perm[bp.ell + i], (t >> i) & 1));
-        bl.Q.thw_ex[x][t] = fixed_u64(w, 63);
+    // pattern masses without arc x: a product table over the other arcs,
+    // indexed by the pattern with bit x removed
+    auto excluded = [&](const int* arcs, int n, unsigned long long (*out)[32]) {
+      for (int x = 0; x < n; ++x) {
+        int others[5];
+        for (int i = 0, c = 0; i < n; ++i)
+          if (i != x) others[c++] = arcs[i];
+        dd tab[16];
+        product_table(p, others, n - 1, tab);
+        for (int j = 0; j < (1 << n); ++j)
+          out[x][j] = fixed_u64(tab[(j & ((1 << x) - 1)) | ((j >> (x + 1)) << x)], 63);
       }
-    for (int x = 0; x < bp.ell; ++x)
-      for (int j = 0; j < (1 << bp.ell); ++j) {
-        dd w = dd_make(1.0);
-        for (int i = 0; i < bp.ell; ++i)
-          if (i != x) w = dd_mul(w, arc_w(p, bp.perm[i], (j >> i) & 1));
-        bl.Q.lw_ex[x][j] = fixed_u64(w, 63);
-      }
+    };
+    excluded(bp.perm.data() + bp.ell, bp.tb, bl.Q.thw_ex);
+    excluded(bp.perm.data(), bp.ell, bl.Q.lw_ex);
     for (int b = 0; b < bp.L; ++b) {
       const int k = bp.ell + bp.tb + b;
       const double pk = p[bp.perm[k]];
@@ -1035,15 +1053,7 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
       dd lw[32], tw[32];
       for (int j = 0; j < 32; ++j) lw[j] = tw[j] = dd{0.0, 0.0};
       product_table(pv, bp.perm.data(), bp.ell, lw);
-      for (int by = 0; by < 4; ++by) {  // byte sums by lowest set bit: one addition each
-        dd sb[256];
-        sb[0] = dd{0.0, 0.0};
-        lt[b.lt_off + (size_t)(by * 256) * Kp + k] = 0;
-        for (int val = 1; val < 256; ++val) {
-          sb[val] = dd_add(sb[val & (val - 1)], lw[8 * by + __builtin_ctz((unsigned)val)]);
-          lt[b.lt_off + (size_t)(by * 256 + val) * Kp + k] = fixed_u64(sb[val], 62);
-        }
-      }
+      byte_table_sums(lw, 1 << bp.ell, lt + b.lt_off + k, Kp);
       dd wtab[32];
       product_table(pv, bp.perm.data() + bp.ell + bp.tb, bp.L, wtab);
       for (int gi = 0; gi < (1 << bp.L); ++gi) wm[b.wm_off + (size_t)gi * Kp + k] = fixed_u64(wtab[gi], 63);
