@@ -154,3 +154,24 @@ def test_generated_sources_compile_with_nvrtc(pb):
         _nvrtc_compile(src.split("\n", 1)[1])
     nets, _ = synth.workload_batched(6, 3)
     _nvrtc_compile(pb.batch_kernel_source(nets, 3))
+
+
+def test_every_template_variant_compiles_with_nvrtc(pb):
+    """The generated source takes different template paths by shape: the
+    fused kernel's accumulators in registers (short walks or small programs)
+    or in global slots (long walks of large programs), two or three unrolled
+    walk arcs, and with or without thread arcs.  Each combination compiles."""
+    seen = set()
+    cases = [(synth.workload_grid_3x6(), 5), (synth.workload_directed_20_34(), 10),
+             (synth.workload_random_24_40(), 10), (synth.workload_random_24_40(), 4),
+             (synth.random_small(31, n=5, m=7), 2)]
+    for net, walk in cases:
+        for grad in (False, True):
+            src = pb.kernel_source(net, pb.options(walk_bits=walk), grad=grad)
+            key = tuple(re.findall(r"#define (BS_GRAD|BS_ACC_REG|BS_IN_BITS|BS_TB) (\d+)", src))
+            if key in seen:
+                continue
+            seen.add(key)
+            _nvrtc_compile(src.split("\n", 1)[1])
+    variants = {(dict(k)["BS_GRAD"], dict(k)["BS_ACC_REG"], dict(k)["BS_IN_BITS"]) for k in seen}
+    assert ("1", "0", "2") in variants and ("1", "1", "3") in variants and ("0", "1", "3") in variants
