@@ -289,6 +289,13 @@ def run_ours(a):
     fused = pb.Plan(net, grad=True, opts=opts_for("fused"), stream=sp)
     ms_f, kern_f, wall_f, res_f = time_plan(fused, a.steps, a.warmup)
     clocks = sampler.stop()
+    # the same fused kernel with the prune off: every state walked
+    if "fused" in shp:
+        nopr_opts = pb.options(walk_bits=shp["fused"][0], block_threads=shp["fused"][1], prune=0)
+    else:
+        nopr_opts = pb.options(prune=0)
+    nopr = pb.Plan(net, grad=True, opts=nopr_opts, stream=sp)
+    ms_np, kern_np, _, res_np = time_plan(nopr, max(3, a.steps // 10), min(a.warmup, 3))
     ronly = pb.Plan(net, grad=False, opts=opts_for("r_only"), stream=sp)
     ms_r, kern_r, _, res_r = time_plan(ronly, a.steps, a.warmup)
     # the plain GPU BAT: one state per thread, per-state PLSA frontier
@@ -302,7 +309,7 @@ def run_ours(a):
     ms_p, kern_p, _, res_p = time_plan(plain, max(3, a.steps // 10), min(a.warmup, 3))
     plain_g = pb.Plan(net, grad=True, opts=pb.options(**popt), stream=sp)
     ms_pg, kern_pg, _, res_pg = time_plan(plain_g, max(3, a.steps // 10), min(a.warmup, 3))
-    assert res_r.Nk == res_f.Nk, "kernels disagree on N_k"
+    assert res_r.Nk == res_f.Nk == res_np.Nk, "kernels disagree on N_k"
     if not plain_rb:
         assert res_r.Nk == res_p.Nk == res_pg.Nk, "kernels disagree on N_k"
 
@@ -359,6 +366,8 @@ def run_ours(a):
                                   "flushed between steps (256 MiB write, outside the timed events)"),
         "roofline": roof,
         "fused_shape": shape,
+        "unpruned": {"value": ws * states / (ms_np / 1e3), "ms_per_step": ms_np, "kernel_ms": kern_np,
+                     "what": "the fused kernel with the monotone prune off (every state walked)"},
         "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r,
                    "kernel": "bs_kernel", "shape": ronly.describe(),
                    "roofline": roofline("bs_kernel", ronly, kern_r)},
@@ -380,7 +389,7 @@ def run_ours(a):
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
-    for pl in (fused, ronly, plain, plain_g):
+    for pl in (fused, nopr, ronly, plain, plain_g):
         pl.close()
     return 0
 
