@@ -22,6 +22,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -328,19 +329,19 @@ struct JitEntry {
 static std::mutex g_jit_mu;
 static std::map<std::string, JitEntry> g_jit;
 
-static int jit_compile(const std::string& src, const DeviceInfo& dev, const char* kname,
-                       JitEntry* out) {
-  std::lock_guard<std::mutex> lk(g_jit_mu);
-  auto it = g_jit.find(src);
-  if (it != g_jit.end()) {
-    *out = it->second;
-    return PBAT_OK;
-  }
+static std::mutex g_cubin_mu;
+static std::map<std::string, std::vector<char>> g_cubin;   // compiled ahead, not yet loaded
+
+// NVRTC only -- no CUDA call, so any host thread may run it.  On failure
+// `err` holds the compiler's error lines.
+static bool nvrtc_cubin(const std::string& src, int cc, std::vector<char>& cubin, std::string& err) {
   nvrtcProgram prog;
   if (nvrtcCreateProgram(&prog, src.c_str(), "pbat_bitslice_gen.cu", 0, nullptr, nullptr) !=
-      NVRTC_SUCCESS)
-    return fail(PBAT_ECUDA, "nvrtcCreateProgram failed");
-  const std::string arch = "-arch=sm_" + std::to_string(dev.cc_major * 10 + dev.cc_minor) + "a";
+      NVRTC_SUCCESS) {
+    err = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const std::string arch = "-arch=sm_" + std::to_string(cc) + "a";
   const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo", "-diag-suppress=177"};
   const nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
   if (rc != NVRTC_SUCCESS) {
@@ -350,24 +351,80 @@ static int jit_compile(const std::string& src, const DeviceInfo& dev, const char
     if (ls) nvrtcGetProgramLog(prog, &all[0]);
     nvrtcDestroyProgram(&prog);
     // keep the error lines only
-    std::string log;
+    err = std::string(nvrtcGetErrorString(rc)) + " ";
     size_t at = 0;
     while (at < all.size()) {
       size_t nl = all.find('\n', at);
       if (nl == std::string::npos) nl = all.size();
       const std::string line = all.substr(at, nl - at);
-      if (line.find("error") != std::string::npos) log += line + " | ";
+      if (line.find("error") != std::string::npos) err += line + " | ";
       at = nl + 1;
     }
-    if (log.size() > 400) log.resize(400);
-    return fail(PBAT_ECUDA, "NVRTC compile of the bit-sliced kernel failed: %s %s",
-                nvrtcGetErrorString(rc), log.c_str());
+    if (err.size() > 400) err.resize(400);
+    return false;
   }
   size_t cs = 0;
   nvrtcGetCUBINSize(prog, &cs);
-  std::vector<char> cubin(cs);
+  cubin.resize(cs);
   nvrtcGetCUBIN(prog, cubin.data());
   nvrtcDestroyProgram(&prog);
+  return true;
+}
+
+// Compile several sources at once on host threads (the autotuner's
+// candidates); the cubins wait for jit_compile.  A failure is left for
+// jit_compile to report when that source is needed.
+static void jit_precompile(const std::vector<std::string>& srcs, int cc) {
+  std::vector<const std::string*> todo;
+  {
+    std::lock_guard<std::mutex> lj(g_jit_mu);
+    std::lock_guard<std::mutex> lc(g_cubin_mu);
+    for (const auto& src : srcs)
+      if (!g_jit.count(src) && !g_cubin.count(src)) todo.push_back(&src);
+  }
+  if (todo.empty()) return;
+  std::atomic<size_t> next{0};
+  auto work = [&]() {
+    for (;;) {
+      const size_t i = next++;
+      if (i >= todo.size()) return;
+      std::vector<char> cubin;
+      std::string err;
+      if (!nvrtc_cubin(*todo[i], cc, cubin, err)) continue;
+      std::lock_guard<std::mutex> lc(g_cubin_mu);
+      g_cubin.emplace(*todo[i], std::move(cubin));
+    }
+  };
+  const int nthreads =
+      std::max(1, std::min({(int)todo.size(), 16, (int)std::thread::hardware_concurrency()}));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nthreads; ++t) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+}
+
+static int jit_compile(const std::string& src, const DeviceInfo& dev, const char* kname,
+                       JitEntry* out) {
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  auto it = g_jit.find(src);
+  if (it != g_jit.end()) {
+    *out = it->second;
+    return PBAT_OK;
+  }
+  std::vector<char> cubin;
+  {
+    std::lock_guard<std::mutex> lc(g_cubin_mu);
+    auto c = g_cubin.find(src);
+    if (c != g_cubin.end()) {
+      cubin.swap(c->second);
+      g_cubin.erase(c);
+    }
+  }
+  if (cubin.empty()) {
+    std::string err;
+    if (!nvrtc_cubin(src, dev.cc_major * 10 + dev.cc_minor, cubin, err))
+      return fail(PBAT_ECUDA, "NVRTC compile of the bit-sliced kernel failed: %s", err.c_str());
+  }
   JitEntry e;
   cudaError_t ce = cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (ce != cudaSuccess) return fail(PBAT_ECUDA, "cudaLibraryLoadData: %s", cudaGetErrorString(ce));
@@ -540,6 +597,29 @@ static std::string bs_plan_key(const GraphIn& g, const double* p, bool grad, con
   if (grad)
     for (int a = 0; a < g.m; ++a) k.push_back(bs_walk_ok(p, a) ? '1' : '0');
   return k;
+}
+
+// Compile the kernels of several option sets ahead of bs_prepare, on host
+// threads (the autotuner's candidates: one NVRTC compile each, which would
+// otherwise run one after another).  Plans that fail are skipped here and
+// reported when bs_prepare meets them.
+void bs_precompile(const GraphIn& g, const double* p, bool grad,
+                   const std::vector<pbat_options>& opts, const DeviceInfo& dev) {
+  std::vector<std::string> srcs;
+  for (const pbat_options& o : opts) {
+    const int nthr = o.block_threads > 0 ? o.block_threads : 128;
+    {
+      std::lock_guard<std::mutex> lk(g_bsplan_mu);
+      if (g_bsplan.count(bs_plan_key(g, p, grad, o, nthr, dev.device))) continue;
+    }
+    BsPlan bp;
+    if (bs_make_plan(g, o, nthr, bp, grad ? p : nullptr)) {
+      clear_error();
+      continue;
+    }
+    srcs.push_back(bs_source(g, bp, nthr));
+  }
+  jit_precompile(srcs, dev.cc_major * 10 + dev.cc_minor);
 }
 
 int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
@@ -1123,6 +1203,20 @@ static int bsb_tune_walk(int G, const pbat_graph* graphs, int K, const double* p
     if (a) cudaEventDestroy(a);
     cudaGetLastError();
     return -1;
+  }
+  {
+    // the candidates' modules compile at once on host threads
+    std::vector<std::string> srcs;
+    for (int L = 3; L <= kBsbMaxWalk; ++L) {
+      pbat_options t = o;
+      t.walk_bits = L;
+      BsBatch T;
+      std::vector<unsigned long long> items;
+      std::string src;
+      if (bsb_source(T, G, graphs, K, t, items, src) == PBAT_OK) srcs.push_back(std::move(src));
+      else clear_error();
+    }
+    jit_precompile(srcs, dev.cc_major * 10 + dev.cc_minor);
   }
   for (int L = 3; L <= kBsbMaxWalk; ++L) {
     pbat_options t = o;

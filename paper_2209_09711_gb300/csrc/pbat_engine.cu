@@ -45,6 +45,8 @@ struct BsLaunch;
 void bs_finish_grad(const BsLaunch& bl, const dd* acc, int m, double* g_internal);
 BsLaunch* bs_new();
 void bs_delete(BsLaunch* b);
+void bs_precompile(const GraphIn& g, const double* p, bool grad,
+                   const std::vector<pbat_options>& opts, const DeviceInfo& dev);
 int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
                const DeviceInfo& dev, BsLaunch& bl);
 cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsigned long long* d_lane,
@@ -518,10 +520,7 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
   // than 128 and 224 threads the R kernel 7% faster than 256
   if (!large) nts.push_back(64), nts.push_back(96);
   for (int nt : {128, 160, 192, 224, 256}) nts.push_back(nt);
-  cudaStream_t st;
-  PBAT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  double best_ms = 1e300;
-  int best_L = -1, best_nt = 128;
+  std::vector<pbat_options> cands;
   for (int L : Ls)
     for (int nt : nts) {
       pbat_options t = o;
@@ -529,34 +528,42 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
       t.walk_bits = L;
       t.block_threads = nt;
       t.time_budget_s = 0;
-      Job* J = nullptr;
-      if (job_create(g, p, grad, &t, &J) != PBAT_OK) {
-        clear_error();
-        continue;
-      }
-      double ms = 1e300;
-      bool ok = !job_upload(J, st);
-      for (int rep = 0; ok && rep < 2; ++rep) {
-        cudaEvent_t a, b;
-        cudaEventCreate(&a);
-        cudaEventCreate(&b);
-        cudaEventRecord(a, st);
-        ok = !job_launch(J, st);
-        cudaEventRecord(b, st);
-        ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
-        float f = 0.f;
-        if (ok && cudaEventElapsedTime(&f, a, b) == cudaSuccess && rep > 0) ms = f;
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-      }
-      job_destroy(J);
-      if (!ok) {
-        cudaGetLastError();
-        clear_error();
-        continue;
-      }
-      if (ms < best_ms) best_ms = ms, best_L = L, best_nt = nt;
+      cands.push_back(t);
     }
+  bs_precompile(g, p, grad, cands, dev);
+  cudaStream_t st;
+  PBAT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  double best_ms = 1e300;
+  int best_L = -1, best_nt = 128;
+  for (pbat_options& t : cands) {
+    Job* J = nullptr;
+    if (job_create(g, p, grad, &t, &J) != PBAT_OK) {
+      clear_error();
+      continue;
+    }
+    double ms = 1e300;
+    bool ok = !job_upload(J, st);
+    for (int rep = 0; ok && rep < 2; ++rep) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, st);
+      ok = !job_launch(J, st);
+      cudaEventRecord(b, st);
+      ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+      float f = 0.f;
+      if (ok && cudaEventElapsedTime(&f, a, b) == cudaSuccess && rep > 0) ms = f;
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+    job_destroy(J);
+    if (!ok) {
+      cudaGetLastError();
+      clear_error();
+      continue;
+    }
+    if (ms < best_ms) best_ms = ms, best_L = t.walk_bits, best_nt = t.block_threads;
+  }
   cudaStreamDestroy(st);
   if (best_L < 0) return PBAT_OK;  // keep the planner's defaults
   o.walk_bits = best_L;
