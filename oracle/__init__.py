@@ -36,8 +36,10 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+            # A test may point this at a copy of the oracle with a planted
+            # mistake, to check that the pins catch it.
+            path = os.environ.get("PBAT_ORACLE_LIB") or build()
+            lib = ctypes.CDLL(path)
             I, U64, D = ctypes.c_int, ctypes.c_uint64, ctypes.c_double
             PI = ctypes.POINTER(ctypes.c_int)
             PD = ctypes.POINTER(ctypes.c_double)
