@@ -5,8 +5,8 @@ with chi = 2^bits divisions of the state space, rank r of w takes the
 contiguous block of divisions [r*chi/w, (r+1)*chi/w) and runs it through the
 engine's range option.  Partial R, N_k and dR/dp of disjoint division
 blocks add up exactly to the whole (Eq. 1 is a sum over states), so the
-only exchange is one sum-reduce of 1 + (m + 1) + m numbers after the
-enumeration (PBAT STEP 3).
+only exchange is a sum-reduce of 1 + m floating-point numbers and m + 1
+integer counts after the enumeration (PBAT STEP 3).
 """
 from __future__ import annotations
 
@@ -30,18 +30,19 @@ def shard_range(m: int, world: int, rank: int, bits: Optional[int] = None) -> Tu
     return bits, lo, hi
 
 
-def pack(R: float, Nk: List[int], grad: Optional[List[float]]) -> np.ndarray:
-    """One float64 vector [R, N_0..N_m, dR/dp...] for a sum-reduce (N_k stay
-    exact: each is below 2^53 for m <= 52, and the reduce is over a handful
-    of ranks)."""
+def pack(R: float, Nk: List[int], grad: Optional[List[float]]) -> Tuple[np.ndarray, np.ndarray]:
+    """The two vectors of a sum-reduce: float64 [R, dR/dp...] and int64
+    [N_0..N_m].  N_k travel as integers so that the reduce stays bit-exact:
+    a count can exceed 2^53 (C(63, 31) is about 9.2e17), and a sum of
+    disjoint blocks' counts is at most the whole network's, below 2^63."""
     g = [] if grad is None else list(grad)
-    return np.asarray([R] + [float(x) for x in Nk] + g, dtype=np.float64)
+    return (np.asarray([R] + g, dtype=np.float64), np.asarray(list(Nk), dtype=np.int64))
 
 
-def unpack(v: np.ndarray, m: int, with_grad: bool):
-    R = float(v[0])
-    Nk = [int(round(x)) for x in v[1:m + 2]]
-    grad = [float(x) for x in v[m + 2:]] if with_grad else None
+def unpack(fv: np.ndarray, nv: np.ndarray, with_grad: bool):
+    R = float(fv[0])
+    Nk = [int(x) for x in nv]
+    grad = [float(x) for x in fv[1:]] if with_grad else None
     return R, Nk, grad
 
 
@@ -49,12 +50,13 @@ def reliability_sharded(net, compute: Callable, world: int, rank: int,
                         all_reduce: Callable[[np.ndarray], np.ndarray], grad: bool = False,
                         bits: Optional[int] = None):
     """Run this rank's block through `compute(net, range_bits, lo, hi, grad)`
-    -> (R, Nk, grad or None), sum-reduce with `all_reduce`, return the whole
+    -> (R, Nk, grad or None), sum-reduce with `all_reduce` (once for the
+    float64 vector, once for the int64 counts), return the whole
     (R, Nk, grad)."""
     b, lo, hi = shard_range(net.m, world, rank, bits)
     R, Nk, g = compute(net, b, lo, hi, grad)
-    total = all_reduce(pack(R, Nk, g if grad else None))
-    return unpack(total, net.m, grad)
+    fv, nv = pack(R, Nk, g if grad else None)
+    return unpack(all_reduce(fv), all_reduce(nv), grad)
 
 
 def gpu_compute(net, range_bits: int, lo: int, hi: int, grad: bool, stream: int = 0):
@@ -66,7 +68,8 @@ def gpu_compute(net, range_bits: int, lo: int, hi: int, grad: bool, stream: int 
 
 
 def torch_all_reduce(group=None) -> Callable[[np.ndarray], np.ndarray]:
-    """Sum-reduce through torch.distributed (float64 on the backend's device)."""
+    """Sum-reduce through torch.distributed (float64 or int64, on the
+    backend's device)."""
     import torch
     import torch.distributed as dist
 

@@ -26,6 +26,18 @@ def _oracle_compute(net, bits, lo, hi, grad):
     return r.R, r.Nk, (r.grad_t1t0 if grad else None)
 
 
+class _Big:
+    m = 63
+
+
+_BIG_BASE = [3 ** 37 + 2 * k for k in range(64)]   # 3^37 > 2^58
+
+
+def _big_compute(net, bits, lo, hi, grad):
+    # a stand-in rank result: odd-sized counts that differ per block
+    return 1e-3 * lo, [c + lo for c in _BIG_BASE], None
+
+
 def _worker(rank, world, port, q):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -36,7 +48,11 @@ def _worker(rank, world, port, q):
             R, Nk, g = shard.reliability_sharded(net, _oracle_compute, world, rank,
                                                  shard.torch_all_reduce(), grad=True)
             out.append((R, Nk, g))
-        q.put((rank, out))
+        # counts above 2^53 (a 63-arc network's middle N_k reach C(63, 31)):
+        # a float64 reduce would round them, the int64 one must not
+        big = shard.reliability_sharded(_Big(), _big_compute, world, rank,
+                                        shard.torch_all_reduce(), grad=False)
+        q.put((rank, out, big))
     finally:
         dist.destroy_process_group()
 
@@ -59,7 +75,9 @@ def test_two_gloo_ranks_match_the_whole():
     procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
-    results = dict(q.get(timeout=120) for _ in range(world))
+    got = [q.get(timeout=120) for _ in range(world)]
+    results = {r: out for r, out, _ in got}
+    bigs = {r: big for r, _, big in got}
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
@@ -71,3 +89,10 @@ def test_two_gloo_ranks_match_the_whole():
             assert Nk == ref.Nk
             assert abs(R - ref.R) <= 1e-14
             assert max(abs(a - b) for a, b in zip(g, ref.grad_t1t0)) <= 1e-14
+    blocks = [shard.shard_range(63, world, r)[1] for r in range(world)]
+    want = [sum(c + lo for lo in blocks) for c in _BIG_BASE]
+    assert max(want) > 2 ** 53
+    for rank in range(world):
+        R, Nk, g = bigs[rank]
+        assert Nk == want
+        assert g is None
