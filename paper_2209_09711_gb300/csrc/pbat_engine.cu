@@ -588,7 +588,8 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
     if ((rc = autotune(g, p, grad, o, dv))) return rc;
   }
   const bool use_bs = o.algo == PBAT_ALGO_BITSLICE || o.algo == PBAT_ALGO_AUTO;
-  std::unique_ptr<Job> J(new Job());
+  // job_destroy also frees the bit-sliced launch if a later step fails
+  std::unique_ptr<Job, void (*)(Job*)> J(new Job(), job_destroy);
   J->g = g;
   J->tail_copy.assign(g.tail, g.tail + g.m);
   J->head_copy.assign(g.head, g.head + g.m);
