@@ -62,12 +62,17 @@ extern "C" {
 
 typedef struct pbat_options {
   int struct_size;      /* sizeof(pbat_options); set by pbat_options_init */
-  int algo;             /* PBAT_ALGO_*; AUTO lets the autotuner choose */
+  int algo;             /* PBAT_ALGO_*; AUTO: the bit-sliced kernel, re-run exactly with the
+                           frontier kernel when R is too small for the bit-sliced kernel's
+                           fixed-point error bound to give 1e-12 relative accuracy */
   int prefix_bits;      /* d: arcs fixed per work item (equal division, Sec. 4.3); -1 = auto */
   int walk_bits;        /* L: arcs each thread walks in Gray-code order; -1 = auto */
   int block_threads;    /* threads per CTA; -1 = auto */
   int prune;            /* 1 (default): exact monotone prefix prune; 0: walk every state */
-  int autotune;         /* 1 (default): consult / fill the autotune cache */
+  int autotune;         /* 1 (default): for problems of at least 2^26 states with walk_bits,
+                           block_threads and prefix_bits all -1, time candidate launch
+                           shapes once per network structure and keep the fastest
+                           (in memory, and in the file named by PBAT_AUTOTUNE_CACHE) */
   int range_bits;       /* 0 (default) = whole space.  Otherwise only the states whose
                            first range_bits coordinates, read as an integer, lie in
                            [range_lo, range_hi) -- the divisions range_lo..range_hi-1 of
