@@ -2,14 +2,16 @@
 """PBAT benchmark: states/s of exact two-terminal reliability on one GB300.
 
 A step is one pass of the whole enumeration (prefix split, exact monotone
-prune, Gray walk, per-state PLSA connectivity, exact accumulation of R,
-N_k and dR/dp, fixed-order reduction) over the 2^m states of the workload,
-with the tables already resident on the device.  ``value`` is 2^m / device
-time of the fused R + N_k + dR/dp step (CUDA events on the launch stream,
-L2 flushed by a 256 MiB write between steps, outside the events);
-``r_only`` is the same for the R + N_k kernel, the plain GPU BAT it is
-compared with.  ``e2e`` times the public C-ABI call with host buffers
-(planning, table build, host -> device and device -> host copies included).
+prune, Gray walk, connectivity of every state, exact accumulation of R,
+N_k and dR/dp into 256-bit fixed-point results) over the 2^m states of the
+workload, with the tables already resident on the device.  ``value`` is
+2^m / device time of the fused R + N_k + dR/dp step (CUDA events on the
+launch stream, L2 flushed by a 256 MiB write between steps, outside the
+events).  ``r_only`` is the same for the R + N_k kernel, and
+``plain_gpu_bat`` for the one-state-per-thread frontier kernel (the plain
+GPU BAT, R and fused).  ``e2e`` times the public C-ABI call with host
+buffers (planning, table build, host -> device and device -> host copies
+included).
 
 --impl reference times the CPU oracle (test infrastructure: plain brute
 force, long double) on the host cores over a bounded sample of the same
