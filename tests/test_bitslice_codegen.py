@@ -175,3 +175,33 @@ def test_every_template_variant_compiles_with_nvrtc(pb):
             _nvrtc_compile(src.split("\n", 1)[1])
     variants = {(dict(k)["BS_GRAD"], dict(k)["BS_ACC_REG"], dict(k)["BS_IN_BITS"]) for k in seen}
     assert ("1", "0", "2") in variants and ("1", "1", "3") in variants and ("0", "1", "3") in variants
+
+
+def test_batched_module_holds_each_network_program(pb):
+    """The batched module's per-network structs carry, in launch order
+    (networks with the most work items first), exactly the connectivity
+    programs emulated above for the single-network kernel with the batched
+    walk length, and the plan constants that go with them."""
+    nets, _ = synth.workload_batched(12, 2)
+    bsrc = pb.batch_kernel_source(nets, 2)
+    singles = []
+    for net in nets:
+        src = pb.kernel_source(net, pb.options(walk_bits=5, block_threads=128))
+        _, D, inv, var = _parse(src)
+        singles.append((D, inv.split("\n", 1)[1], var.split("\n", 1)[1]))
+    order = sorted(range(len(nets)), key=lambda i: -(1 << singles[i][0]["BS_D"]))
+    for r, i in enumerate(order):
+        start = bsrc.index(f"struct G{r} {{")
+        body = bsrc[start:bsrc.index("\n};\n", start) + 1]   # ends with var's "}\n"
+        consts = dict(re.findall(r"(\w+) = (\d+)", body.split("\n")[1]))
+        D = singles[i][0]
+        assert int(consts["M"]) == nets[i].m
+        for key in ("ELL", "TB", "L", "D", "NCORE", "WALK0", "TOP"):
+            assert int(consts[key]) == D["BS_" + key], (r, key)
+        inv = body[body.index("void inv("):]
+        inv = inv[:inv.index("\n}\n")].split("\n", 1)[1]
+        var = body[body.index("u32 var("):]
+        var = var[:var.index("\n}\n")].split("\n", 1)[1]
+        assert inv and var
+        assert inv == singles[i][1], r
+        assert var == singles[i][2], r
