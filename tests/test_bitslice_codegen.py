@@ -205,3 +205,21 @@ def test_batched_module_holds_each_network_program(pb):
         assert inv and var
         assert inv == singles[i][1], r
         assert var == singles[i][2], r
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_generated_program_at_maximum_sizes(pb, directed):
+    """The generator at the ABI's limits: 63 arcs on 64 nodes and on 24
+    nodes, seeded so that random states are a mix of connected and cut
+    (roughly half connected), over the whole space, a deep equal-division range
+    and the longest walk; the emulated program matches the oracle's
+    connectivity, and the R and fused sources compile."""
+    seeds = {False: (77000, 77000), True: (77028, 77002)}[directed]
+    big = synth.random_small(seeds[0], n=64, m=63, directed=directed)
+    mid = synth.random_small(seeds[1], n=24, m=63, directed=directed)
+    for net in (big, mid):
+        _check(pb, net, 5, trials=8)
+        _check(pb, net, 6, pb.options(range_bits=40, range_lo=12345, range_hi=12346), trials=4)
+        _check(pb, net, 7, pb.options(walk_bits=10), trials=4)
+    _nvrtc_compile(pb.kernel_source(big, pb.options(walk_bits=10)))
+    _nvrtc_compile(pb.kernel_source(mid, pb.options(walk_bits=10), grad=True))
