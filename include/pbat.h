@@ -68,7 +68,11 @@ typedef struct pbat_options {
   int prefix_bits;      /* d: arcs fixed per work item (equal division, Sec. 4.3); -1 = auto */
   int walk_bits;        /* L: arcs each thread walks in Gray-code order; -1 = auto */
   int block_threads;    /* threads per CTA; -1 = auto */
-  int prune;            /* 1 (default): exact monotone prefix prune; 0: walk every state */
+  int prune;            /* 1 (default): exact monotone prefix prune; 0: walk every state;
+                           2: the prune, with the bit-sliced kernels' prefix arcs chosen
+                           to maximise the work items it resolves (a deterministic search
+                           at planning time, tenths of a second for 30-40 arcs, kept per
+                           network).  Every setting gives the same exact results. */
   int autotune;         /* 1 (default): for problems of at least 2^26 states with walk_bits,
                            block_threads and prefix_bits all -1, time candidate launch
                            shapes once per network structure and keep the fastest

@@ -181,6 +181,143 @@ static std::vector<int> bfs_dist(const GraphIn& g, int src) {
   return d;
 }
 
+// ---------------------------------------------------------------------------
+// prune-aware prefix arcs (opt-in, pbat_options.prune == 2)
+// ---------------------------------------------------------------------------
+// The monotone prune resolves a work item when the sink is cut off with every
+// non-prefix arc working, or reached with every non-prefix arc failed.  Which
+// arcs form the prefix therefore decides how many items are walked: an s-t
+// cut lying wholly in the prefix resolves every item in which its arcs all
+// fail.  This picks the prefix arcs first -- the arcs nearest to the source
+// or the sink, then a deterministic swap search that maximises the number of
+// resolved items over a fixed sample of prefix values -- and leaves the walk
+// cluster to the remaining arcs.  Work items are counted uniformly (each is
+// 2^(m-d) states of work whatever its probability).
+class PruneScorer {
+ public:
+  PruneScorer(const GraphIn& g, int n_samples) : g_(g) {
+    uint64_t x = 0x2209097110ull;   // fixed: plans must be reproducible
+    for (int i = 0; i < n_samples; ++i) {
+      x += 0x9e3779b97f4a7c15ull;    // splitmix64
+      uint64_t z = x;
+      z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+      z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+      samples_.push_back(z ^ (z >> 31));
+    }
+  }
+  // s-t reachability with the arcs of `on` working
+  bool conn(uint64_t on) const {
+    uint64_t seen = 1ull << g_.source;
+    for (bool grew = true; grew;) {
+      grew = false;
+      for (int k = 0; k < g_.m; ++k) {
+        if (!((on >> k) & 1)) continue;
+        const int u = g_.tail[k], v = g_.head[k];
+        if (((seen >> u) & 1) && !((seen >> v) & 1)) seen |= 1ull << v, grew = true;
+        if (!g_.directed && ((seen >> v) & 1) && !((seen >> u) & 1)) seen |= 1ull << u, grew = true;
+      }
+      if ((seen >> g_.sink) & 1) return true;
+    }
+    return false;
+  }
+  // items resolved by the prune, over every value of a small prefix or the
+  // fixed sample of a large one
+  int score(const std::vector<int>& pre) const {
+    const int d = (int)pre.size();
+    uint64_t pmask = 0;
+    for (int a : pre) pmask |= 1ull << a;
+    const uint64_t all = g_.m >= 64 ? ~0ull : ((1ull << g_.m) - 1);
+    const bool exact = d <= 30 && (1ull << d) <= samples_.size();
+    const uint64_t n = exact ? (1ull << d) : samples_.size();
+    int res = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      const uint64_t v = exact ? i : samples_[i];
+      uint64_t on = 0;
+      for (int j = 0; j < d; ++j)
+        if ((v >> j) & 1) on |= 1ull << pre[j];
+      if (!conn(on | (all & ~pmask))) ++res;
+      else if (conn(on)) ++res;
+    }
+    return res;
+  }
+
+ private:
+  const GraphIn& g_;
+  std::vector<uint64_t> samples_;
+};
+
+static std::vector<int> bfs_dist(const GraphIn& g, int src);
+
+// `fixed` (the range arcs) are always prefix arcs; choose `want` more among
+// `cand`.  Returns the chosen arcs (not including `fixed`).
+static std::vector<int> bs_prune_prefix_search(const GraphIn& g, const std::vector<int>& fixed,
+                                               const std::vector<int>& cand, int want);
+
+// The search is deterministic and depends only on the network, the range
+// arcs and the number of arcs wanted: its result is kept (the autotuner
+// plans every candidate shape, several with the same prefix length).
+static std::mutex g_prefix_mu;
+static std::map<std::string, std::vector<int>> g_prefix;
+
+static std::vector<int> bs_prune_prefix(const GraphIn& g, const std::vector<int>& fixed,
+                                        const std::vector<int>& cand, int want) {
+  std::string key;
+  auto put = [&](long long v) { key.append((const char*)&v, sizeof v); };
+  put(g.n); put(g.m); put(g.directed); put(g.source); put(g.sink); put(want);
+  put((long long)fixed.size());
+  for (int a : cand) put(a);
+  key.append((const char*)g.tail, sizeof(int32_t) * g.m);
+  key.append((const char*)g.head, sizeof(int32_t) * g.m);
+  {
+    std::lock_guard<std::mutex> lk(g_prefix_mu);
+    auto it = g_prefix.find(key);
+    if (it != g_prefix.end()) return it->second;
+  }
+  std::vector<int> r = bs_prune_prefix_search(g, fixed, cand, want);
+  std::lock_guard<std::mutex> lk(g_prefix_mu);
+  g_prefix[key] = r;
+  return r;
+}
+
+static std::vector<int> bs_prune_prefix_search(const GraphIn& g, const std::vector<int>& fixed,
+                                               const std::vector<int>& cand, int want) {
+  const std::vector<int> ds = bfs_dist(g, g.source), dt = bfs_dist(g, g.sink);
+  auto near = [&](int a) {
+    return std::min(std::min(ds[g.tail[a]], ds[g.head[a]]), std::min(dt[g.tail[a]], dt[g.head[a]]));
+  };
+  std::vector<int> order = cand;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return near(x) < near(y); });
+  std::vector<int> chosen(order.begin(), order.begin() + want);
+  std::vector<int> others(order.begin() + want, order.end());
+  if (chosen.empty() || others.empty()) return chosen;
+  const PruneScorer sc(g, 256);
+  auto full = [&](const std::vector<int>& ch) {
+    std::vector<int> pre = fixed;
+    pre.insert(pre.end(), ch.begin(), ch.end());
+    return pre;
+  };
+  int best = sc.score(full(chosen));
+  // first-improvement swaps in a fixed order, at most 1500 evaluations
+  int evals = 0;
+  for (bool improved = true; improved && evals < 1500;) {
+    improved = false;
+    for (size_t i = 0; i < chosen.size() && !improved && evals < 1500; ++i)
+      for (size_t o = 0; o < others.size() && evals < 1500; ++o) {
+        std::vector<int> trial = chosen;
+        trial[i] = others[o];
+        const int sc_t = sc.score(full(trial));
+        ++evals;
+        if (sc_t > best) {
+          std::swap(chosen[i], others[o]);
+          best = sc_t;
+          improved = true;
+          break;
+        }
+      }
+  }
+  return chosen;
+}
+
 // Generate bs_inv / bs_var for a given role assignment; returns bs_var's op count.
 static void bs_generate(const GraphIn& g, BsPlan& bp) {
   const int m = g.m, top = bp.ell + bp.tb + bp.L, w0 = bp.ell + bp.tb;
@@ -258,9 +395,17 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
   // ---- roles.  range arcs are the top prefix bits in input order.
   std::vector<int> cand;
   for (int a = r; a < m; ++a) cand.push_back(a);
+  // prune-aware mode: the prefix arcs first, the walk cluster from the rest
+  std::vector<bool> incore(g.n, false), used(m, false);
+  std::vector<int> pre_first;
+  if (o.prune == 2 && bp.d - r > 0) {
+    std::vector<int> fixed;
+    for (int i = 0; i < r; ++i) fixed.push_back(i);
+    pre_first = bs_prune_prefix(g, fixed, cand, bp.d - r);
+    for (int a : pre_first) used[a] = true;
+  }
   // walk arcs: a compact cluster grown from {source, sink}, so the per-word
   // core stays small
-  std::vector<bool> incore(g.n, false), used(m, false);
   incore[g.source] = incore[g.sink] = true;
   std::vector<int> walk;
   for (int it = 0; it < bp.L; ++it) {
@@ -282,7 +427,7 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
   // prefix arcs: the arcs nearest to the source or the sink (they decide the
   // prune), among the rest
   const std::vector<int> ds = bfs_dist(g, g.source), dt = bfs_dist(g, g.sink);
-  std::vector<int> rest;
+  std::vector<int> rest;   // neither walk arcs nor prefix arcs chosen above
   for (int a : cand)
     if (!used[a]) rest.push_back(a);
   std::stable_sort(rest.begin(), rest.end(), [&](int x, int y) {
@@ -291,15 +436,19 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
     return dx < dy;
   });
   const int npre_free = bp.d - r;
-  if (npre_free < 0 || npre_free + bp.ell + bp.tb != (int)rest.size())
+  // a walk shortened for want of eligible arcs deepens the prefix: the
+  // extra prefix arcs are the nearest of the rest
+  const int extra = npre_free - (int)pre_first.size();
+  if (npre_free < 0 || extra < 0 || extra + bp.ell + bp.tb != (int)rest.size())
     return fail(PBAT_EINVAL, "internal: bit-sliced plan does not fit (m=%d r=%d L=%d)", m, r, bp.L);
   bp.perm.assign(m, -1);
-  // prefix positions [top, m - r): nearest arcs; range arcs at [m - r, m)
+  // prefix positions [top, m - r): chosen or nearest arcs; range arcs at [m - r, m)
   const int top = bp.ell + bp.tb + bp.L;
-  for (int j = 0; j < npre_free; ++j) bp.perm[top + j] = rest[j];
+  for (int j = 0; j < (int)pre_first.size(); ++j) bp.perm[top + j] = pre_first[j];
+  for (int j = 0; j < extra; ++j) bp.perm[top + (int)pre_first.size() + j] = rest[j];
   for (int i = 0; i < r; ++i) bp.perm[m - 1 - i] = i;
   for (int b = 0; b < bp.L; ++b) bp.perm[bp.ell + bp.tb + b] = walk[b];
-  int x = npre_free;
+  int x = extra;
   for (int k = 0; k < bp.ell + bp.tb; ++k) bp.perm[k] = rest[x++];
   // invariants the kernel relies on: a permutation, range arcs on top, and
   // every role within its limits
@@ -591,7 +740,7 @@ static std::string bs_plan_key(const GraphIn& g, const double* p, bool grad, con
   std::string k;
   auto put = [&](long long v) { k.append((const char*)&v, sizeof v); };
   put(device); put(g.n); put(g.m); put(g.directed); put(g.source); put(g.sink); put(grad);
-  put(o.walk_bits); put(o.prefix_bits); put(o.range_bits); put(nthr);
+  put(o.walk_bits); put(o.prefix_bits); put(o.range_bits); put(nthr); put(o.prune == 2);
   k.append((const char*)g.tail, sizeof(int32_t) * g.m);
   k.append((const char*)g.head, sizeof(int32_t) * g.m);
   if (grad)
@@ -931,6 +1080,7 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
     pbat_options oo;
     pbat_options_init(&oo);
     oo.walk_bits = std::min(o.walk_bits >= 0 ? o.walk_bits : kBsbMaxWalk, kBsbMaxWalk);
+    oo.prune = o.prune;   // prune == 2: prune-aware prefix arcs
     int rc = bs_make_plan(g, oo, kBsbThreads, E.plans[i], nullptr);
     if (rc) return rc;
     items[i] = 1ull << E.plans[i].d;

@@ -142,6 +142,7 @@ int validate_options(const pbat_options* o, int m) {
       (o->block_threads < 32 || o->block_threads > 256 || o->block_threads % 32))
     return fail(PBAT_EINVAL, "block_threads=%d must be -1 or a multiple of 32 in [32,256]",
                 o->block_threads);
+  if (o->prune < 0 || o->prune > 2) return fail(PBAT_EINVAL, "prune=%d not in {0,1,2}", o->prune);
   if (!(o->time_budget_s >= 0.0)) return fail(PBAT_EINVAL, "time_budget_s must be >= 0");
   return PBAT_OK;
 }

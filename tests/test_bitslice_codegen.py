@@ -177,16 +177,17 @@ def test_every_template_variant_compiles_with_nvrtc(pb):
     assert ("1", "0", "2") in variants and ("1", "1", "3") in variants and ("0", "1", "3") in variants
 
 
-def test_batched_module_holds_each_network_program(pb):
+@pytest.mark.parametrize("prune", [1, 2])
+def test_batched_module_holds_each_network_program(pb, prune):
     """The batched module's per-network structs carry, in launch order
     (networks with the most work items first), exactly the connectivity
     programs emulated above for the single-network kernel with the batched
     walk length, and the plan constants that go with them."""
     nets, _ = synth.workload_batched(12, 2)
-    bsrc = pb.batch_kernel_source(nets, 2)
+    bsrc = pb.batch_kernel_source(nets, 2, pb.options(prune=prune))
     singles = []
     for net in nets:
-        src = pb.kernel_source(net, pb.options(walk_bits=5, block_threads=128))
+        src = pb.kernel_source(net, pb.options(walk_bits=5, block_threads=128, prune=prune))
         _, D, inv, var = _parse(src)
         singles.append((D, inv.split("\n", 1)[1], var.split("\n", 1)[1]))
     order = sorted(range(len(nets)), key=lambda i: -(1 << singles[i][0]["BS_D"]))
@@ -223,3 +224,79 @@ def test_generated_program_at_maximum_sizes(pb, directed):
         _check(pb, net, 7, pb.options(walk_bits=10), trials=4)
     _nvrtc_compile(pb.kernel_source(big, pb.options(walk_bits=10)))
     _nvrtc_compile(pb.kernel_source(mid, pb.options(walk_bits=10), grad=True))
+
+
+# ---------------------------------------------------------------------------
+# prune-aware prefix arcs (pbat_options.prune == 2)
+# ---------------------------------------------------------------------------
+
+def _prefix_arcs(src):
+    perm, D, _, _ = _parse(src)
+    return [perm[k] for k in range(D["BS_TOP"], D["BS_TOP"] + D["BS_D"])], D
+
+
+def _resolved(net, prefix, values):
+    """Items the monotone prune resolves (oracle connectivity): cut with
+    every other arc working, or connected with every other arc failed."""
+    m = net.m
+    bit = {a: 1 << (m - 1 - a) for a in range(m)}
+    rest = sum(bit[a] for a in range(m) if a not in prefix)
+    n = 0
+    for v in values:
+        on = sum(bit[a] for j, a in enumerate(prefix) if (v >> j) & 1)
+        if not oracle.connected(net, on | rest) or oracle.connected(net, on):
+            n += 1
+    return n
+
+
+@pytest.mark.parametrize("grad", [False, True])
+def test_prune_aware_prefix_resolves_more_items(pb, grad):
+    """On the 34-arc directed network the default roles leave every small
+    s-t cut partly among the walk arcs, so the prune resolves no item; the
+    prune-aware prefix resolves most of them (counted exactly over all 2^14
+    prefix values).  On the 40-arc network (sampled) and the 3x6 grid
+    (exact) it resolves more than the default too."""
+    import random
+    for net, L, sample, floor in ((synth.workload_directed_20_34(), 10, None, 0.9),
+                                  (synth.workload_random_24_40(), 10, 1024, 0.8),
+                                  (synth.workload_grid_3x6(), 5, None, 0.6)):
+        rates = {}
+        for prune in (1, 2):
+            src = pb.kernel_source(net, pb.options(walk_bits=L, prune=prune), grad=grad, p=net.p)
+            pre, D = _prefix_arcs(src)
+            vals = (range(1 << len(pre)) if sample is None
+                    else random.Random(5).sample(range(1 << len(pre)), sample))
+            rates[prune] = _resolved(net, pre, vals) / len(vals)
+        assert rates[2] >= floor and rates[2] > rates[1], (net.name, rates)
+
+
+def test_prune_aware_plans_are_exact_and_deterministic(pb):
+    """Plans of the prune-aware mode: the emulated connectivity program
+    matches the oracle, the role invariants hold (including a range and a
+    gradient walk shortened by arcs with p at 0 or 1, whose extra prefix arcs
+    come from the remaining ones), and planning twice gives the same
+    source."""
+    for seed in range(8):
+        rng = synth.SplitMix64(5150 + seed)
+        net = synth.random_small(5200 + seed, n=4 + rng.below(12), m=12 + rng.below(30),
+                                 directed=bool(seed & 1))
+        for walk in (-1, 4, 10):
+            _check(pb, net, seed, pb.options(walk_bits=walk, prune=2), trials=3)
+    net = synth.workload_random_24_40()
+    _check(pb, net, 2, pb.options(prune=2, range_bits=6, range_lo=5, range_hi=6), trials=3)
+    # most arcs deterministic: too few eligible walk arcs for the fused plan
+    p = [1.0 if k % 4 else 0.7 for k in range(net.m)]
+    for r in (0, 6):
+        o = pb.options(walk_bits=10, prune=2, range_bits=r, range_lo=0, range_hi=1 if r else 0)
+        src = pb.kernel_source(net, o, grad=True, p=p)
+        perm, D, _, _ = _parse(src)
+        m = net.m
+        assert sorted(perm) == list(range(m))
+        assert all(perm[m - 1 - i] == i for i in range(r))
+        walk = [perm[k] for k in range(D["BS_ELL"] + D["BS_TB"], D["BS_TOP"])]
+        assert all(0 < p[a] < 1 for a in walk)
+        assert D["BS_ELL"] + D["BS_TB"] + D["BS_L"] + D["BS_D"] == m
+        assert D["BS_L"] < 10     # the shortened walk: extra prefix arcs were needed
+        assert src == pb.kernel_source(net, o, grad=True, p=p)
+    with pytest.raises(pb.PbatError):
+        pb.kernel_source(net, pb.options(prune=3))
