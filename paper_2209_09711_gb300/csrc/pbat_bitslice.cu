@@ -195,55 +195,77 @@ static std::vector<int> bfs_dist(const GraphIn& g, int src) {
 // 2^(m-d) states of work whatever its probability).
 class PruneScorer {
  public:
-  PruneScorer(const GraphIn& g, int n_samples) : g_(g) {
+  // kWords words of 64 prefix values each are scored at once, bit-sliced:
+  // every arc's state across 64 values is one word
+  static constexpr int kWords = 16;
+  explicit PruneScorer(const GraphIn& g) : g_(g) {
     uint64_t x = 0x2209097110ull;   // fixed: plans must be reproducible
-    for (int i = 0; i < n_samples; ++i) {
-      x += 0x9e3779b97f4a7c15ull;    // splitmix64
-      uint64_t z = x;
-      z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-      z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-      samples_.push_back(z ^ (z >> 31));
-    }
-  }
-  // s-t reachability with the arcs of `on` working
-  bool conn(uint64_t on) const {
-    uint64_t seen = 1ull << g_.source;
-    for (bool grew = true; grew;) {
-      grew = false;
-      for (int k = 0; k < g_.m; ++k) {
-        if (!((on >> k) & 1)) continue;
-        const int u = g_.tail[k], v = g_.head[k];
-        if (((seen >> u) & 1) && !((seen >> v) & 1)) seen |= 1ull << v, grew = true;
-        if (!g_.directed && ((seen >> v) & 1) && !((seen >> u) & 1)) seen |= 1ull << u, grew = true;
+    uint64_t v[64];
+    for (int w = 0; w < kWords; ++w) {
+      for (int i = 0; i < 64; ++i) {
+        x += 0x9e3779b97f4a7c15ull;  // splitmix64
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        v[i] = z ^ (z >> 31);
       }
-      if ((seen >> g_.sink) & 1) return true;
+      for (int j = 0; j < 64; ++j) {   // sample word: bit i = bit j of value i
+        uint64_t t = 0;
+        for (int i = 0; i < 64; ++i) t |= ((v[i] >> j) & 1ull) << i;
+        sample_[w][j] = t;
+      }
     }
-    return false;
   }
-  // items resolved by the prune, over every value of a small prefix or the
-  // fixed sample of a large one
+  // items resolved by the prune -- cut with every other arc working, or
+  // connected with every other arc failed -- over every value of a prefix
+  // of at most 10 arcs, else over the fixed sample of kWords * 64 values
   int score(const std::vector<int>& pre) const {
     const int d = (int)pre.size();
-    uint64_t pmask = 0;
-    for (int a : pre) pmask |= 1ull << a;
-    const uint64_t all = g_.m >= 64 ? ~0ull : ((1ull << g_.m) - 1);
-    const bool exact = d <= 30 && (1ull << d) <= samples_.size();
-    const uint64_t n = exact ? (1ull << d) : samples_.size();
+    const bool exact = d <= 10;
+    const int nw = exact ? std::max(1, (1 << d) / 64) : kWords;
+    const uint64_t valid = exact && d < 6 ? ((1ull << (1 << d)) - 1) : ~0ull;
+    uint64_t up[64], dn[64];
     int res = 0;
-    for (uint64_t i = 0; i < n; ++i) {
-      const uint64_t v = exact ? i : samples_[i];
-      uint64_t on = 0;
-      for (int j = 0; j < d; ++j)
-        if ((v >> j) & 1) on |= 1ull << pre[j];
-      if (!conn(on | (all & ~pmask))) ++res;
-      else if (conn(on)) ++res;
+    for (int w = 0; w < nw; ++w) {
+      for (int k = 0; k < g_.m; ++k) up[k] = ~0ull, dn[k] = 0ull;
+      for (int j = 0; j < d; ++j) {
+        const uint64_t b = exact ? exact_word(w, j) : sample_[w][j];
+        up[pre[j]] = dn[pre[j]] = b;
+      }
+      const uint64_t reach_up = reach(up), reach_dn = reach(dn);
+      res += __builtin_popcountll((~reach_up | reach_dn) & valid);
     }
     return res;
   }
 
  private:
+  // bit i of value 64 w + i, bit j
+  static uint64_t exact_word(int w, int j) {
+    static const uint64_t pat[6] = {0xAAAAAAAAAAAAAAAAull, 0xCCCCCCCCCCCCCCCCull,
+                                    0xF0F0F0F0F0F0F0F0ull, 0xFF00FF00FF00FF00ull,
+                                    0xFFFF0000FFFF0000ull, 0xFFFFFFFF00000000ull};
+    return j < 6 ? pat[j] : (((w >> (j - 6)) & 1) ? ~0ull : 0ull);
+  }
+  // s-t reachability of 64 states at once (arc words `on`): a fixed point
+  uint64_t reach(const uint64_t* on) const {
+    uint64_t R[64] = {};
+    R[g_.source] = ~0ull;
+    for (bool grew = true; grew;) {
+      grew = false;
+      for (int k = 0; k < g_.m; ++k) {
+        const int u = g_.tail[k], v = g_.head[k];
+        const uint64_t nv = R[v] | (R[u] & on[k]);
+        if (nv != R[v]) R[v] = nv, grew = true;
+        if (!g_.directed) {
+          const uint64_t nu = R[u] | (R[v] & on[k]);
+          if (nu != R[u]) R[u] = nu, grew = true;
+        }
+      }
+    }
+    return R[g_.sink];
+  }
   const GraphIn& g_;
-  std::vector<uint64_t> samples_;
+  uint64_t sample_[kWords][64];
 };
 
 static std::vector<int> bfs_dist(const GraphIn& g, int src);
@@ -290,19 +312,20 @@ static std::vector<int> bs_prune_prefix_search(const GraphIn& g, const std::vect
   std::vector<int> chosen(order.begin(), order.begin() + want);
   std::vector<int> others(order.begin() + want, order.end());
   if (chosen.empty() || others.empty()) return chosen;
-  const PruneScorer sc(g, 256);
+  const PruneScorer sc(g);
   auto full = [&](const std::vector<int>& ch) {
     std::vector<int> pre = fixed;
     pre.insert(pre.end(), ch.begin(), ch.end());
     return pre;
   };
   int best = sc.score(full(chosen));
-  // first-improvement swaps in a fixed order, at most 1500 evaluations
+  // first-improvement swaps in a fixed order, at most kMaxEvals evaluations
+  constexpr int kMaxEvals = 20000;
   int evals = 0;
-  for (bool improved = true; improved && evals < 1500;) {
+  for (bool improved = true; improved && evals < kMaxEvals;) {
     improved = false;
-    for (size_t i = 0; i < chosen.size() && !improved && evals < 1500; ++i)
-      for (size_t o = 0; o < others.size() && evals < 1500; ++o) {
+    for (size_t i = 0; i < chosen.size() && !improved && evals < kMaxEvals; ++i)
+      for (size_t o = 0; o < others.size() && evals < kMaxEvals; ++o) {
         std::vector<int> trial = chosen;
         trial[i] = others[o];
         const int sc_t = sc.score(full(trial));
