@@ -393,6 +393,48 @@ static bool bs_walk_ok(const double* p, int a) {
   return !p || (p[a] >= 0x1p-20 && p[a] <= 1.0 - 0x1p-20);
 }
 
+// Prune-aware mode: with the prefix arcs fixed, the walk cluster may sit
+// anywhere among the other arcs.  Grow one from every eligible seed arc (the
+// arc first, then the arcs adding the fewest new core nodes), generate each
+// program and keep the one with the fewest operations per word (then per
+// item).  Lane and thread arcs take what is left, in input order.
+static void bs_smaller_walk(const GraphIn& g, BsPlan& bp, const double* p_for_grad) {
+  const int m = g.m, w0 = bp.ell + bp.tb, top = w0 + bp.L;
+  std::vector<int> pool(bp.perm.begin(), bp.perm.begin() + top);   // lane, thread, walk arcs
+  std::sort(pool.begin(), pool.end());
+  BsPlan best = bp;
+  for (int seed : pool) {
+    if (!bs_walk_ok(p_for_grad, seed)) continue;
+    std::vector<bool> incore(g.n, false), used(m, false);
+    incore[g.source] = incore[g.sink] = true;
+    std::vector<int> walk{seed};
+    used[seed] = true;
+    incore[g.tail[seed]] = incore[g.head[seed]] = true;
+    while ((int)walk.size() < bp.L) {
+      int pick = -1, bscore = 1 << 30;
+      for (int a : pool) {
+        if (used[a] || !bs_walk_ok(p_for_grad, a)) continue;
+        const int add = (!incore[g.tail[a]]) + (!incore[g.head[a]]);
+        if (add < bscore) bscore = add, pick = a;
+      }
+      if (pick < 0) break;
+      used[pick] = true;
+      walk.push_back(pick);
+      incore[g.tail[pick]] = incore[g.head[pick]] = true;
+    }
+    if ((int)walk.size() < bp.L) continue;
+    BsPlan t = bp;
+    int x = 0;
+    for (int a : pool)
+      if (!used[a]) t.perm[x++] = a;
+    for (int b = 0; b < bp.L; ++b) t.perm[w0 + b] = walk[b];
+    bs_generate(g, t);
+    if (t.ops_var < best.ops_var || (t.ops_var == best.ops_var && t.ops_inv < best.ops_inv))
+      best = std::move(t);
+  }
+  bp = std::move(best);
+}
+
 int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
                  const double* p_for_grad) {
   const int m = g.m, r = o.range_bits;
@@ -487,6 +529,7 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
     return fail(PBAT_EINVAL, "internal: inconsistent bit-sliced plan (m=%d r=%d L=%d d=%d)", m, r,
                 bp.L, bp.d);
   bs_generate(g, bp);
+  if (o.prune == 2 && bp.L > 0 && extra == 0) bs_smaller_walk(g, bp, p_for_grad);
   return PBAT_OK;
 }
 

@@ -274,8 +274,8 @@ def test_prune_aware_plans_are_exact_and_deterministic(pb):
     """Plans of the prune-aware mode: the emulated connectivity program
     matches the oracle, the role invariants hold (including a range and a
     gradient walk shortened by arcs with p at 0 or 1, whose extra prefix arcs
-    come from the remaining ones), and planning twice gives the same
-    source."""
+    come from the remaining ones), planning twice gives the same source, and
+    the generated kernels compile."""
     for seed in range(8):
         rng = synth.SplitMix64(5150 + seed)
         net = synth.random_small(5200 + seed, n=4 + rng.below(12), m=12 + rng.below(30),
@@ -300,3 +300,7 @@ def test_prune_aware_plans_are_exact_and_deterministic(pb):
         assert src == pb.kernel_source(net, o, grad=True, p=p)
     with pytest.raises(pb.PbatError):
         pb.kernel_source(net, pb.options(prune=3))
+    # the mode's programs (walk cluster chosen for the fewest operations) compile
+    for big in (synth.workload_random_24_40(), synth.workload_directed_20_34()):
+        _nvrtc_compile(pb.kernel_source(big, pb.options(walk_bits=10, prune=2), grad=True, p=big.p))
+        _nvrtc_compile(pb.kernel_source(big, pb.options(walk_bits=10, prune=2)))
