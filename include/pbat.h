@@ -32,6 +32,11 @@
  *   - Every call returns PBAT_OK (0) or a negative PBAT_E* code.  On error no
  *     output array is written, and pbat_last_error() (thread-local) gives a
  *     one-line reason.  No C++ exception crosses this boundary.
+ *   - Environment: PBAT_AUTOTUNE_CACHE names a file that keeps the
+ *     autotuner's choices across processes.  PBAT_FAULT, for failure-
+ *     detection tests, lists host-side sites to fail ("plan", "compile",
+ *     "alloc", "launch", comma-separated): each fails as its real call can,
+ *     with the same error code, before any GPU work of that step.
  *   - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
  *     The calls are synchronous: they return after the results are on the
  *     host.  Calls are re-entrant; concurrent calls from several host

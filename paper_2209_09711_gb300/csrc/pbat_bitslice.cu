@@ -437,6 +437,7 @@ static void bs_smaller_walk(const GraphIn& g, BsPlan& bp, const double* p_for_gr
 
 int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
                  const double* p_for_grad) {
+  if (fault_at("plan")) return fail(PBAT_EINVAL, "injected fault: planning");
   const int m = g.m, r = o.range_bits;
   bp.r = r;
   bp.grad = p_for_grad != nullptr;
@@ -620,6 +621,7 @@ static void jit_precompile(const std::vector<std::string>& srcs, int cc) {
 
 static int jit_compile(const std::string& src, const DeviceInfo& dev, const char* kname,
                        JitEntry* out) {
+  if (fault_at("compile")) return fail(PBAT_ECUDA, "injected fault: NVRTC compile");
   std::lock_guard<std::mutex> lk(g_jit_mu);
   auto it = g_jit.find(src);
   if (it != g_jit.end()) {
@@ -1521,6 +1523,7 @@ int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, cons
                        cudaGetErrorString(cudaGetLastError())));
     }
   }
+  if (fault_at("launch")) return done(fail(PBAT_ECUDA, "injected fault: kernel launch"));
   if (cudaGraphLaunch(E->exec, st) != cudaSuccess)
     return done(fail(PBAT_ECUDA, "graph launch failed: %s", cudaGetErrorString(cudaGetLastError())));
   if (cudaMemcpyAsync(h + E->o_limbs, d + E->o_limbs, E->o_end - E->o_limbs, cudaMemcpyDeviceToHost,

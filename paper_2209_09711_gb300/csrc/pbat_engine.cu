@@ -84,6 +84,22 @@ int fail(int code, const char* fmt, ...) {
 }
 
 void clear_error() { t_last_error.clear(); }
+
+// Host-side fault injection, for failure-detection tests: PBAT_FAULT holds a
+// comma-separated list of sites -- "plan", "compile", "alloc", "launch" --
+// and a listed site fails the way its real call can, with the same error
+// code, before any GPU work of that step.  Nothing on the device is faulted.
+bool fault_at(const char* site) {
+  const char* f = getenv("PBAT_FAULT");
+  if (!f || !*f) return false;
+  const size_t n = strlen(site);
+  for (const char* q = f; (q = strstr(q, site)) != nullptr; q += n) {
+    const bool starts = q == f || q[-1] == ',';
+    const bool ends = q[n] == '\0' || q[n] == ',';
+    if (starts && ends) return true;
+  }
+  return false;
+}
 const char* last_error() { return t_last_error.c_str(); }
 
 #define PBAT_CUDA(call)                                                                   \
@@ -159,6 +175,7 @@ static bool walk_ok(double p) {  // the gradient divides walk masses by p and 1 
 
 int make_plan(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
               const DeviceInfo& dev, Plan& pl) {
+  if (fault_at("plan")) return fail(PBAT_EINVAL, "injected fault: planning");
   const int m = g.m;
   const int r = o.range_bits;
   pl.grad = grad;
@@ -322,6 +339,7 @@ int device_info(DeviceInfo& out) {
 static std::vector<Scratch*> g_pool;
 
 int scratch_acquire(int device, size_t dbytes, size_t hbytes, Scratch** out) {
+  if (fault_at("alloc")) return fail(PBAT_ENOMEM, "injected fault: device scratch allocation");
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto* s : g_pool) {
@@ -778,6 +796,7 @@ static void event_pairs_release(int device, std::vector<std::pair<cudaEvent_t, c
 // Launch the enumeration (and, for the frontier kernel, the reduction);
 // asynchronous.
 int job_launch(Job* J, cudaStream_t st) {
+  if (fault_at("launch")) return fail(PBAT_ECUDA, "injected fault: kernel launch");
   PBAT_CUDA(cudaMemsetAsync(J->W.counter, 0, J->reset_bytes, st));  // counter, status, stats, results
   const bool timed = J->n_pending < 65536;
   if (timed && J->n_pending == J->evs.size()) {

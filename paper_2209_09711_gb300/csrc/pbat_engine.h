@@ -59,6 +59,7 @@ int run_single(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
 
 int fail(int code, const char* fmt, ...);
 void clear_error();
+bool fault_at(const char* site);   // PBAT_FAULT host-side fault injection
 const char* last_error();
 int validate_graph(const GraphIn& g);
 int validate_p(const double* p, int m);

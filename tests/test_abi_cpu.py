@@ -90,3 +90,25 @@ def test_no_gpu_gives_ecuda_not_a_crash(lib):
     with pytest.raises(lib.PbatError) as e:
         lib.reliability(4, [0, 0, 1, 1, 2], [1, 2, 2, 3, 3], [0.9] * 5, 0, 3)
     assert "PBAT_ECUDA" in str(e.value)
+
+
+def test_host_fault_injection_at_planning(lib, monkeypatch):
+    """PBAT_FAULT injects failures on the host only.  The planning site is
+    reachable without a GPU (the kernel-source diagnostics plan the network):
+    it fails with its error code and message while listed, exact site names
+    only, and the next call without it succeeds."""
+    import synth
+    net = synth.workload_grid_3x6()
+    nets, _ = synth.workload_batched(3, 2)
+    good = lib.kernel_source(net)
+    monkeypatch.setenv("PBAT_FAULT", "launch,plan")
+    with pytest.raises(lib.PbatError) as e:
+        lib.kernel_source(net)
+    assert e.value.code == lib.PBAT_EINVAL and "injected fault: planning" in str(e.value)
+    with pytest.raises(lib.PbatError):
+        lib.batch_kernel_source(nets, 2)
+    for other in ("planning", "xplan", "compile,alloc,launch", ""):
+        monkeypatch.setenv("PBAT_FAULT", other)
+        assert lib.kernel_source(net) == good
+    monkeypatch.delenv("PBAT_FAULT")
+    assert lib.kernel_source(net) == good
