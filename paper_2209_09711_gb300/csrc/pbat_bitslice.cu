@@ -591,6 +591,7 @@ static bool nvrtc_cubin(const std::string& src, int cc, std::vector<char>& cubin
 // candidates); the cubins wait for jit_compile.  A failure is left for
 // jit_compile to report when that source is needed.
 static void jit_precompile(const std::vector<std::string>& srcs, int cc) {
+  NvtxRange nv("pbat NVRTC precompile");
   std::vector<const std::string*> todo;
   {
     std::lock_guard<std::mutex> lj(g_jit_mu);
@@ -638,6 +639,7 @@ static int jit_compile(const std::string& src, const DeviceInfo& dev, const char
     }
   }
   if (cubin.empty()) {
+    NvtxRange nv("pbat NVRTC compile");
     std::string err;
     if (!nvrtc_cubin(src, dev.cc_major * 10 + dev.cc_minor, cubin, err))
       return fail(PBAT_ECUDA, "NVRTC compile of the bit-sliced kernel failed: %s", err.c_str());
@@ -1473,6 +1475,7 @@ static int bsb_tune_walk(int G, const pbat_graph* graphs, int K, const double* p
 int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
                    cudaStream_t st, double* R_out, uint64_t* Nk_out, const std::string& key,
                    const DeviceInfo& dev) {
+  NvtxRange nv("pbat batched");
   if (G > kBsbMaxGraphs) return PBAT_ENOTSUP;
   BsBatch* E = nullptr;
   {

@@ -539,6 +539,7 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
   // than 128 and 224 threads the R kernel 7% faster than 256
   if (!large) nts.push_back(64), nts.push_back(96);
   for (int nt : {128, 160, 192, 224, 256}) nts.push_back(nt);
+  NvtxRange nv("pbat autotune");
   std::vector<pbat_options> cands;
   for (int L : Ls)
     for (int nt : nts) {
@@ -594,6 +595,7 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
 }
 
 int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, Job** out) {
+  NvtxRange nv("pbat plan and tables");
   pbat_options o;
   pbat_options_init(&o);
   if (opt) o = *opt;
@@ -796,6 +798,7 @@ static void event_pairs_release(int device, std::vector<std::pair<cudaEvent_t, c
 // Launch the enumeration (and, for the frontier kernel, the reduction);
 // asynchronous.
 int job_launch(Job* J, cudaStream_t st) {
+  NvtxRange nv("pbat launch");
   if (fault_at("launch")) return fail(PBAT_ECUDA, "injected fault: kernel launch");
   PBAT_CUDA(cudaMemsetAsync(J->W.counter, 0, J->reset_bytes, st));  // counter, status, stats, results
   const bool timed = J->n_pending < 65536;
@@ -825,6 +828,7 @@ void job_destroy(Job* J);
 // Copy results to the host and wait; convert to input arc order.
 int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* dRdp_out,
              pbat_options* opt) {
+  NvtxRange nv("pbat read");
   const int m = J->g.m;
   // one copy of counter, status, statistics, N_k and (bit-sliced) the
   // fixed-point results; the frontier kernel's sums come from the reduce
