@@ -36,6 +36,7 @@
 #include "pbat_bs_template.h"
 #include "pbat_engine.h"
 #include "pbat_internal.h"
+#include "pbat_nvtx.h"
 
 namespace pbat {
 

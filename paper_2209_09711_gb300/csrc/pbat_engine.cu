@@ -31,6 +31,7 @@
 #include "pbat.h"
 #include "pbat_engine.h"
 #include "pbat_internal.h"
+#include "pbat_nvtx.h"
 
 namespace pbat {
 

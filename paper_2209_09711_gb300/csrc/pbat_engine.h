@@ -8,21 +8,10 @@
 
 #include <math.h>
 
-#include <nvtx3/nvToolsExt.h>
-
 #include "pbat.h"
 #include "pbat_num.cuh"
 
 namespace pbat {
-
-// NVTX range over a scope, for timelines and profiler filters (header-only
-// NVTX v3: a no-op unless a tool is attached).
-struct NvtxRange {
-  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
-  ~NvtxRange() { nvtxRangePop(); }
-  NvtxRange(const NvtxRange&) = delete;
-  NvtxRange& operator=(const NvtxRange&) = delete;
-};
 
 struct GraphIn {
   int n, m;
