@@ -685,55 +685,12 @@ struct BsLaunch {
 
 // out[v] = product over x < n of (bit x of v ? p : 1 - p) of arc arcs[x], for
 // every v < 2^n, built by doubling: two double-double products per entry.
-static void product_table(const double* p, const int* arcs, int n, dd* out) {
-  out[0] = dd_make(1.0);
-  for (int x = 0; x < n; ++x) {
-    const dd w0 = arc_w(p, arcs[x], 0), w1 = arc_w(p, arcs[x], 1);
-    for (int v = (1 << x) - 1; v >= 0; --v) {
-      out[v + (1 << x)] = dd_mul(out[v], w1);
-      out[v] = dd_mul(out[v], w0);
-    }
-  }
-}
 
 // Byte-table sums from 32 pattern masses w[]: entry (b, v) is the sum of
 // w[8b + x] over the set bits x of v, rounded to 2^62 fixed point.  The
 // masses are rounded once to 2^126 and the subset sums are exact 128-bit
 // integer additions (one per entry, by the lowest set bit).
-static void byte_table_sums(const dd* w, int n_valid, unsigned long long* out, int stride) {
-  uint128_host fw[32];
-  for (int j = 0; j < 32; ++j) {
-    if (j >= n_valid) {
-      fw[j] = 0;
-      continue;
-    }
-    fw[j] = scaled_round_u(w[j].hi, 126);
-    if (w[j].lo > 0)
-      fw[j] += scaled_round_u(w[j].lo, 126);
-    else if (w[j].lo < 0)
-      fw[j] -= scaled_round_u(-w[j].lo, 126);
-  }
-  const uint128_host half = (uint128_host)1 << 63;
-  for (int b = 0; b < 4; ++b) {
-    uint128_host sb[256];
-    sb[0] = 0;
-    out[(size_t)(b * 256) * stride] = 0;
-    for (int v = 1; v < 256; ++v) {
-      sb[v] = sb[v & (v - 1)] + fw[8 * b + __builtin_ctz((unsigned)v)];
-      out[(size_t)(b * 256 + v) * stride] = (unsigned long long)((sb[v] + half) >> 64);
-    }
-  }
-}
 
-static unsigned long long fixed_u64(dd v, int scale) {
-  // round((hi + lo) * 2^scale) for 0 <= v, result < 2^64
-  uint128_host r = scaled_round_u(v.hi, scale);
-  if (v.lo > 0)
-    r += scaled_round_u(v.lo, scale);
-  else if (v.lo < 0)
-    r -= scaled_round_u(-v.lo, scale);
-  return (unsigned long long)r;
-}
 
 static const int kNkShift[6] = {0, 8, 19, 31, 43, 54};
 

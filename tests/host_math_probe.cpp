@@ -9,6 +9,9 @@
 //   L <l0> ... <l7>         limbs256_to_dd(limbs)        -> <hi bits> <lo bits>
 //   B <n> <k>               binom_u64(n, k)              -> <value>
 //   R <x bits>              dd_recip(x)                  -> <hi bits> <lo bits>
+//   P <n> <p bits> x n      product_table over arcs 0..n-1 -> 2^n lines <hi bits> <lo bits>
+//   T <n> <hi lo bits> x n  byte_table_sums(w, n, out, 1)  -> 1024 lines <value>
+//   X <hi bits> <lo bits> <scale>  fixed_u64({hi, lo}, scale) -> <value>
 #include <cstdio>
 #include <cstring>
 
@@ -62,6 +65,37 @@ int main() {
       if (scanf("%llx", &x) != 1) return 1;
       const dd r = dd_recip(dbl(x));
       printf("%llx %llx\n", bits(r.hi), bits(r.lo));
+    } else if (op == 'P') {
+      int n;
+      if (scanf("%d", &n) != 1 || n < 0 || n > 10) return 1;
+      double p[10];
+      int arcs[10];
+      for (int i = 0; i < n; ++i) {
+        unsigned long long b;
+        if (scanf("%llx", &b) != 1) return 1;
+        p[i] = dbl(b);
+        arcs[i] = i;
+      }
+      dd out[1 << 10];
+      product_table(p, arcs, n, out);
+      for (int v = 0; v < (1 << n); ++v) printf("%llx %llx\n", bits(out[v].hi), bits(out[v].lo));
+    } else if (op == 'T') {
+      int n;
+      if (scanf("%d", &n) != 1 || n < 0 || n > 32) return 1;
+      dd w[32];
+      for (int i = 0; i < n; ++i) {
+        unsigned long long h, l;
+        if (scanf("%llx %llx", &h, &l) != 2) return 1;
+        w[i] = dd{dbl(h), dbl(l)};
+      }
+      unsigned long long out[1024];
+      byte_table_sums(w, n, out, 1);
+      for (int i = 0; i < 1024; ++i) printf("%llx\n", out[i]);
+    } else if (op == 'X') {
+      unsigned long long h, l;
+      int sc;
+      if (scanf("%llx %llx %d", &h, &l, &sc) != 3) return 1;
+      printf("%llx\n", fixed_u64(dd{dbl(h), dbl(l)}, sc));
     } else {
       return 2;
     }

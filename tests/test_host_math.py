@@ -42,10 +42,10 @@ def probe(tmp_path_factory):
     exe = str(tmp_path_factory.mktemp("hostmath") / "probe")
     subprocess.check_call([CXX, "-O2", "-std=c++17", "-I", INCLUDE, "-I", CSRC, "-o", exe, PROBE])
 
-    def run(lines):
+    def run(lines, n_out=None):
         out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True,
                              timeout=120, check=True).stdout.split("\n")
-        return [o.split() for o in out[:len(lines)]]
+        return [o.split() for o in out[:len(lines) if n_out is None else n_out]]
     return run
 
 
@@ -151,3 +151,52 @@ def test_reciprocals_of_walk_reliabilities(probe):
     for x, (hs, ls) in zip(xs, out):
         y = Fraction(_dbl(int(hs, 16))) + Fraction(_dbl(int(ls, 16)))
         assert abs(y * Fraction(x) - 1) <= Fraction(1, 2 ** 100), x
+
+
+def test_product_tables_of_arc_reliabilities(probe):
+    """Every pattern's mass over up to 8 arcs, within 2^-100 of the exact
+    product of p and 1 - p (the doubles as given)."""
+    rng = random.Random(19)
+    for n in (0, 1, 3, 5, 8):
+        p = [rng.choice([0.0, 1.0, 0.5, rng.random(), 1 - 2.0 ** -30]) for _ in range(n)]
+        out = probe(["P %d %s" % (n, " ".join(f"{_bits(x):x}" for x in p))], n_out=1 << n)
+        for v, (hs, ls) in enumerate(out):
+            exact = Fraction(1)
+            for i, x in enumerate(p):
+                exact *= Fraction(x) if (v >> i) & 1 else 1 - Fraction(x)
+            got = Fraction(_dbl(int(hs, 16))) + Fraction(_dbl(int(ls, 16)))
+            assert abs(got - exact) <= Fraction(1, 2 ** 100) * max(exact, Fraction(1, 2 ** 900)), (n, v)
+
+
+def test_byte_tables_of_subset_sums(probe):
+    """Lane and thread tables: entry v of byte b is the mass of the patterns
+    in v's set bits at scale 2^62, within half a unit plus the 2^-126
+    roundings of the (at most 8) weights; weights past n_valid count as 0."""
+    rng = random.Random(23)
+    for n in (32, 17, 5, 1):
+        w = []
+        for _ in range(n):
+            hi = rng.random() / 32
+            w.append((hi, (rng.random() - 0.5) * math.ulp(hi)))
+        out = probe(["T %d %s" % (n, " ".join(f"{_bits(h):x} {_bits(l):x}" for h, l in w))],
+                    n_out=1024)
+        vals = [int(x[0], 16) for x in out]
+        for b in range(4):
+            assert vals[b * 256] == 0
+            for v in range(1, 256):
+                exact = sum((Fraction(w[8 * b + i][0]) + Fraction(w[8 * b + i][1])
+                             for i in range(8) if (v >> i) & 1 and 8 * b + i < n), Fraction(0))
+                err = abs(Fraction(vals[b * 256 + v], 2 ** 62) - exact)
+                assert err <= Fraction(1, 2 ** 63) + Fraction(8, 2 ** 127), (n, b, v)
+
+
+def test_fixed_point_rounding_of_double_doubles(probe):
+    rng = random.Random(29)
+    cases = [(1.0, 0.0, 63), (0.5, 2.0 ** -70, 63), (0.0, 0.0, 62)]
+    for _ in range(1000):
+        hi = rng.random()
+        cases.append((hi, (rng.random() - 0.5) * math.ulp(hi) if hi else 0.0, rng.choice((62, 63))))
+    out = probe([f"X {_bits(h):x} {_bits(l):x} {sc}" for h, l, sc in cases])
+    for (h, l, sc), (v,) in zip(cases, out):
+        exact = (Fraction(h) + Fraction(l)) * 2 ** sc
+        assert abs(int(v, 16) - exact) <= 1, (h, l, sc)
