@@ -2,7 +2,7 @@
 //
 // The engine prepends a block of #defines and the graph-specific
 // connectivity functions (bs_inv / bs_var, written by the planner in
-// pbat_bitslice.cu) and compiles the result with NVRTC for sm_103a.
+// pbat_bs_plan.cu) and compiles the result with NVRTC for sm_103a.
 //
 // State layout: bit j of a thread's 32-bit word is the state whose BS_ELL
 // lane arcs follow the bits of j; the BS_TB thread arcs follow the bits of
