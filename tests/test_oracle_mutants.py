@@ -67,6 +67,14 @@ MUTANTS = {
     "division end off by one": (
         "x1 = prefix_hi << (m - prefix_bits);",
         "x1 = (prefix_hi << (m - prefix_bits)) - 1;"),
+    # Sec. 4.3 equal division: the range starts at the wrong state
+    "division start shifted": (
+        "x0 = prefix_lo << (m - prefix_bits);",
+        "x0 = (prefix_lo << (m - prefix_bits)) >> 1;"),
+    # Table 3: the layer a node is placed in
+    "PLSA layer numbered from 0": (
+        "for (i = 0; i < nnxt; ++i) layer_of[nxt[i]] = l;",
+        "for (i = 0; i < nnxt; ++i) layer_of[nxt[i]] = l - 1;"),
     # Sec. 3.2 STEP P2/P3: a state whose sink is one layer away counted as cut
     "sink checked only among earlier layers": (
         "    if (seen[sink]) return 1;\n",
