@@ -440,3 +440,62 @@ def test_planted_mistakes_are_caught():
     only_a2 = (1 - p[0]) * p[1] * (1 - p[2]) * (1 - p[3]) * (1 - p[4]) * (1 - p[5])
     assert abs(w_ok(x17) - only_a2) < 1e-18
     assert abs(w_reversed(x17) - only_a2) > 0.1 * only_a2
+
+
+# ---------------------------------------------------------------------------
+# The 3x6 grid workload at full size (2^27 states)
+# ---------------------------------------------------------------------------
+
+# Values of the 3x6 grid, corner to corner, every p = 0.9, from a separate
+# brute force written before this project's oracle (plain C, its own
+# connectivity search): R to 12 decimals and the whole coefficient list.
+GRID_3X6_R = 0.969984456182
+GRID_3X6_NK = [0] * 7 + [21, 420, 4035, 24635, 106652, 346092, 867889, 1709032, 2659298, 3267444,
+                         3155927, 2388481, 1421756, 669306, 249627, 73359, 16721, 2866, 349, 27, 1]
+
+
+def _grid_division(d):
+    import oracle as orc
+    net = synth.workload_grid_3x6()
+    r = orc.enumerate_states(net, prefix_bits=8, prefix_lo=d, prefix_hi=d + 1, grad=True)
+    return r.R_hilo, r.Nk, r.T1_hilo, r.T0_hilo
+
+
+def test_grid_3x6_full_space_reproduces_independent_values_and_golden_file():
+    """The oracle over all 2^27 states of the grid (equal divisions on a
+    process pool) gives the independent values above, and the stored
+    expected values that the GPU parity tests compare with are exactly what
+    the oracle computes now."""
+    import multiprocessing as mp
+    net = synth.workload_grid_3x6()
+    m = net.m
+    with mp.get_context("spawn").Pool(os.cpu_count() or 1) as pool:
+        parts = pool.map(_grid_division, range(256), chunksize=2)
+
+    def exact(pairs):
+        return sum((Fraction(h) + Fraction(lo) for h, lo in pairs), Fraction(0))
+
+    R = exact([q[0] for q in parts])
+    Nk = [sum(q[1][k] for q in parts) for k in range(m + 1)]
+    assert Nk == GRID_3X6_NK
+    assert abs(float(R) - GRID_3X6_R) <= 5e-13
+    # the polynomial in p = 0.9 from the counts
+    assert abs(float(R) - sum(c * 0.9**k * 0.1 ** (m - k) for k, c in enumerate(Nk))) <= 1e-14
+    rows = _golden("grid-3x6_full.txt")
+    gold = {}
+    for r in rows:
+        gold.setdefault(r[0], []).append(r[1:])
+    gR = Fraction(float.fromhex(gold["R"][0][0])) + Fraction(float.fromhex(gold["R"][0][1]))
+    # the oracle's long double sums of different division sizes round apart
+    # by about 2^-64 of the mass
+    assert abs(gR - R) <= Fraction(1, 2**60) and [int(v) for v in gold["NK"][0]] == Nk
+    for key, idx in (("T1", 2), ("T0", 3)):
+        for i, hi, lo in gold[key]:
+            want = Fraction(float.fromhex(hi)) + Fraction(float.fromhex(lo))
+            assert abs(want - exact([q[idx][int(i)] for q in parts])) <= Fraction(1, 2**59)
+    # every arc's T1 + T0 is the mass of the other arcs' connected half
+    # states: at most 2, and T1 - T0 = dR/dp >= 0 (R is monotone)
+    for i in range(m):
+        t1 = exact([q[2][i] for q in parts])
+        t0 = exact([q[3][i] for q in parts])
+        assert 0 <= t1 - t0 and t1 + t0 <= 2
