@@ -4,14 +4,20 @@
 A step is one pass of the whole enumeration (prefix split, exact monotone
 prune, Gray walk, connectivity of every state, exact accumulation of R,
 N_k and dR/dp into 256-bit fixed-point results) over the 2^m states of the
-workload, with the tables already resident on the device.  ``value`` is
-2^m / device time of the fused R + N_k + dR/dp step (CUDA events on the
-launch stream, L2 flushed by a 256 MiB write between steps, outside the
-events).  ``r_only`` is the same for the R + N_k kernel, and
-``plain_gpu_bat`` for the one-state-per-thread frontier kernel (the plain
-GPU BAT, R and fused).  ``e2e`` times the public C-ABI call with host
-buffers (planning, table build, host -> device and device -> host copies
-included).
+workload, with the tables already resident on the device.  The headline
+workload is the largest single network, 24 nodes and 40 arcs (2^40
+states).  ``value`` is 2^m / device time of the fused R + N_k + dR/dp step
+(CUDA events on the launch stream, L2 flushed by a 256 MiB write between
+steps, outside the events).  ``r_only`` is the same for the R + N_k kernel,
+``unpruned`` the fused kernel with the prune off, and ``plain_gpu_bat`` the
+one-state-per-thread frontier kernel (the plain GPU BAT, R and fused).
+``e2e`` times the public C-ABI call with host buffers (planning, table
+build, host -> device and device -> host copies included).  ``configs``
+holds the same figures for every other workload of the scope: the 8-node
+and 3x6-grid networks, the directed 34-arc network, and the batched
+workload of 64 networks x 16 p-vectors.  ``cpu_baseline`` is the oracle
+timed on the host cores; ``cpu_paper_pbat`` the paper's own PBAT in C on
+every host core (cpu_pbat/).
 
 --impl reference times the CPU oracle (test infrastructure: plain brute
 force, long double) on the host cores over a bounded sample of the same
@@ -24,6 +30,7 @@ states of all replicas over the slowest rank's time ("scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import multiprocessing as mp
 import os
@@ -40,47 +47,59 @@ import synth  # noqa: E402
 
 METRIC = "states/s (2^m/time) for R and R+∇R vs plain GPU BAT, rel err ≤1e-12"
 WORKLOADS = {
+    "random-undirected-n24-m40": synth.workload_random_24_40,
     "grid-3x6": synth.workload_grid_3x6,
     "random-undirected-n8-m16": synth.workload_small_random,
     "random-directed-n20-m34": synth.workload_directed_20_34,
-    "random-undirected-n24-m40": synth.workload_random_24_40,
 }
-DEFAULT_WORKLOAD = "grid-3x6"
+# the largest single-network workload (2^40 states) is the headline; the
+# others (and the batched workload) are reported as sub-records
+DEFAULT_WORKLOAD = "random-undirected-n24-m40"
+BATCHED = "batched-64x16"
+CONFIG_ORDER = ["random-undirected-n8-m16", "grid-3x6", "random-directed-n20-m34", BATCHED,
+                "random-undirected-n24-m40"]
 
-# Launch shapes (walk arcs L, threads per block) the autotuner picked for
-# these workloads on GB300; the bench pins them (unless --autotune) so that
-# the timed launch is the one the instruction counts below were taken from.
+# Launch shapes (walk arcs L, threads per block, prune mode, occupancy) the
+# bench pins per workload and kernel, from shape sweeps on GB300, so that the
+# timed launch is the one the instruction counts below were taken from
+# (--autotune lets the autotuner choose instead).  prune 2 = prune-aware
+# prefix arcs.
 SHAPES = {
-    "grid-3x6": {"fused": (5, 128), "r_only": (5, 64)},
-    "random-directed-n20-m34": {"fused": (10, 256), "r_only": (10, 192)},
-    "random-undirected-n24-m40": {"fused": (10, 160), "r_only": (10, 224)},
+    "random-undirected-n24-m40": {"fused": (10, 256, 2, 2), "r_only": (9, 128, 2, 0)},
+    "random-directed-n20-m34": {"fused": (7, 192, 2, 0), "r_only": (8, 192, 2, 0)},
+    "grid-3x6": {"fused": (5, 128, 1, 0), "r_only": (5, 64, 1, 0)},
 }
 
-# Warp instructions executed per state (smsp__inst_executed.sum of one launch
-# / 2^m) -- the per-unit figure of the issue-rate roofline -- and DRAM bytes
-# per launch (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
-# (kernel, workload, L, threads per block); from one ncu --set full capture
-# of the same launch (the --probe command with the same shape).
-INST_PER_STATE = {
-    ("bs_kernel_grad", "grid-3x6", 5, 128): 0.139708,
-    ("bs_kernel", "grid-3x6", 5, 64): 0.063786,
-    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 0.042332,
-    ("bs_kernel", "random-directed-n20-m34", 10, 192): 0.020323,
-    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 160): 0.093555,
-    ("bs_kernel", "random-undirected-n24-m40", 10, 224): 0.053999,
-}
-DRAM_BYTES_PER_LAUNCH = {
-    ("bs_kernel_grad", "grid-3x6", 5, 128): 114176,
-    ("bs_kernel", "grid-3x6", 5, 64): 43264,
-    ("bs_kernel_grad", "random-directed-n20-m34", 10, 256): 150784,
-    ("bs_kernel", "random-directed-n20-m34", 10, 192): 57600,
-    ("bs_kernel_grad", "random-undirected-n24-m40", 10, 160): 1110528,
-    ("bs_kernel", "random-undirected-n24-m40", 10, 224): 279296,
+# Per generated kernel source (first 16 hex digits of its SHA-256, as
+# pbat_kernel_source returns it): warp instructions executed per state
+# (smsp__inst_executed.sum of one launch / 2^m) -- the per-unit figure of the
+# issue-rate roofline -- and DRAM bytes per launch (dram__bytes_read.sum +
+# dram__bytes_write.sum), from one ncu capture of that launch (bench.py
+# --probe with the same workload and shape; summaries in profiles/).  A
+# kernel whose source has changed since has no entry, and its roofline
+# fraction is reported as null.
+COUNTS = {
 }
 
 SM_COUNT = 152
 ISSUE_PER_SM_CLK = 4          # warp instructions per clock per SM (4 schedulers)
 SM_MAX_MHZ = 2070.0
+
+
+def shape_opts(pb, workload: str, kind: str, **extra):
+    """pbat_options of the pinned shape (the defaults if none is pinned)."""
+    sh = SHAPES.get(workload, {}).get(kind)
+    if sh is None:
+        return pb.options(**extra)
+    kw = dict(walk_bits=sh[0], block_threads=sh[1], prune=sh[2], occupancy=sh[3])
+    kw.update(extra)
+    return pb.options(**kw)
+
+
+def source_key(pb, net, opts, grad: bool) -> str:
+    """Hash of the generated kernel source a plan with these options runs."""
+    src = pb.kernel_source(net, opts, grad=grad, p=net.p)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def workload_config(name: str, net, ws: int, l2: str) -> dict:
@@ -223,6 +242,102 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def _time_plan(plan, steps, warmup, stream, flush, barrier):
+    """Mean step time (CUDA events on the launch stream, L2 flushed between
+    steps outside the events), the plan's own kernel time per launch, the
+    wall time of the timed loop, and the last result."""
+    import torch
+    sp = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.execute(sp)
+        plan.read(sp)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            plan.execute(sp)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        barrier()
+        res = plan.read(sp)
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    kern_ms = res.stats[4] / 1e6 / max(1, res.stats[7])
+    return statistics.mean(step_ms), kern_ms, wall, res
+
+
+def _peak():
+    return SM_COUNT * ISSUE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9  # G warp-inst/s
+
+
+def _roofline(kernel, key, states, kern_ms):
+    """Issue-rate roofline of one kernel launch from its ncu counts."""
+    cnt = COUNTS.get(key)
+    ipc = cnt[0] if cnt else None
+    achieved = ipc * states / (kern_ms / 1e3) / 1e9 if ipc is not None else None
+    return {"bound": "alu", "achieved": achieved, "peak": _peak(), "unit": "Gwarp-inst/s",
+            "frac": achieved / _peak() if achieved is not None else None,
+            "traffic": cnt[1] if cnt else None, "kernel": kernel, "kernel_ms": kern_ms,
+            "source_key": key, "counts_from": cnt[2] if cnt else "no capture of this source",
+            "peak_source": "4 warp-inst/clk/SM x 152 SMs x 2070 MHz (derived)"}
+
+
+def _single_record(pb, name, steps, warmup, stream, flush, barrier, ws):
+    """Fused and R-only kernels of one network at its pinned shapes."""
+    net = WORKLOADS[name]()
+    states = 2**net.m
+    rec = {"workload": name, "n": net.n, "m": net.m, "directed": bool(net.directed),
+           "states": states}
+    out = {}
+    for kind, grad, kernel in (("fused", True, "bs_kernel_grad"), ("r_only", False, "bs_kernel")):
+        opts = shape_opts(pb, name, kind)
+        key = source_key(pb, net, opts, grad)
+        plan = pb.Plan(net, grad=grad, opts=opts, stream=stream.cuda_stream)
+        ms, kern, _, res = _time_plan(plan, steps, warmup, stream, flush, barrier)
+        out[kind] = res
+        rec[kind] = {"value": ws * states / (ms / 1e3), "ms_per_step": ms, "kernel_ms": kern,
+                     "shape": dict(plan.describe(), prune=opts.prune, occupancy=opts.occupancy),
+                     "walked_fraction": res.stats[0] / states,
+                     "roofline": _roofline(kernel, key, states, kern)}
+        plan.close()
+    assert out["fused"].Nk == out["r_only"].Nk, f"{name}: kernels disagree on N_k"
+    rec["fused_over_r_only_time"] = rec["fused"]["ms_per_step"] / rec["r_only"]["ms_per_step"]
+    rec["R"] = out["fused"].R
+    return rec
+
+
+def _batched_record(pb, steps, warmup, stream, ws):
+    """The batched workload: 64 networks x 16 p-vectors through
+    pbat_reliability_batched (one persistent launch replayed from a CUDA
+    graph).  Device time from the library's events around the graph launch;
+    the call time includes tables, upload and read-back."""
+    import torch
+    nets, pvecs = synth.workload_batched()
+    K = len(pvecs[0])
+    states = sum(2**n.m for n in nets)
+    o = pb.options()
+    dev_ms, call_ms = [], []
+    for i in range(warmup + steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        R, Nk, _ = pb.reliability_batched(nets, pvecs, opts=o, stream=stream.cuda_stream)
+        t1 = time.perf_counter()
+        if i >= warmup:
+            dev_ms.append(o.stats[4] / 1e6)
+            call_ms.append(1e3 * (t1 - t0))
+    ms = statistics.mean(dev_ms)
+    return {"workload": BATCHED, "networks": len(nets), "p_vectors": K, "states": states,
+            "outputs": "R per (network, p-vector), N_k per network",
+            "value": ws * states / (ms / 1e3), "pairs_per_s": ws * states * K / (ms / 1e3),
+            "ms_per_step": ms, "call_ms": statistics.mean(call_ms),
+            "kernel": "bs_batch (one persistent launch, CUDA graph replay)", "R00": float(R[0][0])}
+
+
 def run_ours(a):
     import torch
     ws, rank, local = _dist()
@@ -241,7 +356,8 @@ def run_ours(a):
     build.build()
     import paper_2209_09711_gb300 as pb
 
-    net = WORKLOADS[a.workload]()
+    name = a.workload
+    net = WORKLOADS[name]()
     m = net.m
     states = 2**m
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -253,53 +369,31 @@ def run_ours(a):
         if ws > 1:
             torch.distributed.barrier()
 
-    def time_plan(plan, steps, warmup):
-        with torch.cuda.stream(stream):
-            for _ in range(warmup):
-                plan.execute(sp)
-            plan.read(sp)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(steps)]
-            barrier()
-            torch.cuda.synchronize()
-            w0 = time.perf_counter()
-            for i in range(steps):
-                flush.zero_()
-                ev[i][0].record(stream)
-                plan.execute(sp)
-                ev[i][1].record(stream)
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - w0
-            barrier()
-            res = plan.read(sp)
-        step_ms = [s.elapsed_time(e) for s, e in ev]
-        kern_ms = res.stats[4] / 1e6 / max(1, res.stats[7])
-        return statistics.mean(step_ms), kern_ms, wall, res
-
     sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit()
                            else local)
-    shp = {} if a.autotune else dict(SHAPES.get(a.workload, {}))
-    if a.walk_bits is not None and a.block_threads is not None:
-        shp["fused"] = (a.walk_bits, a.block_threads)
 
-    def opts_for(kind):
-        if kind not in shp:
-            return pb.options()
-        return pb.options(walk_bits=shp[kind][0], block_threads=shp[kind][1])
+    def opts_for(kind, **extra):
+        if a.autotune:
+            return pb.options(**extra)
+        o = shape_opts(pb, name, kind, **extra)
+        if kind == "fused" and a.walk_bits is not None:
+            o.walk_bits = a.walk_bits
+        if kind == "fused" and a.block_threads is not None:
+            o.block_threads = a.block_threads
+        return o
 
-    fused = pb.Plan(net, grad=True, opts=opts_for("fused"), stream=sp)
-    ms_f, kern_f, wall_f, res_f = time_plan(fused, a.steps, a.warmup)
+    f_opts = opts_for("fused")
+    fused = pb.Plan(net, grad=True, opts=f_opts, stream=sp)
+    ms_f, kern_f, wall_f, res_f = _time_plan(fused, a.steps, a.warmup, stream, flush, barrier)
     clocks = sampler.stop()
-    # the same fused kernel with the prune off: every state walked
-    if "fused" in shp:
-        nopr_opts = pb.options(walk_bits=shp["fused"][0], block_threads=shp["fused"][1], prune=0)
-    else:
-        nopr_opts = pb.options(prune=0)
-    nopr = pb.Plan(net, grad=True, opts=nopr_opts, stream=sp)
-    ms_np, kern_np, _, res_np = time_plan(nopr, max(3, a.steps // 10), min(a.warmup, 3))
-    ronly = pb.Plan(net, grad=False, opts=opts_for("r_only"), stream=sp)
-    ms_r, kern_r, _, res_r = time_plan(ronly, a.steps, a.warmup)
+    # the same fused kernel with the monotone prune off: every state walked
+    nopr = pb.Plan(net, grad=True, opts=opts_for("fused", prune=0), stream=sp)
+    ms_np, kern_np, _, res_np = _time_plan(nopr, max(3, a.steps // 10), min(a.warmup, 3), stream,
+                                           flush, barrier)
+    r_opts = opts_for("r_only")
+    ronly = pb.Plan(net, grad=False, opts=r_opts, stream=sp)
+    ms_r, kern_r, _, res_r = _time_plan(ronly, a.steps, a.warmup, stream, flush, barrier)
     # the plain GPU BAT: one state per thread, per-state PLSA frontier
     # expansion; above 2^34 states it runs on the first of 2^(m-34) equal
     # divisions (same per-state work) so that the bench stays within minutes
@@ -308,17 +402,21 @@ def run_ours(a):
         else dict(algo=pb.ALGO_FRONTIER)
     plain_states = states >> plain_rb
     plain = pb.Plan(net, grad=False, opts=pb.options(**popt), stream=sp)
-    ms_p, kern_p, _, res_p = time_plan(plain, max(3, a.steps // 10), min(a.warmup, 3))
+    ms_p, _, _, res_p = _time_plan(plain, max(3, a.steps // 10), min(a.warmup, 3), stream, flush,
+                                   barrier)
     plain_g = pb.Plan(net, grad=True, opts=pb.options(**popt), stream=sp)
-    ms_pg, kern_pg, _, res_pg = time_plan(plain_g, max(3, a.steps // 10), min(a.warmup, 3))
+    ms_pg, _, _, res_pg = _time_plan(plain_g, max(3, a.steps // 10), min(a.warmup, 3), stream,
+                                     flush, barrier)
     assert res_r.Nk == res_f.Nk == res_np.Nk, "kernels disagree on N_k"
     if not plain_rb:
         assert res_r.Nk == res_p.Nk == res_pg.Nk, "kernels disagree on N_k"
 
-    # e2e: the public call with host buffers, copies included
+    # e2e: the public call with host buffers, default options (the first
+    # warm-up call runs the autotuner), copies included
     e2e_t = []
     o = pb.options()
-    for i in range(a.warmup + a.steps):
+    n_e2e = min(a.steps, 10)
+    for i in range(a.warmup + n_e2e):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = pb.reliability_net(net, grad=True, opts=o, stream=sp)
@@ -326,6 +424,19 @@ def run_ours(a):
         if i >= a.warmup:
             e2e_t.append(t1 - t0)
     e2e_s = statistics.mean(e2e_t)
+    assert r.Nk == res_f.Nk, "the public call disagrees with the timed plan on N_k"
+
+    # every other workload of the scope, at its pinned shapes
+    configs = []
+    if not a.no_configs:
+        for cname in CONFIG_ORDER:
+            if cname == name:
+                continue
+            if cname == BATCHED:
+                configs.append(_batched_record(pb, min(a.steps, 10), min(a.warmup, 3), stream, ws))
+            else:
+                configs.append(_single_record(pb, cname, min(a.steps, 20), min(a.warmup, 3), stream,
+                                              flush, barrier, ws))
 
     if ws > 1:
         t = torch.tensor([ms_f, ms_r, e2e_s, ms_p, ms_pg], dtype=torch.float64, device=dev)
@@ -336,43 +447,42 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
         return 0
 
-    cpu = None
+    cpu = cpu_paper = None
     if pool is not None:
-        rate, info = oracle_rate(a.workload, a.cpu_seconds, pool, cores)
+        rate, info = oracle_rate(name, a.cpu_seconds, pool, cores)
         pool.close()
         cpu = {"value": rate, "unit": "states/s", "cores": cores, "kind": "oracle",
                "sample": f"{info['divisions']} equal divisions x {info['division_states']} states "
                          f"(R, N_k, T1/T0 gradient), {info['wall_s']:.1f} s wall on {cores} host "
                          f"processes, extrapolated to states/s"}
+        import cpu_pbat
+        prate, pinfo = cpu_pbat.rate(net, a.cpu_seconds, cores, grad=True)
+        cpu_paper = {"value": prate, "unit": "states/s", "cores": cores, "kind": "pbat-cpu",
+                     "what": "the paper's PBAT (Sec. 5.1): equal divisions on POSIX threads, "
+                             "binary-addition order, PLSA test, FP64 Kahan sums; R, N_k and "
+                             "T1/T0 per arc",
+                     "cpu": _cpu_model(),
+                     "sample": f"{pinfo['divisions']} evenly spread equal divisions x "
+                               f"{pinfo['division_states']} states, {pinfo['wall_s']:.1f} s wall on "
+                               f"{cores} threads, extrapolated to states/s"}
 
-    peak = SM_COUNT * ISSUE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9  # G warp-inst/s
-
-    def roofline(kernel, plan, kern_ms):
-        sh = plan.describe()
-        key = (kernel, a.workload, sh["walk_bits"], sh["block_threads"])
-        ipc = INST_PER_STATE.get(key)
-        achieved = ipc * states / (kern_ms / 1e3) / 1e9 if ipc is not None else None
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
-                "frac": achieved / peak if achieved is not None else None,
-                "traffic": DRAM_BYTES_PER_LAUNCH.get(key), "kernel": kernel, "kernel_ms": kern_ms,
-                "peak_source": "4 warp-inst/clk/SM x 152 SMs x 2070 MHz"}
-
-    shape = fused.describe()
-    roof = roofline("bs_kernel_grad", fused, kern_f)
+    roof = _roofline("bs_kernel_grad", source_key(pb, net, f_opts, True), states, kern_f)
     value = ws * states / (ms_f / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_f, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u128", "data": "synthetic",
-        "config": workload_config(a.workload, net, ws,
+        "config": workload_config(name, net, ws,
                                   "flushed between steps (256 MiB write, outside the timed events)"),
         "roofline": roof,
-        "fused_shape": shape,
+        "fused_shape": dict(fused.describe(), prune=f_opts.prune, occupancy=f_opts.occupancy),
         "unpruned": {"value": ws * states / (ms_np / 1e3), "ms_per_step": ms_np, "kernel_ms": kern_np,
                      "what": "the fused kernel with the monotone prune off (every state walked)"},
         "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r,
-                   "kernel": "bs_kernel", "shape": ronly.describe(),
-                   "roofline": roofline("bs_kernel", ronly, kern_r)},
+                   "kernel": "bs_kernel",
+                   "shape": dict(ronly.describe(), prune=r_opts.prune, occupancy=r_opts.occupancy),
+                   "roofline": _roofline("bs_kernel", source_key(pb, net, r_opts, False), states,
+                                         kern_r)},
         "plain_gpu_bat": {"value": ws * plain_states / (ms_p / 1e3), "ms_per_step": ms_p,
                           "kernel": "frontier_kernel (one state per thread, PLSA frontier)",
                           "states": plain_states,
@@ -381,9 +491,12 @@ def run_ours(a):
         "speedup_over_plain_gpu_bat": {"R": (ms_p / plain_states) / (ms_r / states),
                                        "R+grad": (ms_pg / plain_states) / (ms_f / states)},
         "R": res_f.R, "pruned_states": res_f.stats[1], "walked_states": res_f.stats[0],
+        "configs": configs,
         "cpu_baseline": cpu,
+        "cpu_paper_pbat": cpu_paper,
         "e2e": {"value": ws * states / e2e_s, "unit": "states/s",
-                "h2d_bytes_per_step": int(r.stats[2]), "d2h_bytes_per_step": int(r.stats[3])},
+                "h2d_bytes_per_step": int(r.stats[2]), "d2h_bytes_per_step": int(r.stats[3]),
+                "steps": n_e2e, "call": "pbat_reliability_grad, default options (autotuned)"},
         "gpu_launches": int(res_f.stats[5]),
         "clocks": clocks,
         "wall_s_timed": wall_f,
@@ -396,6 +509,18 @@ def run_ours(a):
     return 0
 
 
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def run_probe(a):
     """One untimed launch of one kernel: the program ncu captures."""
     import torch
@@ -403,7 +528,7 @@ def run_probe(a):
     from paper_2209_09711_gb300 import build
     build.build()
     import paper_2209_09711_gb300 as pb
-    net = WORKLOADS[a.workload]()
+    net = WORKLOADS[a.workload]() if a.workload in WORKLOADS else None
     if a.probe == "batched":
         nets, pvecs = synth.workload_batched()
         t0 = time.perf_counter()
@@ -413,19 +538,23 @@ def run_probe(a):
         return 0
     algo = pb.ALGO_FRONTIER if a.probe.startswith("plain") else pb.ALGO_AUTO
     grad = a.probe.endswith("fused")
-    kw = {}
     kind = "fused" if grad else "r_only"
-    if algo == pb.ALGO_AUTO and not a.autotune and kind in SHAPES.get(a.workload, {}):
-        kw["walk_bits"], kw["block_threads"] = SHAPES[a.workload][kind]
+    if algo == pb.ALGO_AUTO and not a.autotune:
+        o = shape_opts(pb, a.workload, kind)
+    else:
+        o = pb.options(algo=algo)
     if a.walk_bits is not None:
-        kw["walk_bits"] = a.walk_bits
+        o.walk_bits = a.walk_bits
     if a.block_threads is not None:
-        kw["block_threads"] = a.block_threads
-    plan = pb.Plan(net, grad=grad, opts=pb.options(algo=algo, **kw))
+        o.block_threads = a.block_threads
+    key = source_key(pb, net, o, grad) if algo == pb.ALGO_AUTO else None
+    plan = pb.Plan(net, grad=grad, opts=o)
     plan.execute(0)
     r = plan.read(0)
-    print(json.dumps({"probe": a.probe, "workload": a.workload, "R": r.R,
-                      "kernel_ms": r.stats[4] / 1e6, "items": r.stats[6], "shape": plan.describe()}))
+    print(json.dumps({"probe": a.probe, "workload": a.workload, "R": r.R, "source_key": key,
+                      "kernel_ms": r.stats[4] / 1e6, "items": r.stats[6], "walked": r.stats[0],
+                      "states": 2**net.m,
+                      "shape": dict(plan.describe(), prune=o.prune, occupancy=o.occupancy)}))
     plan.close()
     return 0
 
@@ -437,11 +566,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0,
-                    help="target wall time of the cpu_baseline oracle sample")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target wall time of each CPU baseline sample (oracle, paper's PBAT)")
     ap.add_argument("--ref-seconds", type=float, default=6.0,
                     help="target wall time of one --impl reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="time the headline workload only (no sub-records of the other workloads)")
     ap.add_argument("--probe", choices=["fused", "r-only", "plain-r-only", "plain-fused", "batched"],
                     help="run one untimed launch of that kernel (for profiler captures)")
     ap.add_argument("--walk-bits", type=int, default=None,

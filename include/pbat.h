@@ -82,6 +82,12 @@ typedef struct pbat_options {
                            block_threads and prefix_bits all -1, time candidate launch
                            shapes once per network structure and keep the fastest
                            (in memory, and in the file named by PBAT_AUTOTUNE_CACHE) */
+  int occupancy;        /* blocks per SM the bit-sliced single-network kernels are compiled
+                           for: k >= 1 gives them __launch_bounds__(threads, k), so the
+                           compiler keeps their registers within 65536 / (k * threads);
+                           0 = the compiler's own register choice; -1 (default) = 0, or
+                           the autotuner's choice when it runs.  Results do not depend on
+                           it. */
   int range_bits;       /* 0 (default) = whole space.  Otherwise only the states whose
                            first range_bits coordinates, read as an integer, lie in
                            [range_lo, range_hi) -- the divisions range_lo..range_hi-1 of
@@ -194,15 +200,19 @@ int pbat_plan_stats(pbat_plan plan, uint64_t* stats_out);
  * routine.  Its scratch is one static 512 KiB device array inside the
  * library, which every GPU that loads the library holds until the process
  * exits.  Limits that follow from that size: opt->walk_bits <= 12 (a larger
- * value returns PBAT_ERANGE), and the persistent grid is capped at the
- * number of per-block partials that fit.  The gradient is not offered here.
+ * value returns PBAT_ERANGE, where pbat_reliability would quietly use 12),
+ * and the persistent grid is capped at the number of per-block partials
+ * that fit.  The gradient is not offered here.
  *   arguments, layout and ownership: as pbat_reliability (host arrays in and
  *   out; opt nullable, algo must be AUTO or FRONTIER; opt->stats untouched)
- * The first call on each device looks up the array's device address (once
- * per device, with that device current); make that first call before any
- * stream capture.  Every call shares the one array: calls whose work
- * overlaps on the GPU (concurrent host threads, or several streams) race
- * and give wrong results, so serialise them.
+ * Every call looks up the array's device address with the caller's device
+ * current (a lookup, no allocation), so a device reset between calls is
+ * harmless.  The call copies through host memory and waits for its stream,
+ * so it must not be called while that stream is being captured into a CUDA
+ * graph: it returns PBAT_ENOTSUP then.  Every call shares the one array;
+ * work of two calls that overlapped on the GPU would race on it, so the
+ * library runs the calls one at a time (a lock held for the whole call).
+ * A call uses a few KiB of the caller's stack.
  */
 int pbat_reliability_noalloc(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,
                              int directed, const double* p, int source, int sink,

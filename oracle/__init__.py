@@ -2,9 +2,13 @@
 
 Plain brute force over all arc states (arXiv 2209.09711 Eq. 1 with the PLSA
 connectivity test of Sec. 3.2), long double with compensated sums, written
-in C (``pbat_oracle.c``) and loaded with ctypes.  Only the tests, the
-package's smoke check and the benchmark's CPU-baseline leg may import this
-module; the product path never does.  It shares no code with the CUDA engine.
+in C (``pbat_oracle.c``) and loaded with ctypes.  For undirected networks
+too large for the brute force, ``factor`` gives the same exact sums by a
+second, independent method (``pbat_factoring.c``: factoring on each arc as a
+dynamic program over frontier partitions), pinned against the brute force.
+Only the tests, the package's smoke check and the benchmark's CPU-baseline
+leg may import this module; the product path never does.  It shares no code
+with the CUDA engine.
 """
 from __future__ import annotations
 
@@ -18,18 +22,28 @@ from typing import List, Optional, Sequence
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pbat_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# the factoring method (pbat_factoring.c), a separate library: independent of
+# the brute force, and left out of the planted-mistake copies of it
+_FSRC = os.path.join(_HERE, "pbat_factoring.c")
+_FLIB = os.path.join(_HERE, "liboracle_factoring.so")
 _lock = threading.Lock()
 _lib = None
+_flib = None
+
+
+def _compile(src: str, lib: str, force: bool) -> str:
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        cc = os.environ.get("CC", "gcc")
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call([cc, "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, lib)
+    return lib
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (no vendor libraries)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cc = os.environ.get("CC", "gcc")
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call([cc, "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
-    return _LIB
+    _compile(_FSRC, _FLIB, force)
+    return _compile(_SRC, _LIB, force)
 
 
 def _load():
@@ -159,3 +173,63 @@ def grad_critical(net, p: Optional[Sequence[float]] = None) -> List[float]:
 
 def long_double_mantissa_bits() -> int:
     return _load().orc_long_double_mant_bits()
+
+
+# ---------------------------------------------------------------------------
+# The factoring method (undirected networks): exact values at full size
+# ---------------------------------------------------------------------------
+
+def _load_factoring():
+    global _flib
+    with _lock:
+        if _flib is None:
+            lib = ctypes.CDLL(_compile(_FSRC, _FLIB, False))
+            I = ctypes.c_int
+            PI = ctypes.POINTER(ctypes.c_int)
+            PD = ctypes.POINTER(ctypes.c_double)
+            PU = ctypes.POINTER(ctypes.c_uint64)
+            lib.orc_factor.argtypes = [I, I, PI, PI, PD, I, I, PD, PD, PU, PI]
+            lib.orc_factor.restype = I
+            _flib = lib
+    return _flib
+
+
+@dataclass
+class FactorResult:
+    R: float
+    R_hilo: tuple
+    Nk: List[int]
+    max_records: int
+
+
+def factor(net, p: Optional[Sequence[float]] = None) -> FactorResult:
+    """R and N_k of an undirected network by factoring (pbat_factoring.c)."""
+    if net.directed:
+        raise ValueError("the factoring method covers undirected networks only")
+    lib = _load_factoring()
+    m = net.m
+    p = list(net.p if p is None else p)
+    Rh, Rl = ctypes.c_double(), ctypes.c_double()
+    Nk = (ctypes.c_uint64 * (m + 1))()
+    mx = ctypes.c_int()
+    r = lib.orc_factor(net.n, m, _ints(net.tail), _ints(net.head), _dbls(p), net.source, net.sink,
+                       ctypes.byref(Rh), ctypes.byref(Rl), Nk, ctypes.byref(mx))
+    if r < 0:
+        raise ValueError({-1: "bad network", -2: "frontier wider than 16 nodes",
+                          -3: "out of memory"}.get(r, str(r)))
+    return FactorResult(Rh.value + Rl.value, (Rh.value, Rl.value), list(Nk), mx.value)
+
+
+def factor_t1t0(net, p: Optional[Sequence[float]] = None):
+    """T1_i = R with p_i = 1 and T0_i = R with p_i = 0, for every arc i (the
+    sums of prod_{j != i} over connected states with x_i = 1 and x_i = 0),
+    by factoring; returned as two lists of (hi, lo) pairs."""
+    p = list(net.p if p is None else p)
+    T1, T0 = [], []
+    for i in range(net.m):
+        q = p[:]
+        q[i] = 1.0
+        T1.append(factor(net, q).R_hilo)
+        q[i] = 0.0
+        T0.append(factor(net, q).R_hilo)
+    return T1, T0

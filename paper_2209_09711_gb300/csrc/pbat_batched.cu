@@ -543,7 +543,7 @@ static double limbs_value(const unsigned long long* limbs) {
 
 int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
                    cudaStream_t st, double* R_out, uint64_t* Nk_out, const std::string& key,
-                   const DeviceInfo& dev);
+                   const DeviceInfo& dev, uint64_t* kernel_ns);
 
 int run_batched(int G, const pbat_graph* graphs, int K, const double* p, pbat_options* opt,
                 void* stream, double* R_out, uint64_t* Nk_out, double* dRdp_out) {
@@ -578,7 +578,8 @@ int run_batched(int G, const pbat_graph* graphs, int K, const double* p, pbat_op
     int nk_total = 0;
     for (int i = 0; i < G; ++i) nk_total += graphs[i].n_arcs + 1;
     Nb.resize(nk_total);
-    rc = run_batched_bs(G, graphs, K, p, o, st, Rb.data(), Nb.data(), key, dev);
+    uint64_t kns = 0;
+    rc = run_batched_bs(G, graphs, K, p, o, st, Rb.data(), Nb.data(), key, dev, &kns);
     if (rc == PBAT_OK) {
       if (dRdp_out) {
         size_t poff = 0;
@@ -597,7 +598,11 @@ int run_batched(int G, const pbat_graph* graphs, int K, const double* p, pbat_op
       }
       memcpy(R_out, Rb.data(), sizeof(double) * Rb.size());
       if (Nk_out) memcpy(Nk_out, Nb.data(), sizeof(uint64_t) * Nb.size());
-      if (opt) opt->stats[5] = (unsigned long long)((K + 15) / 16);
+      if (opt) {
+        opt->stats[4] = kns;   // device time of the batched launch
+        opt->stats[5] = 1;     // one persistent kernel for every p-vector
+        opt->stats[7] = 1;
+      }
       return PBAT_OK;
     }
     if (rc != PBAT_ENOTSUP || o.algo == PBAT_ALGO_BITSLICE) return rc;
@@ -664,7 +669,7 @@ int run_batched(int G, const pbat_graph* graphs, int K, const double* p, pbat_op
     for (int k = 0; k < K; ++k) Rtmp[(size_t)i * K + k] = limbs_value(limbs + ((size_t)i * K + k) * kLimbs);
   std::vector<uint64_t> Ntmp(nk, nk + E->nk_total);
   if (opt) {
-    opt->stats[2] = (unsigned long long)((E->K + kBatchChunk - 1) / kBatchChunk);
+    opt->stats[5] = (unsigned long long)((E->K + kBatchChunk - 1) / kBatchChunk);  // kernels
   }
   done(PBAT_OK);
   if (dRdp_out) {

@@ -219,16 +219,17 @@ static bool acc_in_registers(const BsPlan& bp) { return bp.L <= 6 || bp.ops_var 
 static int walk_unroll_bits(const BsPlan& bp) { return !bp.grad || acc_in_registers(bp) ? 3 : 2; }
 
 static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
-  char defs[640];
+  char defs[700];
   const unsigned lane_mask = bp.ell >= 5 ? 0xffffffffu : ((1u << (1 << bp.ell)) - 1u);
   snprintf(defs, sizeof defs,
            "#define BS_M %d\n#define BS_ELL %d\n#define BS_TB %d\n#define BS_L %d\n#define BS_D %d\n"
            "#define BS_NTHR %d\n#define BS_WALK0 %d\n#define BS_TOP %d\n#define BS_NCORE %d\n"
            "#define BS_LANE_MASK 0x%08xu\n#define BS_FULL_COUNTS 0x%016llxull\n#define BS_GRAD %d\n"
-           "#define BS_ACC_REG %d\n#define BS_IN_BITS %d\n#define BS_THR_MASK 0x%08xu\n",
+           "#define BS_ACC_REG %d\n#define BS_IN_BITS %d\n#define BS_THR_MASK 0x%08xu\n"
+           "#define BS_MINB %d\n",
            g.m, bp.ell, bp.tb, bp.L, bp.d, nthr, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, bp.ncore,
            lane_mask, full_counts(bp.ell), bp.grad ? 1 : 0, acc_in_registers(bp) ? 1 : 0,
-           walk_unroll_bits(bp), bp.tb >= 5 ? 0xffffffffu : ((1u << (1 << bp.tb)) - 1u));
+           walk_unroll_bits(bp), bp.tb >= 5 ? 0xffffffffu : ((1u << (1 << bp.tb)) - 1u), bp.minb);
   const std::string tmpl = kBsTemplate;
   const size_t cut = tmpl.find("//@@GENERATED@@");
   return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tmpl.substr(cut);
@@ -270,6 +271,7 @@ static std::string bs_plan_key(const GraphIn& g, const double* p, bool grad, con
   auto put = [&](long long v) { k.append((const char*)&v, sizeof v); };
   put(device); put(g.n); put(g.m); put(g.directed); put(g.source); put(g.sink); put(grad);
   put(o.walk_bits); put(o.prefix_bits); put(o.range_bits); put(nthr); put(o.prune == 2);
+  put(std::max(0, o.occupancy));
   k.append((const char*)g.tail, sizeof(int32_t) * g.m);
   k.append((const char*)g.head, sizeof(int32_t) * g.m);
   if (grad)
@@ -933,7 +935,7 @@ static int bsb_tune_walk(int G, const pbat_graph* graphs, int K, const double* p
 // frontier kernel).
 int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
                    cudaStream_t st, double* R_out, uint64_t* Nk_out, const std::string& key,
-                   const DeviceInfo& dev) {
+                   const DeviceInfo& dev, uint64_t* kernel_ns) {
   NvtxRange nv("pbat batched");
   if (G > kBsbMaxGraphs) return PBAT_ENOTSUP;
   BsBatch* E = nullptr;
@@ -986,12 +988,33 @@ int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, cons
     }
   }
   if (fault_at("launch")) return done(fail(PBAT_ECUDA, "injected fault: kernel launch"));
-  if (cudaGraphLaunch(E->exec, st) != cudaSuccess)
+  // CUDA events around the replayed graph (its reset and kernel) give the
+  // device time the caller can read from the statistics
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (kernel_ns && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess)) {
+    cudaGetLastError();
+    if (ev0) cudaEventDestroy(ev0);
+    ev0 = ev1 = nullptr;
+  }
+  if (ev0) cudaEventRecord(ev0, st);
+  if (cudaGraphLaunch(E->exec, st) != cudaSuccess) {
+    if (ev0) cudaEventDestroy(ev0), cudaEventDestroy(ev1);
     return done(fail(PBAT_ECUDA, "graph launch failed: %s", cudaGetErrorString(cudaGetLastError())));
+  }
+  if (ev0) cudaEventRecord(ev1, st);
   if (cudaMemcpyAsync(h + E->o_limbs, d + E->o_limbs, E->o_end - E->o_limbs, cudaMemcpyDeviceToHost,
                       st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    if (ev0) cudaEventDestroy(ev0), cudaEventDestroy(ev1);
     return done(fail(PBAT_ECUDA, "batched run failed: %s", cudaGetErrorString(cudaGetLastError())));
+  }
+  if (ev0) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) *kernel_ns = (uint64_t)(ms * 1e6);
+    else cudaGetLastError();
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
   if (*(unsigned int*)(h + E->o_status) & 1u) return done(fail(PBAT_ETIMEOUT, "time budget ran out on the device"));
   const unsigned long long* limbs = (const unsigned long long*)(h + E->o_limbs);
   const unsigned long long* nk = (const unsigned long long*)(h + E->o_nk);

@@ -418,6 +418,7 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
   const int m = g.m, r = o.range_bits;
   bp.r = r;
   bp.grad = p_for_grad != nullptr;
+  bp.minb = std::max(0, o.occupancy);
   bp.ell = std::min(kMaxLaneBits, m - r);
   bp.tb = std::min(5, m - r - bp.ell);
   const int free_bits = m - r - bp.ell - bp.tb;

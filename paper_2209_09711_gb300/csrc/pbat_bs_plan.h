@@ -13,6 +13,7 @@ namespace pbat {
 struct BsPlan {
   bool grad = false;
   int ell = 0, tb = 0, L = 0, d = 0, r = 0;
+  int minb = 0;           // __launch_bounds__ minimum blocks per SM (0: none)
   std::vector<int> perm;  // internal position -> input arc
   std::string gen;        // generated bs_inv / bs_var
   int ncore = 0, ops_inv = 0, ops_var = 0;

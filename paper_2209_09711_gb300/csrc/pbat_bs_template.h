@@ -31,6 +31,13 @@ typedef unsigned int u32;
 typedef unsigned long long u64;
 
 #define BS_IN (BS_L >= BS_IN_BITS ? BS_IN_BITS : BS_L)
+// launch bounds of the single-network kernels: with BS_MINB blocks per SM
+// requested, the compiler keeps registers within 65536 / (BS_MINB * BS_NTHR)
+#if defined(BS_MINB) && BS_MINB > 0
+#define KERNEL_BOUNDS __launch_bounds__(BS_NTHR, BS_MINB)
+#else
+#define KERNEL_BOUNDS __launch_bounds__(BS_NTHR)
+#endif
 #define BS_OUT (BS_L - BS_IN)
 
 struct dd { double hi, lo; };   // host-side double-double (only carried, never computed here)
@@ -255,7 +262,7 @@ __device__ __forceinline__ void bs_write_out(const BsWork& W, const facc* s_acc,
 // ---------------------------------------------------------------------------
 // R + N_k
 // ---------------------------------------------------------------------------
-extern "C" __global__ void __launch_bounds__(BS_NTHR)
+extern "C" __global__ void KERNEL_BOUNDS
 bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
           const u64* __restrict__ wmid_tab, const mx* __restrict__ ptab, BsWork W) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -441,7 +448,7 @@ __device__ __forceinline__ mx bs_arc_factor(const BsParams& P, const mx* __restr
   return f;
 }
 
-extern "C" __global__ void __launch_bounds__(BS_NTHR)
+extern "C" __global__ void KERNEL_BOUNDS
 bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGradParams Q,
                const u64* __restrict__ lane_tab, const u64* __restrict__ thr_tab,
                const u64* __restrict__ wmid128, const mx* __restrict__ ptab,
@@ -473,10 +480,13 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   u64 n_walk = 0, n_full = 0, n_dead = 0;
 #if BS_ACC_REG
   // short items: this lane's accumulators -- R and the two sums of internal
-  // arc `lane` -- in registers, so an item costs no global round trip; arc
-  // lane + 32 (a prefix arc) stays in the global slots.  Long items keep
-  // them all in the global slots: registers are worth more to the walk.
+  // arcs `lane` and `lane + 32` -- in registers, so an item costs no global
+  // round trip.  Long items keep them all in the global slots: registers are
+  // worth more to the walk.
   facc accR = facc{u128{0ull, 0ull}, 0, 0}, accA = accR, accB = accR;
+#if BS_M > 32
+  facc accA2 = accR, accB2 = accR;
+#endif
 #endif
   u32 a[BS_M];
   bs_init_arcs(a, lane);
@@ -490,12 +500,6 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     task = __shfl_sync(0xffffffffu, task, 0);
     if (task >= P.n_tasks) break;
     const u64 prefix = P.task_lo + task;
-#if BS_ACC_REG
-    // the item's prefix factors first: their table loads overlap the walk
-    const mx wpre = bs_prefix_mass(P, ptab, prefix);
-    const mx f0 = bs_arc_factor(P, ptab, ptab_ex, prefix, lane, wpre);
-    const mx f1 = lane + 32 < BS_M ? bs_arc_factor(P, ptab, ptab_ex, prefix, lane + 32, wpre) : wpre;
-#endif
 #pragma unroll
     for (int j = 0; j < BS_D; ++j) a[BS_TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
     const int pc_pre = __popcll((long long)prefix);
@@ -504,6 +508,14 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
       pr = bs_prune(a);
       if (pr == 1) { ++n_dead; continue; }
     }
+#if BS_ACC_REG
+    // the prefix factors of an item that is not cut off, before its walk so
+    // that their table loads overlap it (a cut-off item needs none: with
+    // prune-aware prefix arcs most items are cut off or fully connected)
+    const mx wpre = bs_prefix_mass(P, ptab, prefix);
+    const mx f0 = bs_arc_factor(P, ptab, ptab_ex, prefix, lane, wpre);
+    const mx f1 = lane + 32 < BS_M ? bs_arc_factor(P, ptab, ptab_ex, prefix, lane + 32, wpre) : wpre;
+#endif
     u128 S;      // sum over the warp of T x thread mass, scale 2^124
     // warp sums of the internal arc this lane owns (internal arcs are below
     // 32): the exact pair difference, or for a walk arc A and T - A
@@ -651,13 +663,20 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     }
 #endif
     if (lane + 32 < BS_M) {
+      // arc lane + 32 is a prefix arc (lanes own arcs below 32 and the top
+      // prefix arcs): the item's total, by whether the arc works here
       const int j = lane + 32 - BS_TOP;
+#if BS_ACC_REG && BS_M > 32
+      if ((prefix >> j) & 1ull) facc_add(accA2, mx_prod(f1, S), f1.e);
+      else facc_add(accB2, mx_prod(f1, S), f1.e);
+#else
       facc* ak = acc + 1 + 2 * (lane + 32);
       facc va = ak[0], vb = ak[1];
       if ((prefix >> j) & 1ull) facc_add(va, mx_prod(f1, S), f1.e);
       else facc_add(vb, mx_prod(f1, S), f1.e);
       ak[0] = va;
       ak[1] = vb;
+#endif
     }
     __syncwarp();
   }
@@ -670,6 +689,12 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     acc[1 + 2 * lane] = accA;
     acc[2 + 2 * lane] = accB;
   }
+#if BS_M > 32
+  if (lane + 32 < BS_M) {
+    acc[1 + 2 * (lane + 32)] = accA2;
+    acc[2 + 2 * (lane + 32)] = accB2;
+  }
+#endif
 #endif
   // ---- per block: R, then A_k and B_k of every arc; the host forms the
   // gradient (A - B for prefix arcs, A / p - B / (1 - p) for walk arcs, A

@@ -160,6 +160,8 @@ int validate_options(const pbat_options* o, int m) {
     return fail(PBAT_EINVAL, "block_threads=%d must be -1 or a multiple of 32 in [32,256]",
                 o->block_threads);
   if (o->prune < 0 || o->prune > 2) return fail(PBAT_EINVAL, "prune=%d not in {0,1,2}", o->prune);
+  if (o->occupancy < -1 || o->occupancy > 8)
+    return fail(PBAT_EINVAL, "occupancy=%d not in [-1,8]", o->occupancy);
   if (!(o->time_budget_s >= 0.0)) return fail(PBAT_EINVAL, "time_budget_s must be >= 0");
   return PBAT_OK;
 }
@@ -413,7 +415,10 @@ struct Job {
   unsigned long long* d_wmid64 = nullptr;
   void* d_ptab = nullptr;
   void* d_ptabx = nullptr;
-  double abs_err_bound = 0.0;  // of R, relative to the enumerated probability mass
+  // absolute error bounds of R and of each dR/dp_k, in units of the
+  // enumerated probability mass (the rounding of the fixed-point tables)
+  double abs_err_bound = 0.0;
+  double grad_err_bound = 0.0;
   double mass = 1.0;           // probability mass of the enumerated states
   std::vector<int> perm;       // internal arc position -> input arc
   unsigned long long item_states = 0, n_items = 0;
@@ -453,23 +458,27 @@ int job_launch(Job* J, cudaStream_t st);
 void job_destroy(Job* J);
 
 // ---------------------------------------------------------------------------
-// autotuner: walk length L and block shape of the bit-sliced kernel
+// autotuner: planning mode, walk length L, block shape and occupancy of the
+// bit-sliced kernel
 // ---------------------------------------------------------------------------
-// Candidates around the planner's default are timed on the real problem
-// (CUDA events around the kernel, best of two launches) and the fastest is
-// kept per network structure, mode and range -- in memory, and in the file
-// named by PBAT_AUTOTUNE_CACHE if that is set ("key walk_bits block_threads"
-// lines).  Only problems of at least 2^26 states are tuned: below that a
-// launch is too short for the choice to matter.
+// Candidates are timed on the real problem (CUDA events around the kernel,
+// best of two launches) and the fastest is kept per network structure, mode
+// and range -- in memory, and in the file named by PBAT_AUTOTUNE_CACHE if
+// that is set ("key walk_bits block_threads prune occupancy" lines).  Only
+// problems of at least 2^26 states are tuned: below that a launch is too
+// short for the choice to matter.
+struct TuneChoice {
+  int L, nt, prune, occ;
+};
 static std::mutex g_tune_mu;
-static std::map<std::string, std::pair<int, int>> g_tune;
+static std::map<std::string, TuneChoice> g_tune;
 static bool g_tune_loaded = false;
 
 static std::string tune_key(const GraphIn& g, bool grad, const pbat_options& o, int device) {
-  char head[160];
-  snprintf(head, sizeof head, "d%d:g%d:n%d:m%d:dir%d:s%d:t%d:r%d:%llx:%llx:pr%d:", device,
+  char head[180];
+  snprintf(head, sizeof head, "d%d:g%d:n%d:m%d:dir%d:s%d:t%d:r%d:%llx:%llx:pr%d:oc%d:", device,
            grad ? 1 : 0, g.n, g.m, g.directed ? 1 : 0, g.source, g.sink, o.range_bits,
-           (unsigned long long)o.range_lo, (unsigned long long)o.range_hi, o.prune);
+           (unsigned long long)o.range_lo, (unsigned long long)o.range_hi, o.prune, o.occupancy);
   std::string k = head;
   for (int i = 0; i < g.m; ++i) {
     char e[24];
@@ -486,18 +495,21 @@ static void tune_load_file() {
   if (!path || !*path) return;
   FILE* f = fopen(path, "r");
   if (!f) return;
-  char key[4096];
-  int L, nt;
-  while (fscanf(f, "%4095s %d %d", key, &L, &nt) == 3) g_tune[key] = {L, nt};
+  char line[4400];
+  while (fgets(line, sizeof line, f)) {
+    char key[4096];
+    TuneChoice c{-1, 128, 1, 0};
+    if (sscanf(line, "%4095s %d %d %d %d", key, &c.L, &c.nt, &c.prune, &c.occ) == 5) g_tune[key] = c;
+  }
   fclose(f);
 }
 
-static void tune_store_file(const std::string& key, int L, int nt) {
+static void tune_store_file(const std::string& key, const TuneChoice& c) {
   const char* path = getenv("PBAT_AUTOTUNE_CACHE");
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d\n", key.c_str(), L, nt);
+  fprintf(f, "%s %d %d %d %d\n", key.c_str(), c.L, c.nt, c.prune, c.occ);
   fclose(f);
 }
 
@@ -510,7 +522,48 @@ static double log2_states(const GraphIn& g, const pbat_options& o) {
   return s;
 }
 
-// Fill o.walk_bits / o.block_threads with the tuned choice when tuning applies.
+// Kernel time of one candidate (ms, best of two launches after its first),
+// or a negative value if it cannot run.
+static double tune_time(const GraphIn& g, const double* p, bool grad, pbat_options t,
+                        cudaStream_t st) {
+  t.autotune = 0;
+  t.time_budget_s = 0;
+  Job* J = nullptr;
+  if (job_create(g, p, grad, &t, &J) != PBAT_OK) {
+    clear_error();
+    return -1.0;
+  }
+  double ms = 1e300;
+  bool ok = !job_upload(J, st);
+  for (int rep = 0; ok && rep < 3; ++rep) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    ok = !job_launch(J, st);
+    cudaEventRecord(b, st);
+    ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+    float f = 0.f;
+    if (ok && cudaEventElapsedTime(&f, a, b) == cudaSuccess && rep > 0) ms = std::min(ms, (double)f);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  job_destroy(J);
+  if (!ok) {
+    cudaGetLastError();
+    clear_error();
+    return -1.0;
+  }
+  return ms;
+}
+
+// Fill o.walk_bits / o.block_threads / o.prune / o.occupancy with the tuned
+// choice when tuning applies.  Two stages: (1) with the prune on, the
+// planning mode -- source/sink-near prefix arcs against prune-aware prefix
+// arcs (prune = 2) -- at the planner's default shape, since the mode changes
+// how many items the prune resolves and so the best shape; (2) walk length,
+// block size and occupancy within the chosen mode.  Every choice gives the
+// same exact results.
 static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& o,
                     const DeviceInfo& dev) {
   if (!o.autotune || o.walk_bits >= 0 || o.block_threads > 0 || o.prefix_bits >= 0) return PBAT_OK;
@@ -521,77 +574,72 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
     tune_load_file();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      o.walk_bits = it->second.first;
-      o.block_threads = it->second.second;
+      o.walk_bits = it->second.L;
+      o.block_threads = it->second.nt;
+      o.prune = it->second.prune;
+      o.occupancy = it->second.occ;
       return PBAT_OK;
     }
   }
+  NvtxRange nv("pbat autotune");
+  cudaStream_t st;
+  PBAT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  // stage 1: planning mode
+  int mode = o.prune;
+  if (o.prune == 1) {
+    pbat_options a = o, b = o;
+    b.prune = 2;
+    bs_precompile(g, p, grad, {a, b}, dev);
+    const double ta = tune_time(g, p, grad, a, st), tb = tune_time(g, p, grad, b, st);
+    if (tb > 0 && (ta < 0 || tb < ta)) mode = 2;
+  }
+  // stage 2: walk length x block size x occupancy.  Candidates run the whole
+  // problem: a block of the equal division is not a fair sample (which arcs
+  // its range fixes changes how much the prune removes; the first block of
+  // the 40-arc network favoured a shape 50% slower on the whole).  Large
+  // problems try fewer candidates: long walks, no 64-thread blocks.
   const int lmax = std::min(10, std::max(0, g.m - o.range_bits - 10));
-  // Candidates run the whole problem: a block of the equal division is not
-  // a fair sample (which arcs its range fixes changes how much the prune
-  // removes; the first block of the 40-arc network favoured a shape 50%
-  // slower on the whole). Large problems try fewer candidates: long walks,
-  // no 64-thread blocks.
   const bool large = log2_states(g, o) > 34.0;
-  std::vector<int> Ls, nts;
+  std::vector<int> Ls, nts, occs;
   for (int L = std::max(0, lmax - (large ? 2 : 6)); L <= lmax; ++L) Ls.push_back(L);
   // warps per block need not be a power of two: on the 40-arc network 160
   // threads (3 blocks, 15 warps per SM) ran the fused kernel 12% faster
   // than 128 and 224 threads the R kernel 7% faster than 256
   if (!large) nts.push_back(64), nts.push_back(96);
   for (int nt : {128, 160, 192, 224, 256}) nts.push_back(nt);
-  NvtxRange nv("pbat autotune");
+  // a register cap of two blocks per SM: on GB300 the fused kernel of the
+  // 40-arc network in prune-aware mode went from 26.0 to 24.7 ms with it
+  if (o.occupancy >= 0) occs.push_back(o.occupancy);
+  else occs = {0, 2};
   std::vector<pbat_options> cands;
   for (int L : Ls)
-    for (int nt : nts) {
-      pbat_options t = o;
-      t.autotune = 0;
-      t.walk_bits = L;
-      t.block_threads = nt;
-      t.time_budget_s = 0;
-      cands.push_back(t);
-    }
+    for (int nt : nts)
+      for (int oc : occs) {
+        if (oc * nt > 2048) continue;
+        pbat_options t = o;
+        t.prune = mode;
+        t.walk_bits = L;
+        t.block_threads = nt;
+        t.occupancy = oc;
+        cands.push_back(t);
+      }
   bs_precompile(g, p, grad, cands, dev);
-  cudaStream_t st;
-  PBAT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   double best_ms = 1e300;
-  int best_L = -1, best_nt = 128;
-  for (pbat_options& t : cands) {
-    Job* J = nullptr;
-    if (job_create(g, p, grad, &t, &J) != PBAT_OK) {
-      clear_error();
-      continue;
-    }
-    double ms = 1e300;
-    bool ok = !job_upload(J, st);
-    for (int rep = 0; ok && rep < 2; ++rep) {
-      cudaEvent_t a, b;
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
-      cudaEventRecord(a, st);
-      ok = !job_launch(J, st);
-      cudaEventRecord(b, st);
-      ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
-      float f = 0.f;
-      if (ok && cudaEventElapsedTime(&f, a, b) == cudaSuccess && rep > 0) ms = f;
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-    }
-    job_destroy(J);
-    if (!ok) {
-      cudaGetLastError();
-      clear_error();
-      continue;
-    }
-    if (ms < best_ms) best_ms = ms, best_L = t.walk_bits, best_nt = t.block_threads;
+  TuneChoice best{-1, 128, mode, 0};
+  for (const pbat_options& t : cands) {
+    const double ms = tune_time(g, p, grad, t, st);
+    if (ms > 0 && ms < best_ms)
+      best_ms = ms, best = TuneChoice{t.walk_bits, t.block_threads, t.prune, t.occupancy};
   }
   cudaStreamDestroy(st);
-  if (best_L < 0) return PBAT_OK;  // keep the planner's defaults
-  o.walk_bits = best_L;
-  o.block_threads = best_nt;
+  if (best.L < 0) return PBAT_OK;  // keep the planner's defaults
+  o.walk_bits = best.L;
+  o.block_threads = best.nt;
+  o.prune = best.prune;
+  o.occupancy = best.occ;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = {best_L, best_nt};
-  tune_store_file(key, best_L, best_nt);
+  g_tune[key] = best;
+  tune_store_file(key, best);
   return PBAT_OK;
 }
 
@@ -634,7 +682,21 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
     J->item_states = bs_item_states(*J->bs);
     int d6[6];
     bs_describe(*J->bs, d6);
-    J->abs_err_bound = grad ? ldexp(1.0, -60) : ldexp(1.0, -61) + ldexp(1.0, d6[2] - 64);
+    // Per item, R is the sum over threads of thread mass x T (T: lane sums
+    // times walk masses, summed over the walk) times the prefix mass.  Its
+    // absolute error in units of the item's mass: the four byte-table
+    // entries of a lane sum, each within 2^-63, give 2^-61; the 32 thread
+    // masses, each within 2^-64 of exact and weighting a T <= 1, give 2^-59;
+    // the R kernel's 64-bit walk masses, each within 2^-64, give 2^(L-64)
+    // over 2^L walk states (the fused kernel's are 128-bit: negligible).
+    // The prefix masses are relative (2^-62 per level): harmless at 1e-12.
+    J->abs_err_bound = ldexp(1.0, -61) + ldexp(1.0, -59) + (grad ? 0.0 : ldexp(1.0, d6[2] - 64));
+    // dR/dp_k of the fused kernel: the same two absolute terms for the
+    // walk-arc sums A and B (whose terms all carry the arc's own factor, so
+    // dividing by p or 1 - p does not amplify them) and the excluded-arc
+    // tables of lane and thread arcs (2^-64 each, summed over 16 pairs with
+    // weights summing to at most one): 2^-57 covers every role
+    J->grad_err_bound = grad ? ldexp(1.0, -57) : 0.0;
     J->pl.grad = grad;
   } else {
     if ((rc = make_plan(g, p, grad, o, J->dev, J->pl))) return rc;
@@ -650,6 +712,7 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
     n_items = J->pl.n_tasks;
     J->item_states = 1ull << (J->pl.ell + J->pl.L);
     J->abs_err_bound = ldexp(1.0, -100);
+    J->grad_err_bound = ldexp(1.0, -98);
   }
   J->n_items = n_items;
   J->grid_nthr = nthr;
@@ -864,9 +927,28 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
   }
   J->n_pending = 0;
   const double R = J->h_acc[0].hi + J->h_acc[0].lo;
-  if (J->bs && J->opt_copy.algo == PBAT_ALGO_AUTO && R < 1e12 * J->abs_err_bound * J->mass) {
-    // the fixed-point bound of the bit-sliced kernel would not guarantee
-    // 1e-12 relative accuracy for so small an R: run the frontier kernel
+  std::vector<double> gi;
+  if (J->bs && dRdp_out) {
+    gi.resize(m);
+    bs_finish_grad(*J->bs, J->h_acc, m, gi.data());
+  }
+  // The bit-sliced kernels' error bounds against the accuracy promised:
+  // R within 1e-12 relative; each dR/dp_k within 1e-12 of max(|g_k|,
+  // 1e-4 R) -- for an arc whose T1/T0 sums cancel, 1e-12 of |g_k| is below
+  // what their rounding can resolve, so the floor 1e-4 R applies; where
+  // they do not cancel (condition number below 2^53 * 1e-13) |g_k| exceeds
+  // 1e-3 R, so 1e-12 * max(|g_k|, 1e-4 R) is met by the same test.
+  bool too_coarse = false;
+  if (J->bs && J->opt_copy.algo == PBAT_ALGO_AUTO) {
+    too_coarse = R < 1e12 * J->abs_err_bound * J->mass;
+    const double E = J->grad_err_bound * J->mass;
+    for (size_t k = 0; k < gi.size() && !too_coarse; ++k)
+      too_coarse = E > 1e-12 * std::max(std::fabs(gi[k]) - E, 1e-4 * R);
+  }
+  if (too_coarse) {
+    // the fixed-point bounds of the bit-sliced kernel would not guarantee
+    // that accuracy for so small an R (or gradient): run the frontier
+    // kernel, whose tables are exact to 2^-100
     pbat_options o = J->opt_copy;
     o.algo = PBAT_ALGO_FRONTIER;
     Job* F = nullptr;
@@ -881,8 +963,6 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
     for (int k = 0; k <= m; ++k) Nk_out[k] = J->h_n[k];
   if (dRdp_out) {
     if (J->bs) {
-      std::vector<double> gi(m);
-      bs_finish_grad(*J->bs, J->h_acc, m, gi.data());
       for (int k = 0; k < m; ++k) dRdp_out[J->perm[k]] = gi[k];
     } else {
       for (int k = 0; k < m; ++k) {
@@ -934,6 +1014,7 @@ void pbat_options_init(pbat_options* o) {
   o->block_threads = -1;
   o->prune = 1;
   o->autotune = 1;
+  o->occupancy = -1;
 }
 
 int pbat_reliability(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,

@@ -11,15 +11,21 @@
 // caller's host arrays, as for pbat_reliability.
 //
 // Host code must not pass `g_noalloc_scratch` itself to a kernel: in host
-// code that name is only a host-side stand-in.  Its device address is taken
-// once per device with cudaGetSymbolAddress (with that device current) and
-// cached; the first call on each device does that set-up, so make the first
-// call on a device before any stream capture begins.
+// code that name is only a host-side stand-in.  Every call looks up its
+// device address with cudaGetSymbolAddress, with the caller's device current
+// (cheap, and it allocates nothing), so the address stays right even after
+// the caller resets the device and the module is loaded again.
 //
 // All calls share the one array and it keeps the last call's contents; the
 // ticket, status and statistics are cleared at the start of every call.
-// Calls whose work overlaps on the GPU (two host threads, or two streams)
-// race on the array and give wrong results: serialise them.
+// Calls whose work overlapped on the GPU would race on the array, so the
+// library holds one lock for the whole of each call (the call waits for its
+// stream before it returns): calls from several host threads run one after
+// another.  The walk-mass table is staged in a static host buffer under the
+// same lock, so a call needs only a few KiB of the caller's stack.
+//
+// The call copies through host memory and waits for its stream, which stream
+// capture does not allow: it refuses to run while its stream is capturing.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,8 +55,9 @@ struct NoAllocDevice {
   void* base = nullptr;  // device address of g_noalloc_scratch on this device
   int sms = 0;
 };
-static NoAllocDevice g_na_dev[kNoAllocMaxDevices];
-static std::mutex g_na_mu;
+static int g_na_sms[kNoAllocMaxDevices];   // SM count per device, 0 = not yet read
+static std::mutex g_na_mu;                 // held for the whole of every call
+static u128 g_na_wmid[1 << kNoAllocMaxWalkBits];   // host staging of the walk table
 
 // Fixed layout of the static scratch (byte offsets).
 constexpr size_t kNaCounter = 0;     // u64 ticket; status at 16; stats at 32..55
@@ -58,25 +65,26 @@ constexpr size_t kNaOutAcc = 64;     // (1 + m) double-doubles, m <= 63
 constexpr size_t kNaOutN = 1088;     // (m + 1) u64
 constexpr size_t kNaWmid = 2048;     // 2^L u128 walk masses
 
+// The scratch's device address on the current device (looked up on every
+// call, with that device current) and its SM count (read once).  Called with
+// g_na_mu held.
 static int na_setup(int device, NoAllocDevice* out) {
   if (device < 0 || device >= kNoAllocMaxDevices)
     return fail(PBAT_ERANGE, "device %d is beyond the %d devices this entry point serves", device,
                 kNoAllocMaxDevices);
-  std::lock_guard<std::mutex> lk(g_na_mu);
-  NoAllocDevice& d = g_na_dev[device];
-  if (!d.base) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr)
-      return fail(PBAT_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
-                  cudaGetErrorString(e));
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr)
+    return fail(PBAT_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                cudaGetErrorString(e));
+  if (!g_na_sms[device]) {
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
-    d.sms = sms;
-    d.base = ptr;
+    g_na_sms[device] = sms;
   }
-  *out = d;
+  out->base = ptr;
+  out->sms = g_na_sms[device];
   return PBAT_OK;
 }
 
@@ -114,6 +122,19 @@ static int run_noalloc(const GraphIn& g, const double* p, const pbat_options* op
   const int d = m - ell - L;
   if (d >= 64) return fail(PBAT_ERANGE, "prefix of %d bits is too deep", d);
 
+  cudaStream_t st = (cudaStream_t)stream;
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PBAT_ECUDA, "cudaStreamIsCapturing failed");
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(PBAT_ENOTSUP, "cannot run while its stream is being captured (the call copies "
+                                "through host memory and waits for the stream)");
+  }
+  // one call at a time: the static device array and host staging are shared
+  std::lock_guard<std::mutex> lk(g_na_mu);
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess)
     return fail(PBAT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(cudaGetLastError()));
@@ -129,7 +150,8 @@ static int run_noalloc(const GraphIn& g, const double* p, const pbat_options* op
     return fail(PBAT_ERANGE, "needs more than the %zu B of static scratch", kNoAllocScratchBytes);
   const long long max_grid = (long long)((kNoAllocScratchBytes - part_off) / per_block);
 
-  // kernel parameters and tables, all on the host stack
+  // kernel parameters on the host stack, the walk table in the static host
+  // staging buffer (under the lock)
   FrontierParams P;
   memset(&P, 0, sizeof P);
   P.n = g.n;
@@ -177,7 +199,7 @@ static int run_noalloc(const GraphIn& g, const double* p, const pbat_options* op
     P.lane_w[j] = w;
   }
   for (int j = 0; j < 64; ++j) P.binom[j] = binom_u64(ell + L, j);
-  u128 wmid[1 << kNoAllocMaxWalkBits];
+  u128* wmid = g_na_wmid;
   for (int gi = 0; gi < (1 << L); ++gi) {
     dd w = dd_make(1.0);
     for (int b = 0; b < L; ++b) w = dd_mul(w, arc_w(p, m - 1 - (ell + b), (gi >> b) & 1));
@@ -212,8 +234,7 @@ static int run_noalloc(const GraphIn& g, const double* p, const pbat_options* op
   W.out_limbs = nullptr;
   const u128* d_wmid = (const u128*)(base + kNaWmid);
 
-  cudaStream_t st = (cudaStream_t)stream;
-  // the copy from this stack buffer returns once the buffer has been staged
+  // the copy from this pageable buffer returns once the buffer has been staged
   if ((e = cudaMemcpyAsync((void*)d_wmid, wmid, wmid_bytes, cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemsetAsync(base + kNaCounter, 0, 64, st)) ||
       (e = launch_frontier(false, wide, grid, nthr, smem, st, P, d_wmid, W)) ||

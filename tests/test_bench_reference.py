@@ -24,7 +24,7 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference" and d["unit"] == "states/s" and d["value"] > 0
     assert d["higher_is_better"] is True and d["data"] == "synthetic"
     cfg = d["config"]
-    assert cfg["workload"] == "grid-3x6" and cfg["m"] == 27 and cfg["states"] == 2**27
+    assert cfg["workload"] == "random-undirected-n24-m40" and cfg["m"] == 40 and cfg["states"] == 2**40
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0

@@ -1,0 +1,203 @@
+"""Full-size parity of the benchmark workloads, at the launch shapes the
+benchmark times, against the oracle's exact values.
+
+- 3x6 grid (2^27 states): the brute-force oracle's stored values
+  (tests/golden/grid-3x6_full.txt, written by tests/golden/make_golden.py).
+- 24-node, 40-arc network (2^40 states) and the 64 batched networks: the
+  oracle's factoring method (exact sums by pivotal decomposition, pinned
+  against the brute force in tests/test_oracle_factoring.py), computed here.
+- Directed 34-arc network (2^34 states; the factoring method covers
+  undirected networks only): sampled equal divisions against the brute force
+  under the benchmark's planning mode, and invariants of the whole run at the
+  benchmark's shapes.
+
+N_k must be bit-exact, R within 1e-12 relative, dR/dp within the reading of
+the 1e-12 target for gradients: 1e-12 * |g*| where the oracle's T1/T0
+condition number is small, else 1e-12 * max(|g*|, 1e-4 * R).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import bench
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def pb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_09711_gb300 import build
+    build.build()
+    import paper_2209_09711_gb300 as mod
+    return mod
+
+
+def _grad_tol(gstar, t1, t0, R):
+    kappa = (t1 + t0) / max(abs(gstar), 1e-300)
+    if kappa * 2.0**-53 <= 1e-13:
+        return 1e-12 * abs(gstar) + 1e-300
+    return 1e-12 * max(abs(gstar), 1e-4 * abs(R)) + 1e-300
+
+
+def _check(res, R, Nk, T1=None, T0=None, ctx=""):
+    assert res.Nk == Nk, ctx
+    assert abs(res.R - R) <= 1e-12 * abs(R) + 1e-300, (ctx, res.R, R)
+    if T1 is not None and res.grad is not None:
+        for i in range(len(Nk) - 1):
+            g = T1[i] - T0[i]
+            assert abs(res.grad[i] - g) <= _grad_tol(g, T1[i], T0[i], R), (ctx, i, res.grad[i], g)
+
+
+def _bench_plan(pb, net, name, kind, **extra):
+    """Run the benchmark's own launch: a prepared plan at the pinned shape."""
+    grad = kind == "fused"
+    plan = pb.Plan(net, grad=grad, opts=bench.shape_opts(pb, name, kind, **extra))
+    plan.execute(0)
+    plan.execute(0)   # a second launch re-zeroes and re-accumulates
+    r = plan.read(0)
+    plan.close()
+    return r
+
+
+def _golden_grid():
+    rows = {}
+    with open(os.path.join(GOLDEN, "grid-3x6_full.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                w = line.split()
+                rows.setdefault(w[0], []).append(w[1:])
+
+    def val(hi, lo):
+        return float(Fraction(float.fromhex(hi)) + Fraction(float.fromhex(lo)))
+
+    R = val(*rows["R"][0])
+    Nk = [int(v) for v in rows["NK"][0]]
+    m = len(Nk) - 1
+    T1, T0 = [0.0] * m, [0.0] * m
+    for i, hi, lo in rows["T1"]:
+        T1[int(i)] = val(hi, lo)
+    for i, hi, lo in rows["T0"]:
+        T0[int(i)] = val(hi, lo)
+    return R, Nk, T1, T0
+
+
+def test_grid_3x6_full_space_at_bench_shapes(pb):
+    net = synth.workload_grid_3x6()
+    R, Nk, T1, T0 = _golden_grid()
+    _check(_bench_plan(pb, net, "grid-3x6", "fused"), R, Nk, T1, T0, "bench fused launch")
+    _check(_bench_plan(pb, net, "grid-3x6", "r_only"), R, Nk, ctx="bench R launch")
+    # the public call with default options (autotuned shape)
+    _check(pb.reliability_net(net, grad=True), R, Nk, T1, T0, "autotuned fused")
+    _check(pb.reliability_net(net), R, Nk, ctx="autotuned R")
+    # both planning modes and the plain GPU BAT
+    for prune in (0, 2):
+        _check(pb.reliability_net(net, grad=True, opts=pb.options(prune=prune, walk_bits=5)), R, Nk,
+               T1, T0, f"prune {prune}")
+    _check(pb.reliability_net(net, grad=True, opts=pb.options(algo=pb.ALGO_FRONTIER)), R, Nk, T1,
+           T0, "frontier kernel")
+
+
+@pytest.fixture(scope="module")
+def forty():
+    net = synth.workload_random_24_40()
+    f = oracle.factor(net)
+    T1h, T0h = oracle.factor_t1t0(net)
+    return net, f.R, f.Nk, [sum(x) for x in T1h], [sum(x) for x in T0h]
+
+
+def test_forty_arc_full_space_at_bench_shapes(pb, forty):
+    """The benchmark's headline workload, 2^40 states, every output."""
+    net, R, Nk, T1, T0 = forty
+    name = "random-undirected-n24-m40"
+    _check(_bench_plan(pb, net, name, "fused"), R, Nk, T1, T0, "bench fused launch")
+    _check(_bench_plan(pb, net, name, "r_only"), R, Nk, ctx="bench R launch")
+
+
+def test_forty_arc_full_space_other_plans(pb, forty):
+    """The source/sink-near planner (prune 1) and the public call with its
+    autotuned choice."""
+    net, R, Nk, T1, T0 = forty
+    _check(pb.reliability_net(net, grad=True, opts=pb.options(prune=1, walk_bits=10,
+                                                                block_threads=160)),
+           R, Nk, T1, T0, "prune 1 fused")
+    _check(pb.reliability_net(net, opts=pb.options(prune=1, walk_bits=10, block_threads=224)), R, Nk,
+           ctx="prune 1 R")
+    _check(pb.reliability_net(net, grad=True), R, Nk, T1, T0, "autotuned fused")
+
+
+def test_forty_arc_half_probability_and_partition(pb, forty):
+    """At p = 1/2, R is the count of connected states over 2^40, exactly;
+    partial results of four range blocks add up to the whole."""
+    net, R, Nk, _, _ = forty
+    m = net.m
+    half = pb.reliability_net(net, p=[0.5] * m, opts=bench.shape_opts(pb, "random-undirected-n24-m40",
+                                                                       "r_only"))
+    assert half.Nk == Nk and half.R == sum(Nk) / 2.0**m
+    parts = [pb.reliability_net(net, opts=pb.options(range_bits=2, range_lo=i, range_hi=i + 1,
+                                                     prune=2, walk_bits=9, block_threads=128))
+             for i in range(4)]
+    assert [sum(x) for x in zip(*[q.Nk for q in parts])] == Nk
+    assert abs(sum(q.R for q in parts) - R) <= 1e-12 * R
+
+
+def test_batched_workload_full_against_factoring(pb):
+    """All 64 networks x 16 p-vectors of the batched workload: every R and
+    every network's N_k against the factoring method."""
+    nets, pvecs = synth.workload_batched()
+    Rb, Nkb, _ = pb.reliability_batched(nets, pvecs)
+    for g, net in enumerate(nets):
+        f0 = oracle.factor(net, pvecs[g][0])
+        assert Nkb[g] == f0.Nk, g
+        for k in range(len(pvecs[g])):
+            Rk = f0.R if k == 0 else oracle.factor(net, pvecs[g][k]).R
+            assert abs(Rb[g][k] - Rk) <= 1e-12 * Rk, (g, k, Rb[g][k], Rk)
+
+
+def test_directed_34_at_bench_shapes(pb):
+    """The directed workload: sampled divisions in the benchmark's planning
+    mode against the brute force, and invariants of the full run at the
+    benchmark's shapes."""
+    net = synth.workload_directed_20_34()
+    name = "random-directed-n20-m34"
+    fused = _bench_plan(pb, net, name, "fused")
+    ronly = _bench_plan(pb, net, name, "r_only")
+    m = net.m
+    assert fused.Nk == ronly.Nk and abs(fused.R - ronly.R) <= 1e-13 * ronly.R
+    assert fused.Nk[m] == 1 and all(fused.Nk[k] <= math.comb(m, k) for k in range(m + 1))
+    for opts in (bench.shape_opts(pb, name, "fused"), pb.options(prune=1)):
+        prune = opts.prune
+        bits = 20
+        for d in (0, 517_000, (1 << bits) - 1):
+            o = bench.shape_opts(pb, name, "fused", range_bits=bits, range_lo=d, range_hi=d + 1) \
+                if prune == 2 else pb.options(range_bits=bits, range_lo=d, range_hi=d + 1)
+            r = pb.reliability_net(net, grad=True, opts=o)
+            ref = oracle.enumerate_states(net, prefix_bits=bits, prefix_lo=d, prefix_hi=d + 1, grad=True)
+            _check(r, ref.R, ref.Nk, ref.T1, ref.T0, f"division {d} prune {prune}")
+    # p = 1/2 ties R to the counts
+    half = pb.reliability_net(net, p=[0.5] * m, opts=bench.shape_opts(pb, name, "r_only"))
+    assert half.Nk == fused.Nk and half.R == sum(fused.Nk) / 2.0**m
+    # every planning mode and kernel gives identical counts
+    plain = pb.reliability_net(net, opts=pb.options(algo=pb.ALGO_FRONTIER))
+    assert plain.Nk == fused.Nk and abs(plain.R - fused.R) <= 1e-13 * fused.R
+    g1 = pb.reliability_net(net, grad=True, opts=pb.options(prune=1))
+    assert g1.Nk == fused.Nk
+    assert np.max(np.abs(np.asarray(g1.grad) - np.asarray(fused.grad))) <= 1e-15
+
+
+def test_small_random_full_space_at_default(pb):
+    """The 8-node, 16-arc workload (2^16 states), whole space."""
+    net = synth.workload_small_random()
+    ref = oracle.enumerate_states(net, grad=True)
+    _check(pb.reliability_net(net, grad=True), ref.R, ref.Nk, ref.T1, ref.T0, "default")
+    f = oracle.factor(net)
+    assert f.Nk == ref.Nk

@@ -316,3 +316,116 @@ def test_autograd_function(pb):
     q = torch.tensor(net.p[:], dtype=torch.float64, device="cuda", requires_grad=True)
     assert torch.autograd.gradcheck(lambda x: pb.PBATReliability.apply(x, net), (q,),
                                     eps=1e-4, atol=1e-9, rtol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# prune-aware planning (prune = 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_prune_aware_plans_whole_space(pb, directed):
+    """Prefix arcs chosen by the prune-aware search: whole small networks,
+    fused and R-only, bit-sliced kernel forced, several walk lengths."""
+    for seed in range(20):
+        rng = synth.SplitMix64(12100 + seed)
+        m = 6 + rng.below(14)
+        net = synth.random_small(12200 + seed, n=3 + rng.below(10), m=m, directed=directed,
+                                 p_lo=0.03, p_hi=0.97)
+        ref = oracle.enumerate_states(net, grad=True)
+        for walk in (-1, 1, 3):
+            o = dict(algo=pb.ALGO_BITSLICE, prune=2, walk_bits=walk)
+            check(run(pb, net, grad=True, **o), ref, True, f"seed={seed} walk={walk} fused")
+            check(run(pb, net, **o), ref, False, f"seed={seed} walk={walk} R")
+
+
+@pytest.mark.parametrize("make,bits,picks", [
+    (synth.workload_directed_20_34, 19, [0, 77777, (1 << 19) - 1]),
+    (synth.workload_random_24_40, 25, [0, 12_345_678, (1 << 25) - 1]),
+])
+def test_prune_aware_plans_sampled_divisions(pb, make, bits, picks):
+    net = make()
+    for d in picks:
+        ref = oracle.enumerate_states(net, prefix_bits=bits, prefix_lo=d, prefix_hi=d + 1, grad=True)
+        for L, nt in ((10, 256), (7, 192), (4, 128)):
+            o = dict(prune=2, walk_bits=L, block_threads=nt, range_bits=bits, range_lo=d,
+                     range_hi=d + 1)
+            check(run(pb, net, grad=True, **o), ref, True, f"{net.name} {d} L={L} fused")
+            check(run(pb, net, **o), ref, False, f"{net.name} {d} L={L} R")
+
+
+# ---------------------------------------------------------------------------
+# precision: small R, extreme arc reliabilities
+# ---------------------------------------------------------------------------
+
+def _small_r_network(seed, n_chain=14, extra=4, p_lo=0.15, p_hi=0.35):
+    """A chain from source to sink with a few shortcuts: R around 1e-6..1e-9."""
+    rng = synth.SplitMix64(seed)
+    tail = list(range(n_chain))
+    head = list(range(1, n_chain + 1))
+    for _ in range(extra):
+        u = rng.below(n_chain - 2)
+        tail.append(u)
+        head.append(u + 2 + rng.below(2))
+    p = synth.uniform_p(rng, len(tail), p_lo, p_hi)
+    return synth.Network(n_chain + 1, tail, head, p, 0, n_chain, False, f"small-r-{seed}")
+
+
+def test_small_reliability_gradient_meets_tolerance(pb):
+    """R between 5e-7 and 6e-5: the default path must meet the 1e-12 targets
+    (the engine re-runs exactly when the bit-sliced bounds cannot), and the
+    bit-sliced kernel, forced, must stay within its stated absolute bounds:
+    2^-58.4 of the mass for R and 2^-57 for each gradient entry."""
+    seen = []
+    for seed in range(6):
+        net = _small_r_network(14000 + seed, n_chain=12 + seed % 4)
+        ref = oracle.enumerate_states(net, grad=True)
+        seen.append(ref.R)
+        check(run(pb, net, grad=True), ref, True, f"seed={seed} R={ref.R:.3g}")
+        check(run(pb, net), ref, False, f"seed={seed}")
+        forced = run(pb, net, grad=True, algo=pb.ALGO_BITSLICE)
+        assert forced.Nk == ref.Nk
+        assert abs(forced.R - ref.R) <= 2.0**-58.4 + 1e-12 * ref.R
+        for i, (a, b) in enumerate(zip(forced.grad, ref.grad_t1t0)):
+            assert abs(a - b) <= 2.0**-57 + 1e-12 * abs(b), (seed, i, a, b)
+    assert min(seen) < 1e-6
+
+
+def test_extreme_interior_reliabilities_on_walk_arcs(pb):
+    """Arcs with p at 2^-20, 2^-19, 1 - 2^-19 and 1 - 2^-20 -- the edge of
+    what the fused kernel accepts as walk arcs (it divides their sums by p
+    and 1 - p) -- against the oracle, with every arc forced into the walk
+    where the network allows it."""
+    tail, head, rng = synth.random_connected_undirected(9, 18, 15151)
+    ext = [2.0**-20, 2.0**-19, 1 - 2.0**-19, 1 - 2.0**-20]
+    p = [ext[k % 4] if k % 3 else 0.5 + 0.4 * rng.uniform01() for k in range(18)]
+    for directed in (False, True):
+        net = synth.Network(9, tail, head, p, 0, 8, directed, "extreme-p")
+        ref = oracle.enumerate_states(net, grad=True)
+        for walk in (-1, 3, 8):
+            check(run(pb, net, grad=True, walk_bits=walk), ref, True, f"dir={directed} walk={walk}")
+            check(run(pb, net, grad=True, walk_bits=walk, algo=pb.ALGO_BITSLICE), ref, True,
+                  f"dir={directed} walk={walk} bit-sliced")
+
+
+# ---------------------------------------------------------------------------
+# failure detection: host-side fault injection on the GPU path
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("site,code", [("compile", "PBAT_ECUDA"), ("alloc", "PBAT_ENOMEM"),
+                                       ("launch", "PBAT_ECUDA")])
+def test_injected_host_faults_then_clean_call(pb, site, code, monkeypatch):
+    """PBAT_FAULT fails one host step the way its real call can; the call
+    returns that error code with a message naming the site, no output is
+    written, and the next call without the fault succeeds."""
+    # a network structure no other test has compiled, so that the compile
+    # site is reached (compiled kernels are cached per structure)
+    tail, head, rng = synth.random_connected_undirected(7, 13, 16000 + len(site))
+    net = synth.Network(7, tail, head, synth.uniform_p(rng, 13, 0.6, 0.95), 0, 6, False, site)
+    ref = oracle.enumerate_states(net, grad=True)
+    monkeypatch.setenv("PBAT_FAULT", site)
+    with pytest.raises(pb.PbatError) as e:
+        run(pb, net, grad=True, algo=pb.ALGO_BITSLICE)
+    assert code in str(e.value) and "injected fault" in str(e.value)
+    monkeypatch.delenv("PBAT_FAULT")
+    check(run(pb, net, grad=True, algo=pb.ALGO_BITSLICE), ref, True, f"after {site}")
+    check(run(pb, net), ref, False, f"after {site}, default")
