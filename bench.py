@@ -320,22 +320,34 @@ def _batched_record(pb, steps, warmup, stream, ws):
     nets, pvecs = synth.workload_batched()
     K = len(pvecs[0])
     states = sum(2**n.m for n in nets)
-    o = pb.options()
-    dev_ms, call_ms = [], []
-    for i in range(warmup + steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        R, Nk, _ = pb.reliability_batched(nets, pvecs, opts=o, stream=stream.cuda_stream)
-        t1 = time.perf_counter()
-        if i >= warmup:
-            dev_ms.append(o.stats[4] / 1e6)
-            call_ms.append(1e3 * (t1 - t0))
-    ms = statistics.mean(dev_ms)
+
+    def timed(grad):
+        o = pb.options()
+        dev_ms, call_ms = [], []
+        for i in range(warmup + steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            R, Nk, G = pb.reliability_batched(nets, pvecs, grad=grad, opts=o,
+                                              stream=stream.cuda_stream)
+            t1 = time.perf_counter()
+            if i >= warmup:
+                dev_ms.append(o.stats[4] / 1e6)
+                call_ms.append(1e3 * (t1 - t0))
+        return statistics.mean(dev_ms), statistics.mean(call_ms), R, Nk, int(o.stats[5])
+
+    ms, call, R, Nk, launches = timed(False)
+    gms, gcall, GR, GNk, glaunches = timed(True)
+    assert GNk == Nk, "the gradient module disagrees with the R module on N_k"
     return {"workload": BATCHED, "networks": len(nets), "p_vectors": K, "states": states,
             "outputs": "R per (network, p-vector), N_k per network",
             "value": ws * states / (ms / 1e3), "pairs_per_s": ws * states * K / (ms / 1e3),
-            "ms_per_step": ms, "call_ms": statistics.mean(call_ms),
-            "kernel": "bs_batch (one persistent launch, CUDA graph replay)", "R00": float(R[0][0])}
+            "ms_per_step": ms, "call_ms": call, "launches": launches,
+            "kernel": "bs_batch (one persistent launch, CUDA graph replay)", "R00": float(R[0][0]),
+            "fused": {"value": ws * states / (gms / 1e3), "pairs_per_s": ws * states * K / (gms / 1e3),
+                      "ms_per_step": gms, "call_ms": gcall, "launches": glaunches,
+                      "outputs": "R, N_k and dR/dp per (network, p-vector)",
+                      "kernel": "bs_batch_grad (one persistent launch, CUDA graph replay)"},
+            "fused_over_r_only_time": gms / ms}
 
 
 def run_ours(a):
@@ -509,6 +521,69 @@ def run_ours(a):
     return 0
 
 
+def run_shard(a):
+    """One enumeration split across the ranks by equal divisions (Sec. 4.3,
+    Eq. 6): each rank runs its contiguous block of divisions through the
+    fused kernel at the workload's pinned shape, then one sum-reduce of the
+    1 + m doubles (R, dR/dp) and the m + 1 int64 counts (N_k) over NCCL
+    (PBAT STEP 3) gives every rank the whole result.  "scaling": "strong"
+    (the total work is fixed); value = 2^m / the slowest rank's step."""
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2209_09711_gb300 import build
+    build.build()
+    import paper_2209_09711_gb300 as pb
+    from paper_2209_09711_gb300 import shard
+    name = a.workload
+    net = WORKLOADS[name]()
+    states = 2**net.m
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    bits, lo, hi = shard.shard_range(net.m, ws, rank)
+    opts = shape_opts(pb, name, "fused", range_bits=bits, range_lo=lo, range_hi=hi)
+    plan = pb.Plan(net, grad=True, opts=opts, stream=stream.cuda_stream)
+    ms, kern, wall, res = _time_plan(plan, a.steps, a.warmup, stream, flush, barrier)
+    # the exchange: one sum-reduce of each vector
+    reduce = shard.torch_all_reduce() if ws > 1 else (lambda v: v)
+    fv, nv = shard.pack(res.R, res.Nk, list(res.grad))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fsum, nsum = reduce(fv), reduce(nv)
+    ex_ms = 1e3 * (time.perf_counter() - t0)
+    R, Nk, g = shard.unpack(fsum, nsum, True)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    plan.close()
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": states / ((ms + ex_ms) / 1e3), "unit": "states/s", "n_gpus": ws,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms + ex_ms, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+        "config": dict(workload_config(name, net, ws, "flushed between steps (256 MiB write)"),
+                       parallelism=f"equal-division shards x{ws} (range_bits {bits})"),
+        "shard_kernel_ms": ms, "exchange_ms": ex_ms, "R": R, "N_m": Nk[-1],
+        "exchange": "NCCL all-reduce of 1 + m float64 and m + 1 int64" if ws > 1 else "none (one rank)",
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def _cpu_model() -> str:
     try:
         with open("/proc/cpuinfo") as f:
@@ -581,9 +656,14 @@ def main():
                     help="pin the block size (default: the tuned shape of the workload)")
     ap.add_argument("--autotune", action="store_true",
                     help="let the autotuner pick the launch shapes instead of the recorded ones")
+    ap.add_argument("--shard", action="store_true",
+                    help="split one enumeration across the ranks by equal divisions (strong "
+                         "scaling) instead of running replicas")
     a = ap.parse_args()
     if a.probe:
         return run_probe(a)
+    if a.shard and a.impl == "ours":
+        return run_shard(a)
     if a.warmup < 0 or a.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
     if a.impl == "reference":

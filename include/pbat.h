@@ -149,6 +149,11 @@ typedef struct pbat_graph {
  * Many networks, each with n_pvec arc-reliability vectors, in one
  * persistent launch (captured once in a CUDA graph and replayed).  Each
  * state's connectivity is computed once and weighted by every p-vector.
+ * With dRdp_out, one launch of the gradient module gives R, N_k and dR/dp
+ * for every (network, p-vector); pairs whose R or gradient the bit-sliced
+ * fixed-point bounds cannot certify to 1e-12 (small R) are re-run exactly
+ * with the frontier kernel, one enumeration each.  opt->stats[4] holds the
+ * device time of the batched launch in ns.
  *   p         per graph g: n_pvec x m_g doubles (vector-major), concatenated in
  *             graph order
  *   R_out     out, n_graphs x n_pvec doubles (graph-major)
@@ -241,6 +246,16 @@ int pbat_kernel_source(int n_nodes, int n_arcs, const int32_t* tail, const int32
  * pbat_kernel_source. */
 int pbat_batch_kernel_source(int n_graphs, const pbat_graph* graphs, int n_pvec,
                              const pbat_options* opt, char* buf, size_t cap);
+
+/* Diagnostic, no GPU needed: the CUDA C++ source of the batched gradient
+ * module (every network's connectivity program and the persistent kernel
+ * that also forms dR/dp for every p-vector).  p: as for
+ * pbat_reliability_batched, or NULL; it decides which arcs may be walk
+ * arcs (p in [2^-20, 1 - 2^-20] under every p-vector).  Same buffer
+ * convention as pbat_kernel_source. */
+int pbat_batch_grad_kernel_source(int n_graphs, const pbat_graph* graphs, int n_pvec,
+                                  const double* p, const pbat_options* opt, char* buf,
+                                  size_t cap);
 
 /* Thread-local description of the last error in this thread ("" if none). */
 const char* pbat_last_error(void);

@@ -82,7 +82,7 @@ EXPORTED = [
     "pbat_options_init", "pbat_reliability", "pbat_reliability_grad",
     "pbat_reliability_batched", "pbat_plan_create", "pbat_plan_execute", "pbat_plan_read",
     "pbat_plan_destroy", "pbat_plan_stats", "pbat_plan_describe", "pbat_reliability_noalloc",
-    "pbat_kernel_source", "pbat_batch_kernel_source",
+    "pbat_kernel_source", "pbat_batch_kernel_source", "pbat_batch_grad_kernel_source",
     "pbat_last_error", "pbat_version",
 ]
 
@@ -131,6 +131,9 @@ def load(path: Optional[str] = None):
         lib.pbat_batch_kernel_source.argtypes = [I, ctypes.POINTER(Graph), I, PO, ctypes.c_char_p,
                                                  ctypes.c_size_t]
         lib.pbat_batch_kernel_source.restype = I
+        lib.pbat_batch_grad_kernel_source.argtypes = [I, ctypes.POINTER(Graph), I, PD, PO,
+                                                      ctypes.c_char_p, ctypes.c_size_t]
+        lib.pbat_batch_grad_kernel_source.restype = I
         lib.pbat_last_error.argtypes = []
         lib.pbat_last_error.restype = ctypes.c_char_p
         lib.pbat_version.argtypes = []
@@ -333,6 +336,28 @@ def batch_kernel_source(nets, n_pvec: int, opts: Optional[Options] = None) -> st
         _check(n)
     buf = ctypes.create_string_buffer(n + 1)
     lib.pbat_batch_kernel_source(len(nets), graphs, n_pvec, ctypes.byref(o), buf, n + 1)
+    return buf.value.decode()
+
+
+def batch_grad_kernel_source(nets, pvecs, opts: Optional[Options] = None) -> str:
+    """The generated CUDA source of the batched gradient module."""
+    lib = load()
+    keep = []
+    graphs = (Graph * len(nets))()
+    for i, net in enumerate(nets):
+        t, tp = _i32(net.tail)
+        h, hp = _i32(net.head)
+        keep += [t, h]
+        graphs[i] = Graph(net.n, len(t), tp, hp, int(net.directed), net.source, net.sink)
+    K = len(pvecs[0])
+    flat = np.concatenate([np.asarray(pv, dtype=np.float64).reshape(K, -1).ravel() for pv in pvecs])
+    pv, pp = _f64(flat)
+    o = opts if opts is not None else options()
+    n = lib.pbat_batch_grad_kernel_source(len(nets), graphs, K, pp, ctypes.byref(o), None, 0)
+    if n < 0:
+        _check(n)
+    buf = ctypes.create_string_buffer(n + 1)
+    lib.pbat_batch_grad_kernel_source(len(nets), graphs, K, pp, ctypes.byref(o), buf, n + 1)
     return buf.value.decode()
 
 

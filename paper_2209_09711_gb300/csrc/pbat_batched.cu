@@ -543,7 +543,8 @@ static double limbs_value(const unsigned long long* limbs) {
 
 int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
                    cudaStream_t st, double* R_out, uint64_t* Nk_out, const std::string& key,
-                   const DeviceInfo& dev, uint64_t* kernel_ns);
+                   const DeviceInfo& dev, uint64_t* kernel_ns, const std::vector<std::string>* elig,
+                   double* dRdp_out, std::vector<std::pair<int, int>>* coarse);
 
 int run_batched(int G, const pbat_graph* graphs, int K, const double* p, pbat_options* opt,
                 void* stream, double* R_out, uint64_t* Nk_out, double* dRdp_out) {
@@ -569,35 +570,63 @@ int run_batched(int G, const pbat_graph* graphs, int K, const double* p, pbat_op
   if ((rc = device_info(dev))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
 
-  const std::string key = batch_key(dev.device, G, graphs, K, o);
+  std::string key = batch_key(dev.device, G, graphs, K, o);
   if (o.algo != PBAT_ALGO_FRONTIER) {
-    // bit-sliced batched kernel for R and N_k; the gradient, if asked for,
-    // comes from one fused enumeration per (network, p-vector) below
+    // bit-sliced batched module: R and N_k, or with the gradient the
+    // gradient module (every p-vector's exact per-arc sums from one
+    // connectivity pass per state); both one persistent launch
     std::vector<double> Rb((size_t)G * K);
     std::vector<uint64_t> Nb;
+    std::vector<double> Gb;
+    std::vector<std::string> elig;
+    std::vector<std::pair<int, int>> coarse;
     int nk_total = 0;
+    size_t ptotal2 = 0;
     for (int i = 0; i < G; ++i) nk_total += graphs[i].n_arcs + 1;
     Nb.resize(nk_total);
-    uint64_t kns = 0;
-    rc = run_batched_bs(G, graphs, K, p, o, st, Rb.data(), Nb.data(), key, dev, &kns);
-    if (rc == PBAT_OK) {
-      if (dRdp_out) {
-        size_t poff = 0;
-        for (int i = 0; i < G; ++i) {
-          GraphIn g{graphs[i].n_nodes, graphs[i].n_arcs, graphs[i].tail, graphs[i].head,
-                    graphs[i].directed, graphs[i].source, graphs[i].sink};
-          for (int k = 0; k < K; ++k) {
-            double Rk;
-            pbat_options oo = o;
-            rc = run_single(g, p + poff + (size_t)k * g.m, true, &oo, stream, &Rk, nullptr,
-                            dRdp_out + poff + (size_t)k * g.m);
-            if (rc) return rc;
+    if (dRdp_out) {
+      // an arc may be a walk arc of the gradient module only if every
+      // p-vector puts its p in [2^-20, 1 - 2^-20] (its sums are divided by
+      // p and 1 - p)
+      elig.resize(G);
+      for (int i = 0; i < G; ++i) {
+        const int m = graphs[i].n_arcs;
+        elig[i].assign(m, '1');
+        for (int k = 0; k < K; ++k)
+          for (int a = 0; a < m; ++a) {
+            const double x = p[ptotal2 + (size_t)k * m + a];
+            if (!(x >= 0x1p-20 && x <= 1.0 - 0x1p-20)) elig[i][a] = '0';
           }
-          poff += (size_t)K * g.m;
-        }
+        ptotal2 += (size_t)K * m;
+        key += "grad:" + elig[i];
+      }
+      Gb.resize(ptotal2);
+    }
+    uint64_t kns = 0;
+    rc = run_batched_bs(G, graphs, K, p, o, st, Rb.data(), Nb.data(), key, dev, &kns,
+                        dRdp_out ? &elig : nullptr, dRdp_out ? Gb.data() : nullptr,
+                        o.algo == PBAT_ALGO_AUTO ? &coarse : nullptr);
+    if (rc == PBAT_OK) {
+      // pairs the fixed-point bounds cannot certify: exact single runs
+      std::vector<size_t> poff(G);
+      for (int i = 0, acc = 0; i < G; ++i) {
+        poff[i] = (size_t)acc;
+        acc += K * graphs[i].n_arcs;
+      }
+      for (const auto& ik : coarse) {
+        const int i = ik.first, k = ik.second;
+        GraphIn g{graphs[i].n_nodes, graphs[i].n_arcs, graphs[i].tail, graphs[i].head,
+                  graphs[i].directed, graphs[i].source, graphs[i].sink};
+        pbat_options oo = o;
+        oo.algo = PBAT_ALGO_FRONTIER;
+        rc = run_single(g, p + poff[i] + (size_t)k * g.m, dRdp_out != nullptr, &oo, stream,
+                        &Rb[(size_t)i * K + k], nullptr,
+                        dRdp_out ? Gb.data() + poff[i] + (size_t)k * g.m : nullptr);
+        if (rc) return rc;
       }
       memcpy(R_out, Rb.data(), sizeof(double) * Rb.size());
       if (Nk_out) memcpy(Nk_out, Nb.data(), sizeof(uint64_t) * Nb.size());
+      if (dRdp_out) memcpy(dRdp_out, Gb.data(), sizeof(double) * Gb.size());
       if (opt) {
         opt->stats[4] = kns;   // device time of the batched launch
         opt->stats[5] = 1;     // one persistent kernel for every p-vector

@@ -226,10 +226,11 @@ static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
            "#define BS_NTHR %d\n#define BS_WALK0 %d\n#define BS_TOP %d\n#define BS_NCORE %d\n"
            "#define BS_LANE_MASK 0x%08xu\n#define BS_FULL_COUNTS 0x%016llxull\n#define BS_GRAD %d\n"
            "#define BS_ACC_REG %d\n#define BS_IN_BITS %d\n#define BS_THR_MASK 0x%08xu\n"
-           "#define BS_MINB %d\n",
+           "#define BS_MINB %d\n#define BS_PEX_MASK 0x%016llxull\n",
            g.m, bp.ell, bp.tb, bp.L, bp.d, nthr, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, bp.ncore,
            lane_mask, full_counts(bp.ell), bp.grad ? 1 : 0, acc_in_registers(bp) ? 1 : 0,
-           walk_unroll_bits(bp), bp.tb >= 5 ? 0xffffffffu : ((1u << (1 << bp.tb)) - 1u), bp.minb);
+           walk_unroll_bits(bp), bp.tb >= 5 ? 0xffffffffu : ((1u << (1 << bp.tb)) - 1u), bp.minb,
+           bp.pex);
   const std::string tmpl = kBsTemplate;
   const size_t cut = tmpl.find("//@@GENERATED@@");
   return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tmpl.substr(cut);
@@ -436,8 +437,10 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     };
     excluded(bp.perm.data() + bp.ell, bp.tb, bl.Q.thw_ex);
     excluded(bp.perm.data(), bp.ell, bl.Q.lw_ex);
-    for (int b = 0; b < bp.L; ++b) {
-      const int k = bp.ell + bp.tb + b;
+    // 1/p and 1/(1 - p) of the walk arcs and of the prefix arcs whose sums
+    // carry their own factor (every prefix arc not in pex)
+    for (int k = bp.ell + bp.tb; k < m; ++k) {
+      if (k >= top && ((bp.pex >> k) & 1ull)) continue;
       const double pk = p[bp.perm[k]];
       bl.Q.inv_p[k] = dd_recip(pk);
       bl.Q.inv_q[k] = dd_recip_dd(dd_one_minus(pk));
@@ -510,16 +513,17 @@ const std::vector<MxHost>& bs_ptab_ex(const BsLaunch& bl) { return bl.ptab_ex; }
 bool bs_grad(const BsLaunch& bl) { return bl.plan.grad; }
 
 // The fused kernel's result holds R, then A_k and B_k for every internal arc
-// k: the gradient is A - B for prefix arcs (mass without the arc, working
-// minus failed), A / p - B / (1 - p) for walk arcs (their masses carry the
-// arc's own factor) and A for lane and thread arcs (exact pair differences).
+// k: the gradient is A / p - B / (1 - p) for walk arcs and for prefix arcs
+// with p in [2^-20, 1 - 2^-20] (their sums carry the arc's own factor), A - B
+// for the other prefix arcs (masses without the arc, working minus failed),
+// and A for lane and thread arcs (exact pair differences).
 void bs_finish_grad(const BsLaunch& bl, const dd* acc, int m, double* g_internal) {
   const BsPlan& bp = bl.plan;
   const int walk0 = bp.ell + bp.tb, top = walk0 + bp.L;
   for (int k = 0; k < m; ++k) {
     const dd a = acc[1 + 2 * k], b = acc[2 + 2 * k];
     dd v;
-    if (k >= top)
+    if (k >= top && ((bp.pex >> k) & 1ull))
       v = dd_sub(a, b);
     else if (k >= walk0)
       v = dd_sub(dd_mul(a, bl.Q.inv_p[k]), dd_mul(b, bl.Q.inv_q[k]));
@@ -550,7 +554,11 @@ struct BGraphHost {
   int L, top;
   unsigned lane_mask;
   int pad0;
+  int wm2_off, tt_off, lwex_off, thwex_off, ptex_off, out_off, ell, d;
+  unsigned thr_mask;
+  int pad1;
   unsigned long long full_counts;
+  unsigned long long pex_mask;
   unsigned long long binom[64];
 };
 
@@ -574,6 +582,13 @@ struct BsBatch {
   Scratch* scr = nullptr;
   size_t o_graphs, o_lt, o_nt, o_wm, o_pt, o_thw, o_upload_end, o_limbs, o_nk, o_counter, o_status, o_end;
   cudaGraphExec_t exec = nullptr;
+  // the gradient module (bs_batch_grad): which arcs of each network may be
+  // walk arcs (p in [2^-20, 1 - 2^-20] for every p-vector), its extra tables
+  // and the size of its results (R, then A_k and B_k of every arc, per
+  // network and p-vector)
+  bool grad = false;
+  std::vector<std::string> elig;   // input order, one '0'/'1' per arc
+  size_t o_wm2 = 0, o_tt = 0, o_lwex = 0, o_thwex = 0, o_ptex = 0, n_out = 0;
 };
 
 static std::mutex g_bsb_mu;
@@ -595,7 +610,7 @@ static int bsb_build(BsBatch& E, int G, const pbat_graph* graphs, int K, const p
   std::string src;
   int rc = bsb_source(E, G, graphs, K, o, items, src);
   if (rc) return rc;
-  if ((rc = jit_compile(src, dev, "bs_batch", &E.jit))) return rc;
+  if ((rc = jit_compile(src, dev, E.grad ? "bs_batch_grad" : "bs_batch", &E.jit))) return rc;
   return bsb_layout(E, G, graphs, K, o, dev, items);
 }
 
@@ -612,7 +627,14 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
     pbat_options_init(&oo);
     oo.walk_bits = std::min(o.walk_bits >= 0 ? o.walk_bits : kBsbMaxWalk, kBsbMaxWalk);
     oo.prune = o.prune;   // prune == 2: prune-aware prefix arcs
-    int rc = bs_make_plan(g, oo, kBsbThreads, E.plans[i], nullptr);
+    // the gradient module divides walk-arc sums by p and 1 - p: only arcs
+    // eligible under every p-vector may be walk arcs
+    std::vector<double> pe;
+    if (E.grad) {
+      pe.resize(g.m);
+      for (int a = 0; a < g.m; ++a) pe[a] = E.elig[i][a] == '1' ? 0.5 : 0.0;
+    }
+    int rc = bs_make_plan(g, oo, kBsbThreads, E.plans[i], E.grad ? pe.data() : nullptr);
     if (rc) return rc;
     items[i] = 1ull << E.plans[i].d;
     E.lmax = std::max(E.lmax, E.plans[i].L);
@@ -642,7 +664,28 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
              r, m, bp.ell, bp.tb, bp.L, bp.d, bp.ncore, bp.ell + bp.tb, bp.ell + bp.tb + bp.L, lane_mask);
     src += head + gen + "};\n";
   }
-  std::string kern = "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR, 4)\n"
+  // shared memory: per-thread N_k bins, the item's connectivity words (and,
+  // in the gradient module, their lane transposes), per-warp N_k counts
+  std::string kern = E.grad ?
+      "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR, 4)\n"
+      "bs_batch_grad(const BGraph* __restrict__ graphs, int G, int K, int Kp, u64 total,\n"
+      "         const u64* __restrict__ lt, const u64* __restrict__ nt, const u64* __restrict__ wm2,\n"
+      "         const mx* __restrict__ pt, const u64* __restrict__ thw, const u64* __restrict__ tt,\n"
+      "         const u64* __restrict__ lwex, const u64* __restrict__ thwex,\n"
+      "         const mx* __restrict__ ptex, u64* limbs, u64* nk,\n"
+      "         u64* counter, u32* status, u64 budget_ns) {\n"
+      "  extern __shared__ __align__(16) u64 s_bins[];\n"
+      "  const int lane = threadIdx.x & 31;\n"
+      "  const BsTr tr = bs_tr_init(lane);\n"
+      "  u64* bins = s_bins + threadIdx.x;\n"
+      "  u32* cw = (u32*)(s_bins + (BSB_LMAX + 1) * BSB_NTHR) + threadIdx.x;\n"
+      "  u32* ctw = (u32*)(s_bins + (BSB_LMAX + 1) * BSB_NTHR) + ((size_t)1 << BSB_LMAX) * BSB_NTHR +\n"
+      "             threadIdx.x;\n"
+      "  u64* nkw = s_bins + (BSB_LMAX + 1) * BSB_NTHR + ((size_t)1 << BSB_LMAX) * BSB_NTHR +\n"
+      "             (threadIdx.x >> 5) * 65;\n"
+      "  for (int i = lane; i < 65; i += 32) nkw[i] = 0ull;\n"
+    :
+      "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR, 4)\n"
       "bs_batch(const BGraph* __restrict__ graphs, int G, int K, int Kp, u64 total,\n"
       "         const u64* __restrict__ lt, const u64* __restrict__ nt, const u64* __restrict__ wm,\n"
       "         const mx* __restrict__ pt, const u64* __restrict__ thw, u64* limbs, u64* nk,\n"
@@ -653,7 +696,8 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
       "  u32* cw = (u32*)(s_bins + (BSB_LMAX + 1) * BSB_NTHR) + threadIdx.x;\n"
       "  u64* nkw = s_bins + (BSB_LMAX + 1) * BSB_NTHR + (((size_t)1 << BSB_LMAX) * BSB_NTHR) / 2 +\n"
       "             (threadIdx.x >> 5) * 65;\n"
-      "  for (int i = lane; i < 65; i += 32) nkw[i] = 0ull;\n"
+      "  for (int i = lane; i < 65; i += 32) nkw[i] = 0ull;\n";
+  kern +=
       "  int cur = -1;   // network whose counts nkw holds\n"
       "  const u64 t0 = bs_timer();\n"
       "  for (;;) {\n"
@@ -679,8 +723,12 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   for (int r = 0; r < G; ++r)
     kern += "      case " + std::to_string(r) + ": st = bsb_conn<G" + std::to_string(r) +
             ">(prefix, lane, prune, cw); break;\n";
-  kern += "    }\n"
-          "    if (st) bsb_finish(Bp, st, prefix, lane, K, Kp, lt, nt, wm, pt, thw, limbs, nkw, bins, cw);\n"
+  kern += "    }\n";
+  kern += E.grad ?
+          "    if (st) bsb_finish_grad(Bp, st, prefix, lane, K, Kp, lt, nt, wm2, pt, thw, tt, lwex, thwex,\n"
+          "                            ptex, limbs, nkw, bins, cw, ctw, tr);\n" :
+          "    if (st) bsb_finish(Bp, st, prefix, lane, K, Kp, lt, nt, wm, pt, thw, limbs, nkw, bins, cw);\n";
+  kern +=
           "    __syncwarp();\n  }\n"
           "  __syncwarp();\n"
           "  if (cur >= 0) bsb_flush_counts(graphs + cur, nkw, nk, lane);\n}\n";
@@ -700,6 +748,7 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   const int Kp = E.Kp;
   unsigned long long begin = 0;
   size_t lt = 0, nt = 0, wm = 0, pt = 0, th = 0;
+  size_t wm2 = 0, tt = 0, lwex = 0, thwex = 0, ptex = 0, outl = 0;   // gradient module
   int nk_off = 0;
   std::vector<int> nk_offs(G);
   for (int i = 0; i < G; ++i) {
@@ -738,8 +787,21 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
     b.top = bp.ell + bp.tb + bp.L;
     b.lane_mask = bp.ell >= 5 ? 0xffffffffu : ((1u << (1 << bp.ell)) - 1u);
     b.full_counts = full_counts(bp.ell);
+    b.ell = bp.ell;
+    b.d = bp.d;
+    b.thr_mask = bp.tb >= 5 ? 0xffffffffu : ((1u << (1 << bp.tb)) - 1u);
+    b.pex_mask = bp.pex;
+    if (E.grad) {
+      b.wm2_off = (int)wm2; wm2 += (size_t)2 * ((size_t)1 << bp.L) * Kp;
+      b.tt_off = (int)tt; tt += (size_t)1024 * Kp;
+      b.lwex_off = (int)lwex; lwex += (size_t)5 * 32 * Kp;
+      b.thwex_off = (int)thwex; thwex += (size_t)5 * 32 * Kp;
+      b.ptex_off = (int)ptex; ptex += (size_t)K * bp.d * 128;
+      b.out_off = (int)outl; outl += (size_t)K * (1 + 2 * b.m) * kBsbLimbs;
+    }
   }
   E.total = begin;
+  E.n_out = E.grad ? outl : (size_t)kBsbLimbs * G * K;
   E.n_lt = lt; E.n_nt = nt; E.n_wm = wm; E.n_pt = pt; E.n_thw = th;
   size_t off = 0;
   E.o_graphs = off; off = a256(off + sizeof(BGraphHost) * G);
@@ -748,15 +810,21 @@ static int bsb_layout(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   E.o_wm = off; off = a256(off + 8 * wm);
   E.o_pt = off; off = a256(off + sizeof(MxHost) * pt);
   E.o_thw = off; off = a256(off + 8 * th);
+  E.o_wm2 = off; off = a256(off + 8 * wm2);
+  E.o_tt = off; off = a256(off + 8 * tt);
+  E.o_lwex = off; off = a256(off + 8 * lwex);
+  E.o_thwex = off; off = a256(off + 8 * thwex);
+  E.o_ptex = off; off = a256(off + sizeof(MxHost) * ptex);
   E.o_upload_end = off;
-  E.o_limbs = off; off = a256(off + 8 * (size_t)kBsbLimbs * G * K);
+  E.o_limbs = off; off = a256(off + 8 * E.n_out);
   E.o_nk = off; off = a256(off + 8 * (size_t)E.nk_total);
   E.o_counter = off; off = a256(off + 8);
   E.o_status = off; off = a256(off + 4);
   E.o_end = off;
   if ((rc = scratch_acquire(dev.device, E.o_end, E.o_end, &E.scr))) return rc;
   memcpy((char*)E.scr->hmem + E.o_graphs, E.bg.data(), sizeof(BGraphHost) * G);
-  E.smem = (size_t)(E.lmax + 1) * kBsbThreads * 8 + ((size_t)1 << E.lmax) * kBsbThreads * 4 +
+  E.smem = (size_t)(E.lmax + 1) * kBsbThreads * 8 +
+           ((size_t)1 << E.lmax) * kBsbThreads * 4 * (E.grad ? 2 : 1) +
            (size_t)(kBsbThreads / 32) * 65 * 8;
   cudaError_t e = cudaFuncSetAttribute((const void*)E.jit.kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E.smem);
@@ -779,6 +847,11 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
   unsigned long long* wm = (unsigned long long*)(h + E.o_wm);
   MxHost* pt = (MxHost*)(h + E.o_pt);
   unsigned long long* th = (unsigned long long*)(h + E.o_thw);
+  unsigned long long* wm2t = (unsigned long long*)(h + E.o_wm2);
+  unsigned long long* ttt = (unsigned long long*)(h + E.o_tt);
+  unsigned long long* lwx = (unsigned long long*)(h + E.o_lwex);
+  unsigned long long* thx = (unsigned long long*)(h + E.o_thwex);
+  MxHost* ptx = (MxHost*)(h + E.o_ptex);
   const int K = E.K, Kp = E.Kp;
   std::vector<size_t> poff(E.G);
   size_t acc = 0;
@@ -827,7 +900,49 @@ static void bsb_tables(BsBatch& E, const pbat_graph* graphs, const double* p) {
         dd tab[1 << 7];
         product_table(pv, bp.perm.data() + top + sh, b.lev_bits[l], tab);
         for (int v = 0; v < (1 << b.lev_bits[l]); ++v) ptk[b.lev_off[l] + v] = to_mx(tab[v]);
+        if (E.grad)
+          for (int jj = 0; jj < b.lev_bits[l]; ++jj) {
+            if (!((bp.pex >> (top + sh + jj)) & 1ull)) continue;   // divided by p on the host
+            // the level's product without prefix arc sh + jj, indexed by the
+            // level value with that arc's bit removed
+            int others[8];
+            for (int x = 0, c = 0; x < b.lev_bits[l]; ++x)
+              if (x != jj) others[c++] = bp.perm[top + sh + x];
+            dd ex[1 << 6];
+            product_table(pv, others, b.lev_bits[l] - 1, ex);
+            MxHost* row = ptx + b.ptex_off + (((size_t)k * bp.d + sh + jj) << 7);
+            for (int v = 0; v < (1 << b.lev_bits[l]); ++v)
+              row[v] = to_mx(ex[(v & ((1 << jj) - 1)) | ((v >> (jj + 1)) << jj)]);
+          }
         sh += b.lev_bits[l];
+      }
+      if (E.grad) {
+        // 128-bit walk masses, thread-pattern byte tables, and the lane and
+        // thread pattern masses without each of their arcs
+        dd w2[32];
+        product_table(pv, bp.perm.data() + bp.ell + bp.tb, bp.L, w2);
+        for (int gi = 0; gi < (1 << bp.L); ++gi) {
+          const u128 f = to_fixed127(w2[gi]);
+          wm2t[b.wm2_off + ((size_t)gi * Kp + k) * 2] = f.lo;
+          wm2t[b.wm2_off + ((size_t)gi * Kp + k) * 2 + 1] = f.hi;
+        }
+        byte_table_sums(tw, 1 << bp.tb, ttt + b.tt_off + k, Kp);
+        auto excluded = [&](const int* arcs, int n, unsigned long long* out) {
+          for (int x = 0; x < 5; ++x)
+            for (int j = 0; j < 32; ++j) out[((size_t)(x * 32 + j)) * Kp + k] = 0ull;
+          for (int x = 0; x < n; ++x) {
+            int oth[5];
+            for (int i = 0, c = 0; i < n; ++i)
+              if (i != x) oth[c++] = arcs[i];
+            dd tab[16];
+            product_table(pv, oth, n - 1, tab);
+            for (int j = 0; j < (1 << n); ++j)
+              out[((size_t)(x * 32 + j)) * Kp + k] =
+                  fixed_u64(tab[(j & ((1 << x) - 1)) | ((j >> (x + 1)) << x)], 63);
+          }
+        };
+        excluded(bp.perm.data(), bp.ell, lwx + b.lwex_off);
+        excluded(bp.perm.data() + bp.ell, bp.tb, thx + b.thwex_off);
       }
     }
   }
@@ -851,9 +966,15 @@ static int bsb_enqueue(BsBatch& E, cudaStream_t st, unsigned long long budget_ns
   void *limbs = d + E.o_limbs, *nk = d + E.o_nk, *counter = d + E.o_counter, *status = d + E.o_status;
   int G = E.G, K = E.K, Kp = E.Kp;
   unsigned long long total = E.total, bud = budget_ns;
+  const void *wm2 = d + E.o_wm2, *tt = d + E.o_tt, *lwex = d + E.o_lwex, *thwex = d + E.o_thwex;
+  const void* ptex = d + E.o_ptex;
   void* args[] = {(void*)&graphs, &G, &K, &Kp, &total, (void*)&lt, (void*)&nt, (void*)&wm,
                   (void*)&pt, (void*)&thw, &limbs, &nk, &counter, &status, &bud};
-  e = cudaLaunchKernel((const void*)E.jit.kernel, dim3(E.grid), dim3(kBsbThreads), args, E.smem, st);
+  void* gargs[] = {(void*)&graphs, &G, &K, &Kp, &total, (void*)&lt, (void*)&nt, (void*)&wm2,
+                   (void*)&pt, (void*)&thw, (void*)&tt, (void*)&lwex, (void*)&thwex, (void*)&ptex,
+                   &limbs, &nk, &counter, &status, &bud};
+  e = cudaLaunchKernel((const void*)E.jit.kernel, dim3(E.grid), dim3(kBsbThreads),
+                       E.grad ? gargs : args, E.smem, st);
   if (e != cudaSuccess) return fail(PBAT_ECUDA, "batched launch: %s", cudaGetErrorString(e));
   return PBAT_OK;
 }
@@ -864,9 +985,14 @@ static double bsb_limbs_value(const unsigned long long* limbs) {
 }
 
 // Source of the batched module (diagnostic; no device needed).
-int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o, std::string& out) {
+int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o,
+                   const std::vector<std::string>* elig, std::string& out) {
   if (G > kBsbMaxGraphs) return fail(PBAT_ERANGE, "at most %d networks per bit-sliced batch", kBsbMaxGraphs);
   BsBatch E;
+  if (elig) {
+    E.grad = true;
+    E.elig = *elig;
+  }
   std::vector<unsigned long long> items;
   return bsb_source(E, G, graphs, K, o, items, out);
 }
@@ -933,9 +1059,17 @@ static int bsb_tune_walk(int G, const pbat_graph* graphs, int K, const double* p
 // R (and N_k) of a batch with the bit-sliced batched kernel; returns
 // PBAT_ENOTSUP when the batch is outside its limits (the caller then uses the
 // frontier kernel).
+// R (and N_k) of a batch with the bit-sliced batched kernel; with `elig`
+// (one string of '0'/'1' walk-arc eligibility per network) the gradient
+// module also returns dR/dp in dRdp_out (the layout of p), and lists in
+// *coarse the (network, p-vector) pairs whose R or gradient the
+// fixed-point error bounds cannot certify to 1e-12 (the caller re-runs them
+// exactly).  Returns PBAT_ENOTSUP when the batch is outside the module's
+// limits (the caller then uses the frontier kernel).
 int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
                    cudaStream_t st, double* R_out, uint64_t* Nk_out, const std::string& key,
-                   const DeviceInfo& dev, uint64_t* kernel_ns) {
+                   const DeviceInfo& dev, uint64_t* kernel_ns, const std::vector<std::string>* elig,
+                   double* dRdp_out, std::vector<std::pair<int, int>>* coarse) {
   NvtxRange nv("pbat batched");
   if (G > kBsbMaxGraphs) return PBAT_ENOTSUP;
   BsBatch* E = nullptr;
@@ -946,10 +1080,17 @@ int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, cons
   }
   if (!E) {
     pbat_options ob = o;
-    if (o.autotune && o.walk_bits < 0) ob.walk_bits = bsb_tune_walk(G, graphs, K, p, o, st, dev);
+    // the gradient module walks the longest items (L = 5) unless told
+    // otherwise: its per-item reductions are the larger share
+    if (!elig && o.autotune && o.walk_bits < 0)
+      ob.walk_bits = bsb_tune_walk(G, graphs, K, p, o, st, dev);
     std::unique_ptr<BsBatch> ne(new BsBatch());
     ne->key = key;
     ne->busy = true;
+    if (elig) {
+      ne->grad = true;
+      ne->elig = *elig;
+    }
     int rc = bsb_build(*ne, G, graphs, K, ob, dev);
     if (rc) {
       if (ne->scr) scratch_release(ne->scr);
@@ -1018,9 +1159,61 @@ int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, cons
   if (*(unsigned int*)(h + E->o_status) & 1u) return done(fail(PBAT_ETIMEOUT, "time budget ran out on the device"));
   const unsigned long long* limbs = (const unsigned long long*)(h + E->o_limbs);
   const unsigned long long* nk = (const unsigned long long*)(h + E->o_nk);
-  for (int i = 0; i < G; ++i)
-    for (int k = 0; k < K; ++k)
-      R_out[(size_t)i * K + k] = bsb_limbs_value(limbs + ((size_t)i * K + k) * kBsbLimbs);
+  if (!E->grad) {
+    for (int r = 0; r < G; ++r) {
+      const int i = E->bg[r].gidx;
+      // absolute error of R: lane sums 2^-61, thread masses 2^-59, 64-bit
+      // walk masses 2^(L-64), in units of the enumerated mass
+      const double bound = ldexp(1.0, -61) + ldexp(1.0, -59) + ldexp(1.0, E->bg[r].L - 64);
+      for (int k = 0; k < K; ++k) {
+        const double R = bsb_limbs_value(limbs + ((size_t)i * K + k) * kBsbLimbs);
+        R_out[(size_t)i * K + k] = R;
+        if (coarse && R < 1e12 * bound) coarse->push_back({i, k});
+      }
+    }
+  } else {
+    // R, then A_q and B_q of every internal arc q per (network, p-vector):
+    // dR/dp is A / p - B / (1 - p) for walk arcs and prefix arcs, except A -
+    // B for prefix arcs outside [2^-20, 1 - 2^-20], and A for lane and
+    // thread arcs (as for the single-network fused kernel)
+    std::vector<size_t> poff(G);
+    for (int i = 0, acc = 0; i < G; ++i) {
+      poff[i] = (size_t)acc;
+      acc += K * graphs[i].n_arcs;
+    }
+    for (int r = 0; r < G; ++r) {
+      const BGraphHost& b = E->bg[r];
+      const int i = b.gidx, m = b.m, top = b.top, walk0 = b.ell + b.tb;
+      const BsPlan& bp = E->plans[i];
+      for (int k = 0; k < K; ++k) {
+        const unsigned long long* base = limbs + b.out_off + (size_t)k * (1 + 2 * m) * kBsbLimbs;
+        const double* pk = p + poff[i] + (size_t)k * m;
+        const dd Rd = limbs256_to_dd(base);
+        const double R = Rd.hi + Rd.lo;
+        R_out[(size_t)i * K + k] = R;
+        // the single-network fused kernel's bounds: R within 2^-61 + 2^-59,
+        // each gradient entry within 2^-57 (walk masses are 128-bit here)
+        bool bad = R < 1e12 * (ldexp(1.0, -61) + ldexp(1.0, -59));
+        const double Eg = ldexp(1.0, -57);
+        for (int q = 0; q < m; ++q) {
+          const dd A = limbs256_to_dd(base + (size_t)(1 + 2 * q) * kBsbLimbs);
+          const dd B = limbs256_to_dd(base + (size_t)(2 + 2 * q) * kBsbLimbs);
+          const int a = bp.perm[q];
+          dd v;
+          if (q >= top && ((bp.pex >> q) & 1ull))
+            v = dd_sub(A, B);
+          else if (q >= walk0)
+            v = dd_sub(dd_mul(A, dd_recip(pk[a])), dd_mul(B, dd_recip_dd(dd_one_minus(pk[a]))));
+          else
+            v = A;
+          const double g = v.hi + v.lo;
+          dRdp_out[poff[i] + (size_t)k * m + a] = g;
+          bad = bad || Eg > 1e-12 * std::max(std::fabs(g) - Eg, 1e-4 * R);
+        }
+        if (bad && coarse) coarse->push_back({i, k});
+      }
+    }
+  }
   if (Nk_out) memcpy(Nk_out, nk, sizeof(uint64_t) * E->nk_total);
   return done(PBAT_OK);
 }

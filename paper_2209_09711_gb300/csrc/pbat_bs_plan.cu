@@ -509,6 +509,10 @@ int bs_make_plan(const GraphIn& g, const pbat_options& o, int nthr, BsPlan& bp,
                 bp.L, bp.d);
   bs_generate(g, bp);
   if (o.prune == 2 && bp.L > 0 && extra == 0) bs_smaller_walk(g, bp, p_for_grad);
+  bp.pex = 0;
+  if (p_for_grad)
+    for (int k = bp.ell + bp.tb + bp.L; k < m; ++k)
+      if (!bs_walk_ok(p_for_grad, bp.perm[k])) bp.pex |= 1ull << k;
   return PBAT_OK;
 }
 

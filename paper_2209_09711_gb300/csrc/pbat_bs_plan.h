@@ -14,6 +14,9 @@ struct BsPlan {
   bool grad = false;
   int ell = 0, tb = 0, L = 0, d = 0, r = 0;
   int minb = 0;           // __launch_bounds__ minimum blocks per SM (0: none)
+  // fused kernel: internal prefix arcs whose p is outside [2^-20, 1 - 2^-20]
+  // (their sums use the excluded-arc tables instead of dividing by p, 1 - p)
+  unsigned long long pex = 0;
   std::vector<int> perm;  // internal position -> input arc
   std::string gen;        // generated bs_inv / bs_var
   int ncore = 0, ops_inv = 0, ops_var = 0;

@@ -196,6 +196,41 @@ __device__ __forceinline__ mx bs_prefix_mass(const BsParams& P, const mx* __rest
   }
   return w;
 }
+// Per-lane constants of the 32x32 bit transpose below: byte selectors of the
+// 16- and 8-bit rounds, rotate amounts and keep-masks of the 4-, 2- and
+// 1-bit rounds.
+struct BsTr { u32 sel16, sel8, rot4, rot2, rot1, keep4, keep2, keep1; };
+__device__ __forceinline__ BsTr bs_tr_init(int lane) {
+  BsTr t;
+  t.sel16 = (lane & 16) ? 0x3276u : 0x5410u;
+  t.sel8 = (lane & 8) ? 0x3715u : 0x6240u;
+  t.rot4 = (lane & 4) ? 28u : 4u;
+  t.rot2 = (lane & 2) ? 30u : 2u;
+  t.rot1 = (lane & 1) ? 31u : 1u;
+  t.keep4 = (lane & 4) ? 0xF0F0F0F0u : 0x0F0F0F0Fu;
+  t.keep2 = (lane & 2) ? 0xCCCCCCCCu : 0x33333333u;
+  t.keep1 = (lane & 1) ? 0xAAAAAAAAu : 0x55555555u;
+  return t;
+}
+// Round with distance sh: lanes with bit sh clear keep the low half of
+// every 2sh-bit group and take the partner's low halves into their high
+// halves; lanes with the bit set keep the high halves and take the
+// partner's high halves into their low halves.  Byte-sized rounds are one
+// byte permute; smaller ones a rotate and a bit select.
+__device__ __forceinline__ u32 bs_transpose32(u32 x, const BsTr& t) {
+  u32 y = __shfl_xor_sync(0xffffffffu, x, 16);
+  x = __byte_perm(x, y, t.sel16);
+  y = __shfl_xor_sync(0xffffffffu, x, 8);
+  x = __byte_perm(x, y, t.sel8);
+  y = __shfl_xor_sync(0xffffffffu, x, 4);
+  x = (x & t.keep4) | (__funnelshift_l(y, y, t.rot4) & ~t.keep4);
+  y = __shfl_xor_sync(0xffffffffu, x, 2);
+  x = (x & t.keep2) | (__funnelshift_l(y, y, t.rot2) & ~t.keep2);
+  y = __shfl_xor_sync(0xffffffffu, x, 1);
+  x = (x & t.keep1) | (__funnelshift_l(y, y, t.rot1) & ~t.keep1);
+  return x;
+}
+
 //@@GENERATED@@
 // connectivity of one uniform state (every word 0 or ~0): the prune test
 __device__ __forceinline__ u32 bs_uniform(const u32* a) {
@@ -391,49 +426,18 @@ struct BsGradParams {
   dd inv_p[64], inv_q[64];
 };
 
-// Per-lane constants of the 32x32 bit transpose below: byte selectors of the
-// 16- and 8-bit rounds, rotate amounts and keep-masks of the 4-, 2- and
-// 1-bit rounds.
-struct BsTr { u32 sel16, sel8, rot4, rot2, rot1, keep4, keep2, keep1; };
-__device__ __forceinline__ BsTr bs_tr_init(int lane) {
-  BsTr t;
-  t.sel16 = (lane & 16) ? 0x3276u : 0x5410u;
-  t.sel8 = (lane & 8) ? 0x3715u : 0x6240u;
-  t.rot4 = (lane & 4) ? 28u : 4u;
-  t.rot2 = (lane & 2) ? 30u : 2u;
-  t.rot1 = (lane & 1) ? 31u : 1u;
-  t.keep4 = (lane & 4) ? 0xF0F0F0F0u : 0x0F0F0F0Fu;
-  t.keep2 = (lane & 2) ? 0xCCCCCCCCu : 0x33333333u;
-  t.keep1 = (lane & 1) ? 0xAAAAAAAAu : 0x55555555u;
-  return t;
-}
-// Round with distance sh: lanes with bit sh clear keep the low half of
-// every 2sh-bit group and take the partner's low halves into their high
-// halves; lanes with the bit set keep the high halves and take the
-// partner's high halves into their low halves.  Byte-sized rounds are one
-// byte permute; smaller ones a rotate and a bit select.
-__device__ __forceinline__ u32 bs_transpose32(u32 x, const BsTr& t) {
-  u32 y = __shfl_xor_sync(0xffffffffu, x, 16);
-  x = __byte_perm(x, y, t.sel16);
-  y = __shfl_xor_sync(0xffffffffu, x, 8);
-  x = __byte_perm(x, y, t.sel8);
-  y = __shfl_xor_sync(0xffffffffu, x, 4);
-  x = (x & t.keep4) | (__funnelshift_l(y, y, t.rot4) & ~t.keep4);
-  y = __shfl_xor_sync(0xffffffffu, x, 2);
-  x = (x & t.keep2) | (__funnelshift_l(y, y, t.rot2) & ~t.keep2);
-  y = __shfl_xor_sync(0xffffffffu, x, 1);
-  x = (x & t.keep1) | (__funnelshift_l(y, y, t.rot1) & ~t.keep1);
-  return x;
-}
-
 static_assert(BS_TOP <= 32, "lane k owns internal arc k");
 
-// The prefix factor of internal arc k for this item: for a prefix arc the
-// item's prefix mass without that arc's own factor (its level's entry from
-// the excluded-arc table), otherwise the whole prefix mass.
+// The prefix factor of internal arc k for this item.  Internal arcs, and
+// prefix arcs with p in [2^-20, 1 - 2^-20], take the whole prefix mass: a
+// prefix arc's two sums then carry its own factor p or 1 - p, which the
+// host divides out once (as for walk arcs) -- the sums' errors are relative
+// to their terms, so the division does not amplify them.  Prefix arcs with
+// p outside that range (bits set in BS_PEX_MASK) take the item's prefix
+// mass without their own factor, from the excluded-arc table.
 __device__ __forceinline__ mx bs_arc_factor(const BsParams& P, const mx* __restrict__ ptab,
                                             const mx* __restrict__ ptab_ex, u64 prefix, int k, mx wpre) {
-  if (k < BS_TOP) return wpre;
+  if (k < BS_TOP || !((BS_PEX_MASK >> k) & 1ull)) return wpre;
   const int j = k - BS_TOP;
   int l = 0, sh = 0;
   while (sh + P.lev_bits[l] <= j) { sh += P.lev_bits[l]; ++l; }
@@ -729,7 +733,14 @@ struct BGraph {
   int L, top;
   u32 lane_mask;
   int pad0;
+  // gradient module only: offsets of the 128-bit walk masses, the thread
+  // byte tables, the excluded-arc masses of lane, thread and prefix arcs,
+  // and of this network's results; lane arcs, prefix arcs, thread mask
+  int wm2_off, tt_off, lwex_off, thwex_off, ptex_off, out_off, ell, d;
+  u32 thr_mask;
+  int pad1;
   u64 full_counts;
+  u64 pex_mask;   // gradient module: prefix arcs using the excluded-arc tables
   u64 binom[64];
 };
 
@@ -948,6 +959,202 @@ __device__ __forceinline__ void bsb_finish(const BGraph* __restrict__ Bp, int st
     if (!(lane & 1) && idx < kc) {
       const mx w = bsb_prefix_mass(gpt + (size_t)(k0 + idx) * pt_size, nlev, lev_bits, lev_off, prefix);
       bsb_limb_add(glimbs + (size_t)(k0 + idx) * BSB_LIMBS, mx_prod(w, T[0]), w.e);
+    }
+  }
+}
+// ---------------------------------------------------------------------------
+// Batched fused R + N_k + dR/dp (the gradient module): the item's
+// connectivity words (cw, one per walk state) and their 32x32 lane
+// transposes (ctw) are formed once; then for each p-vector in turn the
+// per-arc sums of the single-network fused kernel are built from them --
+// exact integer pair differences for lane and thread arcs, the parts A and
+// T - A of the walk arcs (128-bit walk masses), item totals times the
+// prefix mass without the arc for prefix arcs -- and added to that
+// (network, p-vector)'s 256-bit results: R, then A_k and B_k of every
+// internal arc k.  Prefix arcs take the item's whole prefix mass (the host
+// divides their sums by p and 1 - p) unless some p-vector puts their p
+// outside [2^-20, 1 - 2^-20] (bit set in pex_mask).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ mx bsb_ex_factor(const mx* __restrict__ tk, const mx* __restrict__ exk,
+                                            int nlev, const int (&lev_bits)[8], const int (&lev_off)[8],
+                                            u64 prefix, int j) {
+  // prefix mass without prefix arc j: its level's entry from the excluded
+  // table (rows of 128), the other levels from the plain table
+  mx f = mx{1ull << 63, 0, 0};
+  int sh = 0;
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    if (l >= nlev) break;
+    const u64 v = (prefix >> sh) & ((1ull << lev_bits[l]) - 1ull);
+    const bool mine = j >= sh && j < sh + lev_bits[l];
+    const ulonglong2 q = __ldg((const ulonglong2*)(mine ? exk + ((size_t)j << 7) + v : tk + lev_off[l] + v));
+    const mx t = mx{q.x, (int)(u32)q.y, 0};
+    f = l ? mx_mul(f, t) : t;
+    sh += lev_bits[l];
+  }
+  return f;
+}
+
+__device__ __forceinline__ void bsb_finish_grad(
+    const BGraph* __restrict__ Bp, int st, u64 prefix, int lane, int K, int Kp,
+    const u64* __restrict__ lt, const u64* __restrict__ nt, const u64* __restrict__ wm2,
+    const mx* __restrict__ pt, const u64* __restrict__ thw, const u64* __restrict__ tt,
+    const u64* __restrict__ lwex, const u64* __restrict__ thwex, const mx* __restrict__ ptex,
+    u64* limbs, u64* nkw, u64* bins, const u32* cw, u32* ctw, const BsTr& tr) {
+  constexpr int nsh[6] = BS_NK_SHIFTS, nwd[6] = BS_NK_WIDTHS;
+  const int L = Bp->L, tb = Bp->tb, ell = Bp->ell, top = Bp->top, m = Bp->m, nlev = Bp->nlev;
+  const int pt_size = Bp->pt_size, d = Bp->d;
+  const u32 lane_mask = Bp->lane_mask, thr_mask = Bp->thr_mask;
+  int lev_bits[8], lev_off[8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    lev_bits[l] = Bp->lev_bits[l];
+    lev_off[l] = Bp->lev_off[l];
+  }
+  const int pc_pre = __popcll((long long)prefix);
+  const bool thr_on = lane < (1 << tb);
+  const int nw = 1 << L;
+  // ---- N_k, as in the R module
+  if (st == 1) {
+    for (int j = lane; j <= top; j += 32) nkw[pc_pre + j] += __ldg(&Bp->binom[j]);
+  } else {
+    for (int r = 0; r <= L; ++r) bins[r * BSB_NTHR] = 0ull;
+    const u64* ntg = nt + Bp->nt_off;
+    for (int g = 0; g < nw; ++g) {
+      const u32 c = cw[g * BSB_NTHR];
+      if (!c) continue;
+      bins[__popc(g) * BSB_NTHR] += c == lane_mask ? Bp->full_counts
+          : __ldg(ntg + (c & 0xffu)) + __ldg(ntg + 256 + ((c >> 8) & 0xffu)) +
+            __ldg(ntg + 512 + ((c >> 16) & 0xffu)) + __ldg(ntg + 768 + (c >> 24));
+    }
+    u64 c11[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) c11[i] = 0ull;
+#pragma unroll
+    for (int r = 0; r <= 5; ++r) {
+      if (r > L) break;
+      const u64 n = bins[r * BSB_NTHR];
+#pragma unroll
+      for (int cl = 0; cl < 6; ++cl) c11[r + cl] += (n >> nsh[cl]) & ((1ull << nwd[cl]) - 1ull);
+    }
+    if (thr_on) {
+      const int base = pc_pre + __popc(lane);
+#pragma unroll
+      for (int i = 0; i < 11; ++i)
+        if (c11[i]) atomicAdd(&nkw[base + i], c11[i]);
+    }
+    // ---- the lane transposes, once per word: lane j then holds the
+    // threads' bits of lane pattern j (lanes past the thread patterns hold
+    // no thread's states); zero when no lane's word is partly connected
+    for (int g = 0; g < nw; ++g) {
+      const u32 c = thr_on ? cw[g * BSB_NTHR] : 0u;
+      const bool mixed = __any_sync(0xffffffffu, c != 0u && c != lane_mask);
+      const u32 ct = mixed ? bs_transpose32(c, tr) : 0u;
+      ctw[g * BSB_NTHR] = lane < (1 << ell) ? ct : 0u;
+    }
+  }
+  const int stride = 1 + 2 * m;
+  u64* gl = limbs + Bp->out_off;
+  const u64* ltg = lt + Bp->lt_off;
+  const u64* ttg = tt + Bp->tt_off;
+  const ulonglong2* wmg = (const ulonglong2*)(wm2 + Bp->wm2_off);
+  for (int k = 0; k < K; ++k) {
+    u128 S = u128{0ull, 1ull << 60};   // a fully connected item: mass 1 at scale 2^124
+    u128 myX = u128{0ull, 0ull}, myY = u128{0ull, 0ull};
+    if (st == 2) {
+      u128 T = u128{0ull, 0ull}, T2 = u128{0ull, 0ull};
+      u128 Aw[5];
+#pragma unroll
+      for (int b = 0; b < 5; ++b) Aw[b] = u128{0ull, 0ull};
+      for (int g = 0; g < nw; ++g) {
+        const u32 c = cw[g * BSB_NTHR], ct = ctw[g * BSB_NTHR];
+        if (!(c | ct)) continue;
+        const ulonglong2 wv = __ldg(wmg + (size_t)g * Kp + k);
+        const u128 full = u128{(wv.x >> 2) | (wv.y << 62), wv.y >> 2};   // scale 2^125
+        if (c) {
+          u128 x = full;
+          if (c != lane_mask) {
+            const u64 sR = __ldg(ltg + (size_t)(c & 0xffu) * Kp + k) +
+                           __ldg(ltg + (size_t)(256 + ((c >> 8) & 0xffu)) * Kp + k) +
+                           __ldg(ltg + (size_t)(512 + ((c >> 16) & 0xffu)) * Kp + k) +
+                           __ldg(ltg + (size_t)(768 + (c >> 24)) * Kp + k);
+            x = mul64x128_shr64(sR, wv.x, wv.y);
+          }
+          u128_add(T, x.lo, x.hi);
+#pragma unroll
+          for (int b = 0; b < 5; ++b)
+            if (b < L && ((g >> b) & 1)) u128_add(Aw[b], x.lo, x.hi);
+        }
+        if (ct) {
+          u128 y = full;
+          if (ct != thr_mask) {
+            const u64 s2 = __ldg(ttg + (size_t)(ct & 0xffu) * Kp + k) +
+                           __ldg(ttg + (size_t)(256 + ((ct >> 8) & 0xffu)) * Kp + k) +
+                           __ldg(ttg + (size_t)(512 + ((ct >> 16) & 0xffu)) * Kp + k) +
+                           __ldg(ttg + (size_t)(768 + (ct >> 24)) * Kp + k);
+            y = mul64x128_shr64(s2, wv.x, wv.y);
+          }
+          u128_add(T2, y.lo, y.hi);
+        }
+      }
+      // exact warp sums (scale 2^124); lane k ends with internal arc k's
+      const u64 thwk = thr_on ? __ldg(thw + Bp->thw_off + (size_t)lane * Kp + k) : 0ull;
+      S = warp_sum_u128(mul64x128_shr64(thwk, T.lo, T.hi));
+      for (int i = 0; i < ell; ++i) {
+        const u128 o = shfl_xor_u128(T2, 1 << i);
+        const u128 d2 = u128_sub(T2, o);
+        const u64 w = ((lane >> i) & 1) && lane < (1 << ell)
+                          ? __ldg(lwex + Bp->lwex_off + ((size_t)(i * 32 + lane)) * Kp + k) : 0ull;
+        const u128 sv = warp_sum_u128(mul64x128_shr64(w, d2.lo, d2.hi));
+        if (lane == i) myX = sv;
+      }
+      for (int i = 0; i < tb; ++i) {
+        const u128 o = shfl_xor_u128(T, 1 << i);
+        const u128 d1 = u128_sub(T, o);
+        const u64 w = ((lane >> i) & 1) && thr_on
+                          ? __ldg(thwex + Bp->thwex_off + ((size_t)(i * 32 + lane)) * Kp + k) : 0ull;
+        const u128 sv = warp_sum_u128(mul64x128_shr64(w, d1.lo, d1.hi));
+        if (lane == ell + i) myX = sv;
+      }
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        if (b >= L) break;
+        const u128 sa = warp_sum_u128(mul64x128_shr64(thwk, Aw[b].lo, Aw[b].hi));
+        const u128 z = u128_sub(T, Aw[b]);
+        const u128 sz = warp_sum_u128(mul64x128_shr64(thwk, z.lo, z.hi));
+        if (lane == ell + tb + b) { myX = sa; myY = sz; }
+      }
+    }
+    // ---- prefix factors of p-vector k and the additions to its results
+    const mx* tk = pt + Bp->pt_off + (size_t)k * pt_size;
+    const mx* exk = ptex + Bp->ptex_off + ((size_t)k * d << 7);
+    const mx wpre = bsb_prefix_mass(tk, nlev, lev_bits, lev_off, prefix);
+    u64* out = gl + (size_t)k * stride * BSB_LIMBS;
+    if (lane == 0) bsb_limb_add(out, mx_prod(wpre, S), wpre.e);
+    if (lane < m) {
+      u128 X = u128{0ull, 0ull}, Y = u128{0ull, 0ull};
+      mx f = wpre;
+      if (lane >= top) {
+        // a prefix arc: the item's total, into A when the arc works in this
+        // item and into B when it fails -- with the whole prefix mass (the
+        // host divides by p and 1 - p), or for an arc whose p is outside
+        // [2^-20, 1 - 2^-20] under some p-vector, without its own factor
+        if ((Bp->pex_mask >> lane) & 1ull)
+          f = bsb_ex_factor(tk, exk, nlev, lev_bits, lev_off, prefix, lane - top);
+        if ((prefix >> (lane - top)) & 1ull) X = S; else Y = S;
+      } else if (st == 2) {
+        X = myX;
+        Y = myY;
+      }
+      bsb_limb_add(out + (1 + 2 * lane) * BSB_LIMBS, mx_prod(f, X), f.e);
+      bsb_limb_add(out + (2 + 2 * lane) * BSB_LIMBS, mx_prod(f, Y), f.e);
+    }
+    if (lane + 32 < m) {
+      const int j = lane + 32 - top;
+      const mx f = ((Bp->pex_mask >> (lane + 32)) & 1ull)
+                       ? bsb_ex_factor(tk, exk, nlev, lev_bits, lev_off, prefix, j) : wpre;
+      const bool on = (prefix >> j) & 1ull;
+      bsb_limb_add(out + ((on ? 1 : 2) + 2 * (lane + 32)) * BSB_LIMBS, mx_prod(f, S), f.e);
     }
   }
 }

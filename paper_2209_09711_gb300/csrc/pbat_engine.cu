@@ -67,7 +67,8 @@ const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl);
 void bs_describe(const BsLaunch& bl, int* out6);
 int bs_source_for(const GraphIn& g, const double* p, bool grad, const pbat_options& o,
                   std::string& out);
-int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o, std::string& out);
+int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o,
+                   const std::vector<std::string>* elig, std::string& out);
 
 // ---------------------------------------------------------------------------
 // errors
@@ -1064,23 +1065,37 @@ int pbat_kernel_source(int n_nodes, int n_arcs, const int32_t* tail, const int32
   }
 }
 
-int pbat_batch_kernel_source(int n_graphs, const pbat_graph* graphs, int n_pvec,
-                             const pbat_options* opt, char* buf, size_t cap) {
+static int batch_source(int n_graphs, const pbat_graph* graphs, int n_pvec, const double* p,
+                        bool grad, const pbat_options* opt, char* buf, size_t cap) {
   try {
     pbat::clear_error();
     if (n_graphs < 1 || !graphs || n_pvec < 1 || n_pvec > 64)
       return pbat::fail(PBAT_EINVAL, "bad batch");
+    std::vector<std::string> elig;
+    size_t poff = 0;
     for (int i = 0; i < n_graphs; ++i) {
       pbat::GraphIn g{graphs[i].n_nodes, graphs[i].n_arcs, graphs[i].tail, graphs[i].head,
                       graphs[i].directed, graphs[i].source, graphs[i].sink};
       int rc = pbat::validate_graph(g);
       if (rc) return rc;
+      if (grad) {
+        // walk arcs of the gradient module: p in [2^-20, 1 - 2^-20] under
+        // every p-vector (every arc when p is NULL)
+        elig.emplace_back(g.m, '1');
+        if (p)
+          for (int k = 0; k < n_pvec; ++k)
+            for (int a = 0; a < g.m; ++a) {
+              const double x = p[poff + (size_t)k * g.m + a];
+              if (!(x >= 0x1p-20 && x <= 1.0 - 0x1p-20)) elig.back()[a] = '0';
+            }
+        poff += (size_t)n_pvec * g.m;
+      }
     }
     pbat_options o;
     pbat_options_init(&o);
     if (opt) o = *opt;
     std::string src;
-    int rc = pbat::bsb_source_for(n_graphs, graphs, n_pvec, o, src);
+    int rc = pbat::bsb_source_for(n_graphs, graphs, n_pvec, o, grad ? &elig : nullptr, src);
     if (rc) return rc;
     if (buf && cap) {
       const size_t n = std::min(cap - 1, src.size());
@@ -1091,6 +1106,16 @@ int pbat_batch_kernel_source(int n_graphs, const pbat_graph* graphs, int n_pvec,
   } catch (...) {
     return pbat::fail(PBAT_ENOMEM, "host exception");
   }
+}
+
+int pbat_batch_kernel_source(int n_graphs, const pbat_graph* graphs, int n_pvec,
+                             const pbat_options* opt, char* buf, size_t cap) {
+  return batch_source(n_graphs, graphs, n_pvec, nullptr, false, opt, buf, cap);
+}
+
+int pbat_batch_grad_kernel_source(int n_graphs, const pbat_graph* graphs, int n_pvec,
+                                  const double* p, const pbat_options* opt, char* buf, size_t cap) {
+  return batch_source(n_graphs, graphs, n_pvec, p, true, opt, buf, cap);
 }
 
 struct pbat_plan_s {

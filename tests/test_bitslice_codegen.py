@@ -356,3 +356,18 @@ def test_prune_aware_plan_resolves_the_whole_directed_network(pb):
     grid = synth.workload_grid_3x6()
     pre, _ = _prefix_arcs(pb.kernel_source(grid, pb.options(walk_bits=5, prune=2)))
     assert _walked_items_exact(grid, pre) == (1 << len(pre)) - _resolved(grid, pre, range(1 << len(pre)))
+
+
+def test_batched_gradient_module_compiles_with_nvrtc(pb):
+    """The batched gradient module (bs_batch_grad): every network's
+    connectivity program and the kernel body, with walk arcs restricted to
+    those whose p is inside [2^-20, 1 - 2^-20] under every p-vector."""
+    nets, pvecs = synth.workload_batched(6, 3)
+    src = pb.batch_grad_kernel_source(nets, pvecs)
+    assert "bs_batch_grad(" in src and "bsb_finish_grad(" in src
+    _nvrtc_compile(src)
+    # an arc at p = 0 in one p-vector cannot be a walk arc of its network
+    pv = [[list(v) for v in pvs] for pvs in pvecs]
+    pv[0][1][0] = 0.0
+    src0 = pb.batch_grad_kernel_source(nets, pv)
+    _nvrtc_compile(src0)

@@ -201,3 +201,28 @@ def test_small_random_full_space_at_default(pb):
     _check(pb.reliability_net(net, grad=True), ref.R, ref.Nk, ref.T1, ref.T0, "default")
     f = oracle.factor(net)
     assert f.Nk == ref.Nk
+
+
+def test_shard_blocks_sum_to_the_whole_at_bench_shape(pb, forty):
+    """The sharded mode's blocks of equal divisions (four ranks, run here one
+    after another on one GPU) at the benchmark's fused shape: their counts
+    add up exactly to the whole, and R and dR/dp to the factoring values."""
+    from paper_2209_09711_gb300 import shard
+    net, R, Nk, T1, T0 = forty
+    name = "random-undirected-n24-m40"
+    world = 4
+    parts = []
+    for rank in range(world):
+        bits, lo, hi = shard.shard_range(net.m, world, rank)
+        parts.append(_bench_plan(pb, net, name, "fused", range_bits=bits, range_lo=lo, range_hi=hi))
+    fv = sum(shard.pack(q.R, q.Nk, list(q.grad))[0] for q in parts)
+    nv = sum(shard.pack(q.R, q.Nk, list(q.grad))[1] for q in parts)
+    Rs, Nks, gs = shard.unpack(fv, nv, True)
+    assert Nks == Nk
+    assert abs(Rs - R) <= 1e-12 * R
+    for i in range(net.m):
+        g = T1[i] - T0[i]
+        assert abs(gs[i] - g) <= 4 * _grad_tol(g, T1[i], T0[i], R), (i, gs[i], g)
+    # the library's own sharded driver on one rank (identity exchange)
+    r1 = shard.reliability_sharded(net, shard.gpu_compute, 1, 0, lambda v: v, grad=True)
+    assert r1[1] == Nk and abs(r1[0] - R) <= 1e-12 * R

@@ -429,3 +429,58 @@ def test_injected_host_faults_then_clean_call(pb, site, code, monkeypatch):
     monkeypatch.delenv("PBAT_FAULT")
     check(run(pb, net, grad=True, algo=pb.ALGO_BITSLICE), ref, True, f"after {site}")
     check(run(pb, net), ref, False, f"after {site}, default")
+
+
+# ---------------------------------------------------------------------------
+# batched gradient (one launch of the gradient module)
+# ---------------------------------------------------------------------------
+
+def test_batched_gradient_against_oracle_odd_many_pvectors(pb):
+    """dR/dp of several networks x 7 p-vectors from one launch, against the
+    oracle's T1 - T0: directed and undirected networks, networks too small
+    for five thread arcs, and a p-vector with arcs at exactly 0 and 1 (which
+    then cannot be walk arcs)."""
+    nets, pvecs = [], []
+    for i in range(6):
+        rng = synth.SplitMix64(17100 + i)
+        m = 6 + rng.below(12)
+        nets.append(synth.random_small(17200 + i, n=4 + rng.below(6), m=m, directed=bool(i & 1)))
+        pv = [synth.uniform_p(rng, m, 0.05, 0.95) for _ in range(7)]
+        if i == 2:
+            pv[3][0], pv[3][m - 1] = 0.0, 1.0
+        pvecs.append(pv)
+    R, Nk, G = pb.reliability_batched(nets, pvecs, grad=True)
+    for g, net in enumerate(nets):
+        for k in range(7):
+            ref = oracle.enumerate_states(net, p=pvecs[g][k], grad=True)
+            assert Nk[g] == ref.Nk, g
+            assert abs(R[g][k] - ref.R) <= R_TOL * ref.R + 1e-300, (g, k)
+            gstar = ref.grad_t1t0
+            for i in range(net.m):
+                assert abs(G[g][k][i] - gstar[i]) <= _grad_tol(gstar[i], ref.T1[i], ref.T0[i], ref.R), \
+                    (g, k, i, G[g][k][i], gstar[i])
+    # the same batch without the gradient gives the same R and N_k
+    R2, Nk2, _ = pb.reliability_batched(nets, pvecs)
+    assert Nk2 == Nk and np.max(np.abs(R2 - R) / R) <= 1e-13
+
+
+def test_batched_workload_gradient_one_launch(pb):
+    """The 64-network x 16-p-vector workload with the gradient: one
+    persistent launch (timed by the library), R and N_k identical to the
+    R-only module, and dR/dp of sampled networks against the factoring
+    method's T1 - T0."""
+    nets, pvecs = synth.workload_batched()
+    o = pb.options()
+    R, Nk, G = pb.reliability_batched(nets, pvecs, grad=True, opts=o)
+    assert o.stats[5] == 1 and o.stats[4] > 0
+    R0, Nk0, _ = pb.reliability_batched(nets, pvecs)
+    assert Nk == Nk0 and np.max(np.abs(R - R0) / R0) <= 1e-13
+    for g in (0, 9, 31, 47, 63):
+        net = nets[g]
+        for k in (0, 5, 15):
+            T1, T0 = oracle.factor_t1t0(net, pvecs[g][k])
+            Rk = oracle.factor(net, pvecs[g][k]).R
+            for i in range(net.m):
+                t1, t0 = sum(T1[i]), sum(T0[i])
+                gs = t1 - t0
+                assert abs(G[g][k][i] - gs) <= _grad_tol(gs, t1, t0, Rk), (g, k, i, G[g][k][i], gs)
