@@ -79,6 +79,15 @@ SHAPES = {
 # kernel whose source has changed since has no entry, and its roofline
 # fraction is reported as null.
 COUNTS = {
+    # 24 nodes, 40 arcs: fused (L 10, 256 threads, prune 2, occupancy 2) and R-only (L 9, 128, 2, 0)
+    "357f266c9ed0a6cb": (15862482255 / 2**40, 167680, "profiles/bs_kernel_grad_undirected24x40.md"),
+    "d1fa767e4a7c1c6c": (6497359334 / 2**40, 67584, "profiles/bs_kernel_undirected24x40.md"),
+    # directed, 20 nodes, 34 arcs: fused (7, 192, 2, 0) and R-only (8, 192, 2, 0)
+    "af2a14dc32809044": (27929511 / 2**34, 110080, "profiles/bs_kernel_grad_directed20x34.md"),
+    "e13f7bf524725d17": (11980584 / 2**34, 64512, "profiles/bs_kernel_directed20x34.md"),
+    # 3x6 grid: fused (5, 128, 1, 0) and R-only (5, 64, 1, 0)
+    "c512006d5dd496df": (17711335 / 2**27, 96256, "profiles/bs_kernel_grad_grid3x6.md"),
+    "89fe3f746591f645": (8524601 / 2**27, 44288, "profiles/bs_kernel_grid3x6.md"),
 }
 
 SM_COUNT = 152
@@ -604,12 +613,14 @@ def run_probe(a):
     build.build()
     import paper_2209_09711_gb300 as pb
     net = WORKLOADS[a.workload]() if a.workload in WORKLOADS else None
-    if a.probe == "batched":
+    if a.probe in ("batched", "batched-fused"):
         nets, pvecs = synth.workload_batched()
         t0 = time.perf_counter()
-        R, Nk, _ = pb.reliability_batched(nets, pvecs, opts=pb.options(algo=pb.ALGO_BITSLICE))
+        o = pb.options(algo=pb.ALGO_BITSLICE)
+        R, Nk, _ = pb.reliability_batched(nets, pvecs, grad=a.probe == "batched-fused", opts=o)
         print(json.dumps({"probe": a.probe, "networks": len(nets), "p_vectors": len(pvecs[0]),
-                          "R00": R[0][0], "first_call_s": time.perf_counter() - t0}))
+                          "states": sum(2**n.m for n in nets), "R00": R[0][0],
+                          "kernel_ms": o.stats[4] / 1e6, "first_call_s": time.perf_counter() - t0}))
         return 0
     algo = pb.ALGO_FRONTIER if a.probe.startswith("plain") else pb.ALGO_AUTO
     grad = a.probe.endswith("fused")
@@ -648,7 +659,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="time the headline workload only (no sub-records of the other workloads)")
-    ap.add_argument("--probe", choices=["fused", "r-only", "plain-r-only", "plain-fused", "batched"],
+    ap.add_argument("--probe", choices=["fused", "r-only", "plain-r-only", "plain-fused", "batched",
+                                        "batched-fused"],
                     help="run one untimed launch of that kernel (for profiler captures)")
     ap.add_argument("--walk-bits", type=int, default=None,
                     help="pin the walk length L (default: the tuned shape of the workload)")

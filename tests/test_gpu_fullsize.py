@@ -49,13 +49,23 @@ def _grad_tol(gstar, t1, t0, R):
     return 1e-12 * max(abs(gstar), 1e-4 * abs(R)) + 1e-300
 
 
-def _check(res, R, Nk, T1=None, T0=None, ctx=""):
+def _check(res, R, Nk, T=None, ctx=""):
+    """T: (G, T1, T0) -- the exact gradient (from the oracle's hi/lo sums,
+    not from T1 - T0 rounded to doubles) and the two sums for the condition
+    number."""
     assert res.Nk == Nk, ctx
     assert abs(res.R - R) <= 1e-12 * abs(R) + 1e-300, (ctx, res.R, R)
-    if T1 is not None and res.grad is not None:
+    if T is not None and res.grad is not None:
+        G, T1, T0 = T
         for i in range(len(Nk) - 1):
-            g = T1[i] - T0[i]
-            assert abs(res.grad[i] - g) <= _grad_tol(g, T1[i], T0[i], R), (ctx, i, res.grad[i], g)
+            assert abs(res.grad[i] - G[i]) <= _grad_tol(G[i], T1[i], T0[i], R), \
+                (ctx, i, res.grad[i], G[i])
+
+
+def _exact_grad(T1h, T0h):
+    """dR/dp_i = T1_i - T0_i from (hi, lo) pairs, exactly, then rounded."""
+    return [float(Fraction(a[0]) + Fraction(a[1]) - Fraction(b[0]) - Fraction(b[1]))
+            for a, b in zip(T1h, T0h)]
 
 
 def _bench_plan(pb, net, name, kind, **extra):
@@ -78,33 +88,34 @@ def _golden_grid():
                 rows.setdefault(w[0], []).append(w[1:])
 
     def val(hi, lo):
-        return float(Fraction(float.fromhex(hi)) + Fraction(float.fromhex(lo)))
+        return Fraction(float.fromhex(hi)) + Fraction(float.fromhex(lo))
 
-    R = val(*rows["R"][0])
+    R = float(val(*rows["R"][0]))
     Nk = [int(v) for v in rows["NK"][0]]
     m = len(Nk) - 1
-    T1, T0 = [0.0] * m, [0.0] * m
+    T1, T0 = [Fraction(0)] * m, [Fraction(0)] * m
     for i, hi, lo in rows["T1"]:
         T1[int(i)] = val(hi, lo)
     for i, hi, lo in rows["T0"]:
         T0[int(i)] = val(hi, lo)
-    return R, Nk, T1, T0
+    G = [float(a - b) for a, b in zip(T1, T0)]
+    return R, Nk, (G, [float(x) for x in T1], [float(x) for x in T0])
 
 
 def test_grid_3x6_full_space_at_bench_shapes(pb):
     net = synth.workload_grid_3x6()
-    R, Nk, T1, T0 = _golden_grid()
-    _check(_bench_plan(pb, net, "grid-3x6", "fused"), R, Nk, T1, T0, "bench fused launch")
+    R, Nk, T = _golden_grid()
+    _check(_bench_plan(pb, net, "grid-3x6", "fused"), R, Nk, T, "bench fused launch")
     _check(_bench_plan(pb, net, "grid-3x6", "r_only"), R, Nk, ctx="bench R launch")
     # the public call with default options (autotuned shape)
-    _check(pb.reliability_net(net, grad=True), R, Nk, T1, T0, "autotuned fused")
+    _check(pb.reliability_net(net, grad=True), R, Nk, T, "autotuned fused")
     _check(pb.reliability_net(net), R, Nk, ctx="autotuned R")
     # both planning modes and the plain GPU BAT
     for prune in (0, 2):
         _check(pb.reliability_net(net, grad=True, opts=pb.options(prune=prune, walk_bits=5)), R, Nk,
-               T1, T0, f"prune {prune}")
-    _check(pb.reliability_net(net, grad=True, opts=pb.options(algo=pb.ALGO_FRONTIER)), R, Nk, T1,
-           T0, "frontier kernel")
+               T, f"prune {prune}")
+    _check(pb.reliability_net(net, grad=True, opts=pb.options(algo=pb.ALGO_FRONTIER)), R, Nk, T,
+           "frontier kernel")
 
 
 @pytest.fixture(scope="module")
@@ -112,33 +123,33 @@ def forty():
     net = synth.workload_random_24_40()
     f = oracle.factor(net)
     T1h, T0h = oracle.factor_t1t0(net)
-    return net, f.R, f.Nk, [sum(x) for x in T1h], [sum(x) for x in T0h]
+    return net, f.R, f.Nk, (_exact_grad(T1h, T0h), [sum(x) for x in T1h], [sum(x) for x in T0h])
 
 
 def test_forty_arc_full_space_at_bench_shapes(pb, forty):
     """The benchmark's headline workload, 2^40 states, every output."""
-    net, R, Nk, T1, T0 = forty
+    net, R, Nk, T = forty
     name = "random-undirected-n24-m40"
-    _check(_bench_plan(pb, net, name, "fused"), R, Nk, T1, T0, "bench fused launch")
+    _check(_bench_plan(pb, net, name, "fused"), R, Nk, T, "bench fused launch")
     _check(_bench_plan(pb, net, name, "r_only"), R, Nk, ctx="bench R launch")
 
 
 def test_forty_arc_full_space_other_plans(pb, forty):
     """The source/sink-near planner (prune 1) and the public call with its
     autotuned choice."""
-    net, R, Nk, T1, T0 = forty
+    net, R, Nk, T = forty
     _check(pb.reliability_net(net, grad=True, opts=pb.options(prune=1, walk_bits=10,
                                                                 block_threads=160)),
-           R, Nk, T1, T0, "prune 1 fused")
+           R, Nk, T, "prune 1 fused")
     _check(pb.reliability_net(net, opts=pb.options(prune=1, walk_bits=10, block_threads=224)), R, Nk,
            ctx="prune 1 R")
-    _check(pb.reliability_net(net, grad=True), R, Nk, T1, T0, "autotuned fused")
+    _check(pb.reliability_net(net, grad=True), R, Nk, T, "autotuned fused")
 
 
 def test_forty_arc_half_probability_and_partition(pb, forty):
     """At p = 1/2, R is the count of connected states over 2^40, exactly;
     partial results of four range blocks add up to the whole."""
-    net, R, Nk, _, _ = forty
+    net, R, Nk, _ = forty
     m = net.m
     half = pb.reliability_net(net, p=[0.5] * m, opts=bench.shape_opts(pb, "random-undirected-n24-m40",
                                                                        "r_only"))
@@ -182,7 +193,7 @@ def test_directed_34_at_bench_shapes(pb):
                 if prune == 2 else pb.options(range_bits=bits, range_lo=d, range_hi=d + 1)
             r = pb.reliability_net(net, grad=True, opts=o)
             ref = oracle.enumerate_states(net, prefix_bits=bits, prefix_lo=d, prefix_hi=d + 1, grad=True)
-            _check(r, ref.R, ref.Nk, ref.T1, ref.T0, f"division {d} prune {prune}")
+            _check(r, ref.R, ref.Nk, (ref.grad_t1t0, ref.T1, ref.T0), f"division {d} prune {prune}")
     # p = 1/2 ties R to the counts
     half = pb.reliability_net(net, p=[0.5] * m, opts=bench.shape_opts(pb, name, "r_only"))
     assert half.Nk == fused.Nk and half.R == sum(fused.Nk) / 2.0**m
@@ -198,7 +209,8 @@ def test_small_random_full_space_at_default(pb):
     """The 8-node, 16-arc workload (2^16 states), whole space."""
     net = synth.workload_small_random()
     ref = oracle.enumerate_states(net, grad=True)
-    _check(pb.reliability_net(net, grad=True), ref.R, ref.Nk, ref.T1, ref.T0, "default")
+    _check(pb.reliability_net(net, grad=True), ref.R, ref.Nk, (ref.grad_t1t0, ref.T1, ref.T0),
+           "default")
     f = oracle.factor(net)
     assert f.Nk == ref.Nk
 
@@ -208,7 +220,7 @@ def test_shard_blocks_sum_to_the_whole_at_bench_shape(pb, forty):
     after another on one GPU) at the benchmark's fused shape: their counts
     add up exactly to the whole, and R and dR/dp to the factoring values."""
     from paper_2209_09711_gb300 import shard
-    net, R, Nk, T1, T0 = forty
+    net, R, Nk, (G, T1, T0) = forty
     name = "random-undirected-n24-m40"
     world = 4
     parts = []
@@ -221,8 +233,7 @@ def test_shard_blocks_sum_to_the_whole_at_bench_shape(pb, forty):
     assert Nks == Nk
     assert abs(Rs - R) <= 1e-12 * R
     for i in range(net.m):
-        g = T1[i] - T0[i]
-        assert abs(gs[i] - g) <= 4 * _grad_tol(g, T1[i], T0[i], R), (i, gs[i], g)
+        assert abs(gs[i] - G[i]) <= 4 * _grad_tol(G[i], T1[i], T0[i], R), (i, gs[i], G[i])
     # the library's own sharded driver on one rank (identity exchange)
     r1 = shard.reliability_sharded(net, shard.gpu_compute, 1, 0, lambda v: v, grad=True)
     assert r1[1] == Nk and abs(r1[0] - R) <= 1e-12 * R
