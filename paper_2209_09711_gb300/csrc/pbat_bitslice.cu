@@ -998,26 +998,40 @@ int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o
 }
 
 // The batch's walk length (split depth: each network's items are its
-// prefixes of d = m - 10 - L arcs): every candidate L in {3, 4, 5} builds its
-// module and runs the batch once; the fastest launch wins.  -1 keeps the
-// planner's default.
-static int bsb_tune_walk(int G, const pbat_graph* graphs, int K, const double* p,
-                         const pbat_options& o, cudaStream_t st, const DeviceInfo& dev) {
+// prefixes of d = m - 10 - L arcs) and, with the prune on, its planning mode
+// (source/sink-near or prune-aware prefix arcs): every candidate builds its
+// module and runs the batch once; the fastest launch wins.  The gradient
+// module (elig given) is tuned the same way.  Returns false when no
+// candidate ran (the planner's defaults are kept).
+static bool bsb_tune(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
+                     cudaStream_t st, const DeviceInfo& dev, const std::vector<std::string>* elig,
+                     int* best_L, int* best_prune) {
   double best_ms = 1e300;
-  int best = -1;
+  bool found = false;
   cudaEvent_t a = nullptr, b = nullptr;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
     if (a) cudaEventDestroy(a);
     cudaGetLastError();
-    return -1;
+    return false;
   }
-  {
-    // the candidates' modules compile at once on host threads
-    std::vector<std::string> srcs;
+  std::vector<pbat_options> cands;
+  for (int mode : (o.prune == 1 ? std::vector<int>{1, 2} : std::vector<int>{o.prune}))
     for (int L = 3; L <= kBsbMaxWalk; ++L) {
       pbat_options t = o;
       t.walk_bits = L;
+      t.prune = mode;
+      t.time_budget_s = 0;
+      cands.push_back(t);
+    }
+  {
+    // the candidates' modules compile at once on host threads
+    std::vector<std::string> srcs;
+    for (const pbat_options& t : cands) {
       BsBatch T;
+      if (elig) {
+        T.grad = true;
+        T.elig = *elig;
+      }
       std::vector<unsigned long long> items;
       std::string src;
       if (bsb_source(T, G, graphs, K, t, items, src) == PBAT_OK) srcs.push_back(std::move(src));
@@ -1025,11 +1039,12 @@ static int bsb_tune_walk(int G, const pbat_graph* graphs, int K, const double* p
     }
     jit_precompile(srcs, dev.cc_major * 10 + dev.cc_minor);
   }
-  for (int L = 3; L <= kBsbMaxWalk; ++L) {
-    pbat_options t = o;
-    t.walk_bits = L;
-    t.time_budget_s = 0;
+  for (const pbat_options& t : cands) {
     BsBatch T;
+    if (elig) {
+      T.grad = true;
+      T.elig = *elig;
+    }
     if (bsb_build(T, G, graphs, K, t, dev) != PBAT_OK) {
       if (T.scr) scratch_release(T.scr);
       clear_error();
@@ -1043,7 +1058,9 @@ static int bsb_tune_walk(int G, const pbat_graph* graphs, int K, const double* p
     float ms = 0.f;
     if (ok && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
       best_ms = ms;
-      best = L;
+      *best_L = t.walk_bits;
+      *best_prune = t.prune;
+      found = true;
     }
     if (!ok) {
       cudaGetLastError();
@@ -1053,12 +1070,9 @@ static int bsb_tune_walk(int G, const pbat_graph* graphs, int K, const double* p
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  return best;
+  return found;
 }
 
-// R (and N_k) of a batch with the bit-sliced batched kernel; returns
-// PBAT_ENOTSUP when the batch is outside its limits (the caller then uses the
-// frontier kernel).
 // R (and N_k) of a batch with the bit-sliced batched kernel; with `elig`
 // (one string of '0'/'1' walk-arc eligibility per network) the gradient
 // module also returns dR/dp in dRdp_out (the layout of p), and lists in
@@ -1080,10 +1094,13 @@ int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, cons
   }
   if (!E) {
     pbat_options ob = o;
-    // the gradient module walks the longest items (L = 5) unless told
-    // otherwise: its per-item reductions are the larger share
-    if (!elig && o.autotune && o.walk_bits < 0)
-      ob.walk_bits = bsb_tune_walk(G, graphs, K, p, o, st, dev);
+    if (o.autotune && o.walk_bits < 0) {
+      int L = -1, mode = o.prune;
+      if (bsb_tune(G, graphs, K, p, o, st, dev, elig, &L, &mode)) {
+        ob.walk_bits = L;
+        ob.prune = mode;
+      }
+    }
     std::unique_ptr<BsBatch> ne(new BsBatch());
     ne->key = key;
     ne->busy = true;

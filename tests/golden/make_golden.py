@@ -27,7 +27,8 @@ if ROOT not in sys.path:
 
 import synth  # noqa: E402
 
-WORKLOADS = {"grid-3x6": synth.workload_grid_3x6}
+WORKLOADS = {"grid-3x6": synth.workload_grid_3x6,
+             "random-directed-n20-m34": synth.workload_directed_20_34}
 DIV_BITS = 10
 
 
@@ -53,7 +54,8 @@ def make(name: str) -> str:
     net = WORKLOADS[name]()
     m = net.m
     t0 = time.time()
-    with mp.get_context("spawn").Pool(os.cpu_count() or 1) as pool:
+    procs = int(os.environ.get("GOLDEN_PROCS", os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(procs) as pool:
         parts = pool.map(_division, [(name, d) for d in range(1 << DIV_BITS)], chunksize=4)
     R = _exact([p[1] for p in parts])
     Nk = [sum(p[2][k] for p in parts) for k in range(m + 1)]
