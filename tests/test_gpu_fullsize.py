@@ -7,9 +7,9 @@ benchmark times, against the oracle's exact values.
   oracle's factoring method (exact sums by pivotal decomposition, pinned
   against the brute force in tests/test_oracle_factoring.py), computed here.
 - Directed 34-arc network (2^34 states; the factoring method covers
-  undirected networks only): sampled equal divisions against the brute force
-  under the benchmark's planning mode, and invariants of the whole run at the
-  benchmark's shapes.
+  undirected networks only): the brute-force oracle's stored values
+  (tests/golden/random-directed-n20-m34_full.txt), sampled equal divisions
+  in both planning modes, and invariants of the whole run.
 
 N_k must be bit-exact, R within 1e-12 relative, dR/dp within the reading of
 the 1e-12 target for gradients: 1e-12 * |g*| where the oracle's T1/T0
@@ -79,9 +79,11 @@ def _bench_plan(pb, net, name, kind, **extra):
     return r
 
 
-def _golden_grid():
+def _golden(name):
+    """R, N_k and (exact dR/dp, T1, T0) stored for a workload by
+    tests/golden/make_golden.py (the brute-force oracle over every state)."""
     rows = {}
-    with open(os.path.join(GOLDEN, "grid-3x6_full.txt")) as f:
+    with open(os.path.join(GOLDEN, f"{name}_full.txt")) as f:
         for line in f:
             if line.strip() and not line.startswith("#"):
                 w = line.split()
@@ -104,7 +106,7 @@ def _golden_grid():
 
 def test_grid_3x6_full_space_at_bench_shapes(pb):
     net = synth.workload_grid_3x6()
-    R, Nk, T = _golden_grid()
+    R, Nk, T = _golden("grid-3x6")
     _check(_bench_plan(pb, net, "grid-3x6", "fused"), R, Nk, T, "bench fused launch")
     _check(_bench_plan(pb, net, "grid-3x6", "r_only"), R, Nk, ctx="bench R launch")
     # the public call with default options (autotuned shape)
@@ -172,6 +174,21 @@ def test_batched_workload_full_against_factoring(pb):
         for k in range(len(pvecs[g])):
             Rk = f0.R if k == 0 else oracle.factor(net, pvecs[g][k]).R
             assert abs(Rb[g][k] - Rk) <= 1e-12 * Rk, (g, k, Rb[g][k], Rk)
+
+
+def test_directed_34_full_space_at_bench_shapes(pb):
+    """The directed workload, all 2^34 states, against the brute-force
+    oracle's stored values: the benchmark's fused and R launches, the other
+    planning mode and the autotuned call."""
+    net = synth.workload_directed_20_34()
+    name = "random-directed-n20-m34"
+    R, Nk, T = _golden(name)
+    _check(_bench_plan(pb, net, name, "fused"), R, Nk, T, "bench fused launch")
+    _check(_bench_plan(pb, net, name, "r_only"), R, Nk, ctx="bench R launch")
+    _check(pb.reliability_net(net, grad=True, opts=pb.options(prune=1, walk_bits=10,
+                                                                block_threads=256)),
+           R, Nk, T, "prune 1 fused")
+    _check(pb.reliability_net(net, grad=True), R, Nk, T, "autotuned fused")
 
 
 def test_directed_34_at_bench_shapes(pb):
