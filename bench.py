@@ -65,7 +65,7 @@ CONFIG_ORDER = ["random-undirected-n8-m16", "grid-3x6", "random-directed-n20-m34
 # (--autotune lets the autotuner choose instead).  prune 2 = prune-aware
 # prefix arcs.
 SHAPES = {
-    "random-undirected-n24-m40": {"fused": (10, 256, 2, 2), "r_only": (9, 128, 2, 0)},
+    "random-undirected-n24-m40": {"fused": (9, 256, 2, 2), "r_only": (9, 128, 2, 0)},
     "random-directed-n20-m34": {"fused": (7, 192, 2, 0), "r_only": (8, 192, 2, 0)},
     "grid-3x6": {"fused": (5, 128, 1, 0), "r_only": (5, 64, 1, 0)},
 }

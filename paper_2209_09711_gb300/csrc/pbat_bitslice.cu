@@ -42,6 +42,8 @@ struct BsParamsHost {
 struct JitEntry {
   cudaLibrary_t lib = nullptr;
   cudaKernel_t kernel = nullptr;
+  // the two launches of a two-launch run (single-network kernels only)
+  cudaKernel_t kernel_p1 = nullptr, kernel_p2 = nullptr;
   int regs = 0;
 };
 static std::mutex g_jit_mu;
@@ -151,6 +153,12 @@ static int jit_compile(const std::string& src, const DeviceInfo& dev, const char
   if (ce != cudaSuccess) return fail(PBAT_ECUDA, "cudaLibraryLoadData: %s", cudaGetErrorString(ce));
   ce = cudaLibraryGetKernel(&e.kernel, e.lib, kname);
   if (ce != cudaSuccess) return fail(PBAT_ECUDA, "cudaLibraryGetKernel: %s", cudaGetErrorString(ce));
+  // optional per-phase entry points: absent from the batched modules
+  if (cudaLibraryGetKernel(&e.kernel_p1, e.lib, (std::string(kname) + "_p1").c_str()) != cudaSuccess ||
+      cudaLibraryGetKernel(&e.kernel_p2, e.lib, (std::string(kname) + "_p2").c_str()) != cudaSuccess) {
+    cudaGetLastError();
+    e.kernel_p1 = e.kernel_p2 = nullptr;
+  }
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, (const void*)e.kernel) == cudaSuccess) e.regs = fa.numRegs;
   else cudaGetLastError();
@@ -181,7 +189,8 @@ struct BsLaunch {
   JitEntry jit;
   int nthr = 128;
   size_t smem = 0;
-  int per_sm = 1;
+  int per_sm = 1;                     // resident blocks per SM: one-launch kernel
+  int per_sm1 = 1, per_sm2 = 1;       // the two launches of a two-launch run
 };
 
 // out[v] = product over x < n of (bit x of v ? p : 1 - p) of arc arcs[x], for
@@ -261,7 +270,8 @@ struct BsCached {
   BsPlan plan;
   JitEntry jit;
   size_t smem = 0;   // shared memory the kernel attribute was set for
-  int per_sm = 0;    // resident blocks per SM at that size
+  int per_sm = 0;    // resident blocks per SM at that size (one-launch kernel)
+  int per_sm1 = 0, per_sm2 = 0;   // the two launches of a two-launch run
 };
 static std::mutex g_bsplan_mu;
 static std::map<std::string, BsCached> g_bsplan;
@@ -457,42 +467,55 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
     auto it = g_bsplan.find(key);
     if (it != g_bsplan.end() && it->second.per_sm > 0 && it->second.smem == bl.smem) {
       bl.per_sm = it->second.per_sm;
+      bl.per_sm1 = it->second.per_sm1;
+      bl.per_sm2 = it->second.per_sm2;
       return PBAT_OK;
     }
   }
-  cudaError_t e = cudaFuncSetAttribute((const void*)bl.jit.kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bl.smem);
-  if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)bl.jit.kernel, bl.nthr,
-                                                    bl.smem);
-  if (e != cudaSuccess || per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
-  bl.per_sm = per_sm;
+  // shared-memory attribute and resident blocks per SM of each entry point
+  auto setup = [&](cudaKernel_t k, int* per_sm) -> int {
+    *per_sm = 1;
+    if (!k) return PBAT_OK;
+    cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bl.smem);
+    if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, (const void*)k, bl.nthr, bl.smem);
+    if (e != cudaSuccess || *per_sm < 1) {
+      cudaGetLastError();
+      *per_sm = 1;
+    }
+    return PBAT_OK;
+  };
+  if ((rc = setup(bl.jit.kernel, &bl.per_sm)) || (rc = setup(bl.jit.kernel_p1, &bl.per_sm1)) ||
+      (rc = setup(bl.jit.kernel_p2, &bl.per_sm2)))
+    return rc;
   std::lock_guard<std::mutex> lk(g_bsplan_mu);
   auto it = g_bsplan.find(key);
   if (it != g_bsplan.end()) {
     it->second.smem = bl.smem;
-    it->second.per_sm = per_sm;
+    it->second.per_sm = bl.per_sm;
+    it->second.per_sm1 = bl.per_sm1;
+    it->second.per_sm2 = bl.per_sm2;
   }
   return PBAT_OK;
 }
 
 // Launch with the device copies of the tables (see bs_tables for the order).
+// phase 0: the one-launch kernel; 1, 2: the two launches of a two-launch run.
 cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsigned long long* d_lane,
                       const unsigned long long* d_thr, const unsigned long long* d_wmid,
-                      const void* d_ptab, const void* d_ptab_ex, const DevWork& W) {
+                      const void* d_ptab, const void* d_ptab_ex, const DevWork& W, int phase) {
   const BsParamsHost& P = bl.P;
+  const cudaKernel_t k = phase == 1 ? bl.jit.kernel_p1 : phase == 2 ? bl.jit.kernel_p2 : bl.jit.kernel;
+  if (!k) return cudaErrorInvalidDeviceFunction;
   if (bl.plan.grad) {
     const BsGradParamsHost& Q = bl.Q;
     void* args[] = {(void*)&P, (void*)&Q, (void*)&d_lane, (void*)&d_thr, (void*)&d_wmid,
                     (void*)&d_ptab, (void*)&d_ptab_ex, (void*)&W};
-    return cudaLaunchKernel((const void*)bl.jit.kernel, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
+    return cudaLaunchKernel((const void*)k, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
   }
   void* args[] = {(void*)&P, (void*)&d_lane, (void*)&d_wmid, (void*)&d_ptab, (void*)&W};
-  return cudaLaunchKernel((const void*)bl.jit.kernel, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
+  return cudaLaunchKernel((const void*)k, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
 }
 
 // accessors used by the engine
@@ -501,7 +524,9 @@ unsigned long long bs_items(const BsLaunch& bl) { return bl.P.n_tasks; }
 unsigned long long bs_item_states(const BsLaunch& bl) {
   return 1ull << (bl.plan.ell + bl.plan.tb + bl.plan.L);
 }
-int bs_per_sm(const BsLaunch& bl) { return bl.per_sm; }
+int bs_per_sm(const BsLaunch& bl, int phase) {
+  return phase == 1 ? bl.per_sm1 : phase == 2 ? bl.per_sm2 : bl.per_sm;
+}
 int bs_nthr(const BsLaunch& bl) { return bl.nthr; }
 const std::vector<unsigned long long>& bs_lane_tab(const BsLaunch& bl) { return bl.lane_tab; }
 const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl) {

@@ -178,7 +178,33 @@ struct BsWork {
   dd* part_acc; u64* part_n; dd* out_acc; u64* out_n;
   facc* wacc;       // fused kernel: per warp, R and the two sums of every arc
   u64* out_limbs;   // [n_acc][8]: 256-bit fixed point at scale 2^250, 32 bits per limb
+  u64* list;        // two-launch runs: items deferred to the walking launch
+  u64 list_cap;     // 0: one-launch run
+  u64* list_n;
+  u64* counter2;    // ticket of the walking launch
 };
+
+// Work items of a launch.  One-launch runs (phase 0) take items by the
+// atomic ticket over [0, n_tasks).  Two-launch runs: the first (phase 1)
+// visits every item with a fixed warp stride -- no ticket, the items it
+// keeps are short -- resolves what the prune can and defers the items left
+// to walk; the second (phase 2) takes the deferred items by a ticket over
+// the list.  ~0: no item left.
+__device__ __forceinline__ u64 bs_list_task(const BsWork& W) {
+  const u64 i = atomicAdd(W.counter2, 1ull);
+  return i < *W.list_n ? W.list[i] : ~0ull;
+}
+
+// Phase 1: a warp collects its deferred items one per lane (entry j in lane
+// j) and appends them to the list 32 at a time, with one atomic per batch.
+// The list holds every item (list_cap = n_tasks), so it cannot overflow.
+__device__ __forceinline__ void bs_flush_deferred(const BsWork& W, u64 pend, int npend, int lane) {
+  if (!npend) return;
+  u64 base = 0;
+  if (lane == 0) base = atomicAdd(W.list_n, (u64)npend);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (lane < npend) W.list[base + lane] = pend;
+}
 
 __device__ __forceinline__ u64 bs_timer() {
   u64 t; asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t)); return t;
@@ -297,9 +323,15 @@ __device__ __forceinline__ void bs_write_out(const BsWork& W, const facc* s_acc,
 // ---------------------------------------------------------------------------
 // R + N_k
 // ---------------------------------------------------------------------------
-extern "C" __global__ void KERNEL_BOUNDS
-bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
-          const u64* __restrict__ wmid_tab, const mx* __restrict__ ptab, BsWork W) {
+#if !BS_GRAD
+// PHASE 0: a one-launch run; 1 and 2: the two launches of a two-launch run
+// (the first resolves what the prune can and defers the items left to walk,
+// the second walks them).  One entry point per phase, so that a one-launch
+// kernel carries none of the two-launch state in its registers.
+template <int PHASE>
+__device__ __forceinline__ void bs_kernel_body(const BsParams& P, const u64* __restrict__ lane_tab,
+                                               const u64* __restrict__ wmid_tab,
+                                               const mx* __restrict__ ptab, const BsWork& W) {
   extern __shared__ __align__(16) unsigned char smem[];
   ulonglong2* s_lt = (ulonglong2*)smem;                     // [4][256] {lane mass 2^62, packed counts}
   u64* s_wmid = (u64*)(s_lt + 4 * 256);                     // [2^L], scale 2^63
@@ -320,11 +352,21 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
   facc accR = facc{u128{0ull, 0ull}, 0, 0};   // this warp's R (the same in every lane)
   u32 a[BS_M];
   bs_init_arcs(a, lane);
+  constexpr int phase = PHASE;
+  const u64 n_warps = (u64)gridDim.x * (BS_NTHR / 32);
+  u64 stride_task = (u64)blockIdx.x * (BS_NTHR / 32) + warp;   // phase 1
+  u64 pend = 0;   // phase 1: this warp's deferred items, entry j in lane j
+  int npend = 0;
 
   for (;;) {
     u64 task = 0;
+    if constexpr (phase == 1) {
+      task = stride_task;
+      stride_task += n_warps;
+    }
     if (lane == 0) {
-      task = atomicAdd(W.counter, 1ull);
+      if constexpr (phase == 2) task = bs_list_task(W);
+      else if constexpr (phase == 0) task = atomicAdd(W.counter, 1ull);
       if (P.budget_ns && bs_timer() - t_start > P.budget_ns) { atomicOr(W.status, 1u); task = ~0ull; }
     }
     task = __shfl_sync(0xffffffffu, task, 0);
@@ -333,7 +375,7 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
 #pragma unroll
     for (int j = 0; j < BS_D; ++j) a[BS_TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
     const int pc_pre = __popcll((long long)prefix);
-    if (P.prune) {
+    if ((P.prune && phase == 0) || phase == 1) {   // two-launch runs always prune
       const int pr = bs_prune(a);
       if (pr == 1) { ++n_dead; continue; }
       if (pr == 2) {
@@ -343,6 +385,11 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
         facc_add(accR, mx_prod(w, u128{0ull, 1ull << 60}), w.e);
         continue;
       }
+    }
+    if constexpr (phase == 1) {   // left to walk: deferred to the second launch
+      if (lane == npend) pend = task;
+      if (++npend == 32) { bs_flush_deferred(W, pend, npend, lane); npend = 0; }
+      continue;
     }
     ++n_walk;
     u32 e[BS_NCORE > 0 ? BS_NCORE : 1];
@@ -391,6 +438,7 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
     const mx w = bs_prefix_mass(P, ptab, prefix);
     facc_add(accR, mx_prod(w, S), w.e);
   }
+  if constexpr (phase == 1) bs_flush_deferred(W, pend, npend, lane);
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
     s_acc[warp] = accR;
@@ -398,6 +446,13 @@ bs_kernel(const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab,
   __syncthreads();
   bs_write_out(W, s_acc, 1, 1, s_nbins);
 }
+
+#define KERNEL_R_ARGS const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab, \
+                  const u64* __restrict__ wmid_tab, const mx* __restrict__ ptab, const BsWork W
+extern "C" __global__ void KERNEL_BOUNDS bs_kernel(KERNEL_R_ARGS) { bs_kernel_body<0>(P, lane_tab, wmid_tab, ptab, W); }
+extern "C" __global__ void KERNEL_BOUNDS bs_kernel_p1(KERNEL_R_ARGS) { bs_kernel_body<1>(P, lane_tab, wmid_tab, ptab, W); }
+extern "C" __global__ void KERNEL_BOUNDS bs_kernel_p2(KERNEL_R_ARGS) { bs_kernel_body<2>(P, lane_tab, wmid_tab, ptab, W); }
+#endif
 
 #if BS_GRAD
 // ---------------------------------------------------------------------------
@@ -452,11 +507,11 @@ __device__ __forceinline__ mx bs_arc_factor(const BsParams& P, const mx* __restr
   return f;
 }
 
-extern "C" __global__ void KERNEL_BOUNDS
-bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGradParams Q,
-               const u64* __restrict__ lane_tab, const u64* __restrict__ thr_tab,
-               const u64* __restrict__ wmid128, const mx* __restrict__ ptab,
-               const mx* __restrict__ ptab_ex, BsWork W) {
+template <int PHASE>
+__device__ __forceinline__ void bs_kernel_grad_body(
+    const BsParams& P, const BsGradParams& Q, const u64* __restrict__ lane_tab,
+    const u64* __restrict__ thr_tab, const u64* __restrict__ wmid128, const mx* __restrict__ ptab,
+    const mx* __restrict__ ptab_ex, const BsWork& W) {
   extern __shared__ __align__(16) unsigned char smem[];
   ulonglong2* s_lt = (ulonglong2*)smem;                     // [4][256] {lane mass 2^62, packed counts}
   ulonglong2* s_wm = s_lt + 4 * 256;                        // [2^L] walk masses {lo, hi} (2^127)
@@ -494,11 +549,21 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
 #endif
   u32 a[BS_M];
   bs_init_arcs(a, lane);
+  constexpr int phase = PHASE;
+  const u64 n_warps = (u64)gridDim.x * (BS_NTHR / 32);
+  u64 stride_task = (u64)blockIdx.x * (BS_NTHR / 32) + warp;   // phase 1
+  u64 pend = 0;   // phase 1: this warp's deferred items, entry j in lane j
+  int npend = 0;
 
   for (;;) {
     u64 task = 0;
+    if constexpr (phase == 1) {
+      task = stride_task;
+      stride_task += n_warps;
+    }
     if (lane == 0) {
-      task = atomicAdd(W.counter, 1ull);
+      if constexpr (phase == 2) task = bs_list_task(W);
+      else if constexpr (phase == 0) task = atomicAdd(W.counter, 1ull);
       if (P.budget_ns && bs_timer() - t_start > P.budget_ns) { atomicOr(W.status, 1u); task = ~0ull; }
     }
     task = __shfl_sync(0xffffffffu, task, 0);
@@ -508,9 +573,16 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     for (int j = 0; j < BS_D; ++j) a[BS_TOP + j] = 0u - (u32)((prefix >> j) & 1ull);
     const int pc_pre = __popcll((long long)prefix);
     int pr = 0;
-    if (P.prune) {
+    if ((P.prune && phase == 0) || phase == 1) {   // two-launch runs always prune
       pr = bs_prune(a);
       if (pr == 1) { ++n_dead; continue; }
+    }
+    if constexpr (phase == 1) {
+      if (pr == 0) {   // left to walk: deferred to the second launch
+        if (lane == npend) pend = task;
+        if (++npend == 32) { bs_flush_deferred(W, pend, npend, lane); npend = 0; }
+        continue;
+      }
     }
 #if BS_ACC_REG
     // the prefix factors of an item that is not cut off, before its walk so
@@ -524,7 +596,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     // warp sums of the internal arc this lane owns (internal arcs are below
     // 32): the exact pair difference, or for a walk arc A and T - A
     u128 myX = u128{0ull, 0ull}, myY = u128{0ull, 0ull};
-    if (pr == 2) {
+    if (pr == 2 || phase == 1) {   // (the first of two launches walks nothing)
       ++n_full;
       for (int j = lane; j <= BS_TOP; j += 32) atomicAdd(&s_nbins[pc_pre + j], P.binom[j]);
       S = u128{0ull, 1ull << 60};   // the whole item: mass 1 at scale 2^124
@@ -684,6 +756,7 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
     }
     __syncwarp();
   }
+  if constexpr (phase == 1) bs_flush_deferred(W, pend, npend, lane);
   if (lane == 0) {
     atomicAdd(&W.stats[0], n_walk); atomicAdd(&W.stats[1], n_full); atomicAdd(&W.stats[2], n_dead);
   }
@@ -706,6 +779,15 @@ bs_kernel_grad(const __grid_constant__ BsParams P, const __grid_constant__ BsGra
   __syncthreads();
   bs_write_out(W, g_acc, 1 + 2 * BS_M, 1 + 2 * BS_M, s_nbins);
 }
+
+#define KERNEL_G_ARGS const __grid_constant__ BsParams P, const __grid_constant__ BsGradParams Q, \
+                  const u64* __restrict__ lane_tab, const u64* __restrict__ thr_tab, \
+                  const u64* __restrict__ wmid128, const mx* __restrict__ ptab, \
+                  const mx* __restrict__ ptab_ex, const BsWork W
+#define KERNEL_G_PASS P, Q, lane_tab, thr_tab, wmid128, ptab, ptab_ex, W
+extern "C" __global__ void KERNEL_BOUNDS bs_kernel_grad(KERNEL_G_ARGS) { bs_kernel_grad_body<0>(KERNEL_G_PASS); }
+extern "C" __global__ void KERNEL_BOUNDS bs_kernel_grad_p1(KERNEL_G_ARGS) { bs_kernel_grad_body<1>(KERNEL_G_PASS); }
+extern "C" __global__ void KERNEL_BOUNDS bs_kernel_grad_p2(KERNEL_G_ARGS) { bs_kernel_grad_body<2>(KERNEL_G_PASS); }
 #endif
 )PBAT";
 

@@ -52,7 +52,7 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
                const DeviceInfo& dev, BsLaunch& bl);
 cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsigned long long* d_lane,
                       const unsigned long long* d_thr, const unsigned long long* d_wmid,
-                      const void* d_ptab, const void* d_ptab_ex, const DevWork& W);
+                      const void* d_ptab, const void* d_ptab_ex, const DevWork& W, int phase);
 const std::vector<MxHost>& bs_ptab(const BsLaunch& bl);
 const std::vector<MxHost>& bs_ptab_ex(const BsLaunch& bl);
 const std::vector<unsigned long long>& bs_thr_tab(const BsLaunch& bl);
@@ -60,7 +60,7 @@ bool bs_grad(const BsLaunch& bl);
 const std::vector<int>& bs_perm(const BsLaunch& bl);
 unsigned long long bs_items(const BsLaunch& bl);
 unsigned long long bs_item_states(const BsLaunch& bl);
-int bs_per_sm(const BsLaunch& bl);
+int bs_per_sm(const BsLaunch& bl, int phase);
 int bs_nthr(const BsLaunch& bl);
 const std::vector<unsigned long long>& bs_lane_tab(const BsLaunch& bl);
 const std::vector<unsigned long long>& bs_wmid(const BsLaunch& bl);
@@ -424,6 +424,11 @@ struct Job {
   std::vector<int> perm;       // internal arc position -> input arc
   unsigned long long item_states = 0, n_items = 0;
   int grid_nthr = 128;
+  // two launches per enumeration: the first resolves what the prune can and
+  // defers the items left to walk, the second walks them (bit-sliced kernels
+  // with the prune on and many items)
+  bool two_phase = false;
+  int grid1 = 0, grid2 = 0;   // grids of the two launches
   // the inputs, kept to re-run the exact frontier kernel when R is too small
   // for the bit-sliced kernel's fixed-point error bound
   std::vector<int32_t> tail_copy, head_copy;
@@ -677,7 +682,7 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
     J->bs = bs_new();
     if ((rc = bs_prepare(g, p, grad, o, J->dev, *J->bs))) return rc;
     J->perm = bs_perm(*J->bs);
-    per_sm = bs_per_sm(*J->bs);
+    per_sm = bs_per_sm(*J->bs, 0);
     nthr = bs_nthr(*J->bs);
     n_items = bs_items(*J->bs);
     J->item_states = bs_item_states(*J->bs);
@@ -717,6 +722,19 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   }
   J->n_items = n_items;
   J->grid_nthr = nthr;
+  // Deferring the walked items to a second launch lets the whole grid share
+  // them at the end instead of meeting them in ticket order: with the
+  // prune-aware plan of the 40-arc network 9% of the items are walked, each
+  // about 10^5 instructions per warp, spread over the whole ticket range, so
+  // the last ones otherwise start late (fused kernel on GB300: 22.7 -> 20.8
+  // ms at the best shapes).  The first launch visits the items with a fixed
+  // warp stride and appends deferred items 32 at a time.  The R kernel's
+  // items are shorter and it stays faster in one launch (7.7 against 8.0
+  // ms), so only the fused kernel defers.  Small item counts keep one launch
+  // (the second costs a launch latency).
+  J->two_phase = J->bs && grad && o.prune && n_items >= (1ull << 18) && n_items <= (1ull << 24);
+  // the list has a slot for every item (at most 128 MiB), so it never fills
+  const unsigned long long list_cap = J->two_phase ? n_items : 0;
   const long long warps_per_block = nthr / 32;
   long long grid = (long long)per_sm * J->dev.sms;
   // never more warps than work items
@@ -724,6 +742,11 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
                           warps_per_block - 1) / warps_per_block;
   grid = std::max(1LL, std::min(grid, need));
   J->grid = (int)grid;
+  if (J->bs) {
+    // the two launches of a two-launch run fill the GPU at their own occupancy
+    J->grid1 = (int)std::max(1LL, std::min((long long)bs_per_sm(*J->bs, 1) * J->dev.sms, need));
+    J->grid2 = (int)std::max(1LL, std::min((long long)bs_per_sm(*J->bs, 2) * J->dev.sms, need));
+  }
   const int m = g.m;
   // accumulators per block: the frontier kernel and the bit-sliced R kernel
   // write R and one value per arc (zeros for R only) or R alone; the fused
@@ -737,6 +760,8 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t o_counter = off; off = up16(off + 8);
   const size_t o_status = off; off = up16(off + 4);
   const size_t o_stats = off; off = up16(off + 3 * 8);
+  const size_t o_list_n = off; off = up16(off + 8);     // deferred-item count and ticket
+  const size_t o_counter2 = off; off = up16(off + 8);
   const size_t o_out_n = off; off = up16(off + (size_t)(m + 1) * 8);
   const size_t limbs_bytes = J->bs ? (size_t)n_acc * 8 * 8 : 0;
   const size_t o_out_limbs = off; off = up16(off + limbs_bytes);
@@ -746,7 +771,10 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   const size_t o_part_acc = off; off = up16(off + part_bytes);
   const size_t o_part_n = off; off = up16(off + (J->bs ? 0 : (size_t)grid * (m + 1) * 8));
   const size_t o_out_acc = off; off = up16(off + (size_t)n_acc * sizeof(dd));
-  const size_t wacc_bytes = (J->bs && bs_grad(*J->bs)) ? (size_t)grid * (nthr / 32) * (1 + 2 * m) * 24 : 0;
+  // per-warp slots of every block of the largest of the launches' grids
+  const long long grid_max = std::max<long long>(grid, std::max(J->grid1, J->grid2));
+  const size_t wacc_bytes =
+      (J->bs && bs_grad(*J->bs)) ? (size_t)grid_max * (nthr / 32) * (1 + 2 * m) * 24 : 0;
   const size_t o_wacc = off; off = up16(off + wacc_bytes);
   const size_t o_wmid = off; off = up16(off + wmid.size() * sizeof(u128));
   size_t o_lane = 0, o_thr = 0, o_wmid64 = 0, o_ptab = 0, o_ptabx = 0, o_tab_end = 0;
@@ -758,6 +786,7 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
     o_ptabx = off; off = up16(off + bs_ptab_ex(*J->bs).size() * sizeof(MxHost));
     o_tab_end = off;
   }
+  const size_t o_list = off; off = up16(off + (size_t)list_cap * 8);
   const size_t dbytes = off;
   // host (pinned) layout: results + staging of the walk table
   // the first reset_bytes mirror the device's result region (one copy back)
@@ -785,6 +814,10 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   J->W.out_n = (unsigned long long*)(d + o_out_n);
   J->W.out_limbs = limbs_bytes ? (unsigned long long*)(d + o_out_limbs) : nullptr;
   J->W.wacc = wacc_bytes ? (void*)(d + o_wacc) : nullptr;
+  J->W.list = list_cap ? (unsigned long long*)(d + o_list) : nullptr;
+  J->W.list_cap = list_cap;
+  J->W.list_n = (unsigned long long*)(d + o_list_n);
+  J->W.counter2 = (unsigned long long*)(d + o_counter2);
   J->d_wmid = (u128*)(d + o_wmid);
   J->h_region = h + h_region;
   J->h_acc = (dd*)(h + h_acc);
@@ -874,9 +907,15 @@ int job_launch(Job* J, cudaStream_t st) {
     J->evs.push_back(e);
   }
   if (timed) PBAT_CUDA(cudaEventRecord(J->evs[J->n_pending].first, st));
-  if (J->bs)
+  if (J->bs && !J->two_phase) {
     PBAT_CUDA(bs_launch(*J->bs, J->grid, st, J->d_lane, J->d_thr, J->d_wmid64, J->d_ptab,
-                        J->d_ptabx, J->W));
+                        J->d_ptabx, J->W, 0));
+  } else if (J->bs) {
+    PBAT_CUDA(bs_launch(*J->bs, J->grid1, st, J->d_lane, J->d_thr, J->d_wmid64, J->d_ptab,
+                        J->d_ptabx, J->W, 1));
+    PBAT_CUDA(bs_launch(*J->bs, J->grid2, st, J->d_lane, J->d_thr, J->d_wmid64, J->d_ptab,
+                        J->d_ptabx, J->W, 2));
+  }
   else
     PBAT_CUDA(launch_frontier(J->pl.grad, J->pl.wide, J->grid, J->pl.nthr, J->pl.smem, st, J->P,
                               J->d_wmid, J->W));
@@ -922,7 +961,8 @@ int job_read(Job* J, cudaStream_t st, double* R_out, uint64_t* Nk_out, double* d
         cudaGetLastError();
     }
     opt->stats[4] = (unsigned long long)ns;
-    opt->stats[5] = (J->bs ? 1 : 2) * J->n_pending;   // the frontier kernel adds its reduce
+    // one kernel per launch, two in two-phase runs; the frontier kernel adds its reduce
+    opt->stats[5] = (J->bs ? (J->two_phase ? 2 : 1) : 2) * J->n_pending;
     opt->stats[6] = J->n_items;
     opt->stats[7] = J->n_pending;
   }

@@ -50,6 +50,13 @@ struct DevWork {
   unsigned long long* out_n;    // [m + 1]
   void* wacc;                   // fused bit-sliced kernel: per-warp accumulators (24 B each)
   unsigned long long* out_limbs;  // bit-sliced kernels: [n_acc][8] 256-bit fixed point, scale 2^250
+  // two-phase bit-sliced launches: the first defers the items its prune
+  // leaves to walk to `list` (capacity list_cap, count list_n), the second
+  // walks them, taking them by the ticket counter2
+  unsigned long long* list;
+  unsigned long long list_cap;
+  unsigned long long* list_n;
+  unsigned long long* counter2;
 };
 
 }  // namespace pbat

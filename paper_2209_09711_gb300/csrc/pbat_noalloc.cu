@@ -222,7 +222,7 @@ static int run_noalloc(const GraphIn& g, const double* p, const pbat_options* op
   const int grid = (int)std::max(1LL, std::min({(long long)per_sm * nd.sms, need, max_grid}));
 
   char* base = (char*)nd.base;
-  DevWork W;
+  DevWork W{};
   W.counter = (unsigned long long*)(base + kNaCounter);
   W.status = (unsigned int*)(base + kNaCounter + 16);
   W.stats = (unsigned long long*)(base + kNaCounter + 32);
