@@ -79,15 +79,16 @@ SHAPES = {
 # kernel whose source has changed since has no entry, and its roofline
 # fraction is reported as null.
 COUNTS = {
-    # 24 nodes, 40 arcs: fused (L 10, 256 threads, prune 2, occupancy 2) and R-only (L 9, 128, 2, 0)
-    "357f266c9ed0a6cb": (15862482255 / 2**40, 167680, "profiles/bs_kernel_grad_undirected24x40.md"),
-    "d1fa767e4a7c1c6c": (6497359334 / 2**40, 67584, "profiles/bs_kernel_undirected24x40.md"),
+    # 24 nodes, 40 arcs: fused (L 9, 256 threads, prune 2, occupancy 2; its two launches
+    # summed) and R-only (L 9, 128, 2, 0)
+    "955f268a1ba972fb": (14332281402 / 2**40, 2065408, "profiles/bs_kernel_grad_undirected24x40.md"),
+    "51c3d7bb603a7930": (6496949619 / 2**40, 66304, "profiles/bs_kernel_undirected24x40.md"),
     # directed, 20 nodes, 34 arcs: fused (7, 192, 2, 0) and R-only (8, 192, 2, 0)
-    "af2a14dc32809044": (27929511 / 2**34, 110080, "profiles/bs_kernel_grad_directed20x34.md"),
-    "e13f7bf524725d17": (11980584 / 2**34, 64512, "profiles/bs_kernel_directed20x34.md"),
+    "6c6a6d704fc7838e": (27930517 / 2**34, 110336, "profiles/bs_kernel_grad_directed20x34.md"),
+    "d264275e6a8b2fb8": (11970600 / 2**34, 64512, "profiles/bs_kernel_directed20x34.md"),
     # 3x6 grid: fused (5, 128, 1, 0) and R-only (5, 64, 1, 0)
-    "c512006d5dd496df": (17711335 / 2**27, 96256, "profiles/bs_kernel_grad_grid3x6.md"),
-    "89fe3f746591f645": (8524601 / 2**27, 44288, "profiles/bs_kernel_grid3x6.md"),
+    "ec6db57fa8c5e143": (17705145 / 2**27, 97280, "profiles/bs_kernel_grad_grid3x6.md"),
+    "fe6aa55f83b627cb": (8556685 / 2**27, 44032, "profiles/bs_kernel_grid3x6.md"),
 }
 
 SM_COUNT = 152

@@ -191,6 +191,7 @@ struct BsLaunch {
   size_t smem = 0;
   int per_sm = 1;                     // resident blocks per SM: one-launch kernel
   int per_sm1 = 1, per_sm2 = 1;       // the two launches of a two-launch run
+  size_t smem1 = 0;                   // shared memory of the first of two fused launches
 };
 
 // out[v] = product over x < n of (bit x of v ? p : 1 - p) of arc arcs[x], for
@@ -469,25 +470,29 @@ int bs_prepare(const GraphIn& g, const double* p, bool grad, const pbat_options&
       bl.per_sm = it->second.per_sm;
       bl.per_sm1 = it->second.per_sm1;
       bl.per_sm2 = it->second.per_sm2;
+      bl.smem1 = grad ? (size_t)(m + 1) * 8 : bl.smem;
       return PBAT_OK;
     }
   }
   // shared-memory attribute and resident blocks per SM of each entry point
-  auto setup = [&](cudaKernel_t k, int* per_sm) -> int {
+  // (the first of two fused launches needs only the N_k counts)
+  bl.smem1 = grad ? (size_t)(m + 1) * 8 : bl.smem;
+  auto setup = [&](cudaKernel_t k, size_t smem, int* per_sm) -> int {
     *per_sm = 1;
     if (!k) return PBAT_OK;
     cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bl.smem);
+                                         (int)smem);
     if (e != cudaSuccess) return fail(PBAT_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, (const void*)k, bl.nthr, bl.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, (const void*)k, bl.nthr, smem);
     if (e != cudaSuccess || *per_sm < 1) {
       cudaGetLastError();
       *per_sm = 1;
     }
     return PBAT_OK;
   };
-  if ((rc = setup(bl.jit.kernel, &bl.per_sm)) || (rc = setup(bl.jit.kernel_p1, &bl.per_sm1)) ||
-      (rc = setup(bl.jit.kernel_p2, &bl.per_sm2)))
+  if ((rc = setup(bl.jit.kernel, bl.smem, &bl.per_sm)) ||
+      (rc = setup(bl.jit.kernel_p1, bl.smem1, &bl.per_sm1)) ||
+      (rc = setup(bl.jit.kernel_p2, bl.smem, &bl.per_sm2)))
     return rc;
   std::lock_guard<std::mutex> lk(g_bsplan_mu);
   auto it = g_bsplan.find(key);
@@ -512,7 +517,8 @@ cudaError_t bs_launch(const BsLaunch& bl, int grid, cudaStream_t st, const unsig
     const BsGradParamsHost& Q = bl.Q;
     void* args[] = {(void*)&P, (void*)&Q, (void*)&d_lane, (void*)&d_thr, (void*)&d_wmid,
                     (void*)&d_ptab, (void*)&d_ptab_ex, (void*)&W};
-    return cudaLaunchKernel((const void*)k, dim3(grid), dim3(bl.nthr), args, bl.smem, st);
+    return cudaLaunchKernel((const void*)k, dim3(grid), dim3(bl.nthr), args,
+                            phase == 1 ? bl.smem1 : bl.smem, st);
   }
   void* args[] = {(void*)&P, (void*)&d_lane, (void*)&d_wmid, (void*)&d_ptab, (void*)&W};
   return cudaLaunchKernel((const void*)k, dim3(grid), dim3(bl.nthr), args, bl.smem, st);

@@ -38,6 +38,14 @@ typedef unsigned long long u64;
 #else
 #define KERNEL_BOUNDS __launch_bounds__(BS_NTHR)
 #endif
+// the first of two launches (prune and closed-form sums, no walk) is compiled
+// for at least 24 resident warps per SM: on GB300 it needs about 80 registers
+// then, without spills
+#if defined(BS_MINB) && BS_MINB > 768 / BS_NTHR
+#define KERNEL_BOUNDS_P1 __launch_bounds__(BS_NTHR, BS_MINB)
+#else
+#define KERNEL_BOUNDS_P1 __launch_bounds__(BS_NTHR, (768 / BS_NTHR > 0 ? 768 / BS_NTHR : 1))
+#endif
 #define BS_OUT (BS_L - BS_IN)
 
 struct dd { double hi, lo; };   // host-side double-double (only carried, never computed here)
@@ -450,7 +458,7 @@ __device__ __forceinline__ void bs_kernel_body(const BsParams& P, const u64* __r
 #define KERNEL_R_ARGS const __grid_constant__ BsParams P, const u64* __restrict__ lane_tab, \
                   const u64* __restrict__ wmid_tab, const mx* __restrict__ ptab, const BsWork W
 extern "C" __global__ void KERNEL_BOUNDS bs_kernel(KERNEL_R_ARGS) { bs_kernel_body<0>(P, lane_tab, wmid_tab, ptab, W); }
-extern "C" __global__ void KERNEL_BOUNDS bs_kernel_p1(KERNEL_R_ARGS) { bs_kernel_body<1>(P, lane_tab, wmid_tab, ptab, W); }
+extern "C" __global__ void KERNEL_BOUNDS_P1 bs_kernel_p1(KERNEL_R_ARGS) { bs_kernel_body<1>(P, lane_tab, wmid_tab, ptab, W); }
 extern "C" __global__ void KERNEL_BOUNDS bs_kernel_p2(KERNEL_R_ARGS) { bs_kernel_body<2>(P, lane_tab, wmid_tab, ptab, W); }
 #endif
 
@@ -518,13 +526,17 @@ __device__ __forceinline__ void bs_kernel_grad_body(
   u64* s_tt = (u64*)(s_wm + (1 << BS_L));                   // [4][256] thread-pattern masses (2^62)
   u64* s_bins = s_tt + 4 * 256;                             // [L + 1][NTHR]
   u128* s_A = (u128*)(s_bins + (BS_L + 1) * BS_NTHR);       // [BS_OUT][NTHR]
-  u64* s_nbins = (u64*)(s_A + (BS_OUT > 0 ? BS_OUT : 1) * BS_NTHR);
+  // the first of two launches walks nothing: it holds only the N_k counts,
+  // so it is launched with (m + 1) * 8 bytes of shared memory
+  u64* s_nbins = PHASE == 1 ? (u64*)smem : (u64*)(s_A + (BS_OUT > 0 ? BS_OUT : 1) * BS_NTHR);
   // per warp, in global scratch: R, then A_k and B_k of every arc k
   facc* g_acc = W.wacc + (size_t)blockIdx.x * (BS_NTHR / 32) * (1 + 2 * BS_M);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
-  for (int i = tid; i < 4 * 256; i += BS_NTHR) s_tt[i] = thr_tab[i];
-  for (int i = tid; i < (1 << BS_L); i += BS_NTHR) s_wm[i] = ((const ulonglong2*)wmid128)[i];
+  if constexpr (PHASE != 1) {
+    for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
+    for (int i = tid; i < 4 * 256; i += BS_NTHR) s_tt[i] = thr_tab[i];
+    for (int i = tid; i < (1 << BS_L); i += BS_NTHR) s_wm[i] = ((const ulonglong2*)wmid128)[i];
+  }
   for (int i = tid; i < (BS_NTHR / 32) * (1 + 2 * BS_M); i += BS_NTHR) g_acc[i] = facc{u128{0ull, 0ull}, 0, 0};
   for (int i = tid; i <= BS_M; i += BS_NTHR) s_nbins[i] = 0ull;
   __syncthreads();
@@ -786,7 +798,7 @@ __device__ __forceinline__ void bs_kernel_grad_body(
                   const mx* __restrict__ ptab_ex, const BsWork W
 #define KERNEL_G_PASS P, Q, lane_tab, thr_tab, wmid128, ptab, ptab_ex, W
 extern "C" __global__ void KERNEL_BOUNDS bs_kernel_grad(KERNEL_G_ARGS) { bs_kernel_grad_body<0>(KERNEL_G_PASS); }
-extern "C" __global__ void KERNEL_BOUNDS bs_kernel_grad_p1(KERNEL_G_ARGS) { bs_kernel_grad_body<1>(KERNEL_G_PASS); }
+extern "C" __global__ void KERNEL_BOUNDS_P1 bs_kernel_grad_p1(KERNEL_G_ARGS) { bs_kernel_grad_body<1>(KERNEL_G_PASS); }
 extern "C" __global__ void KERNEL_BOUNDS bs_kernel_grad_p2(KERNEL_G_ARGS) { bs_kernel_grad_body<2>(KERNEL_G_PASS); }
 #endif
 )PBAT";
