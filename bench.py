@@ -59,15 +59,16 @@ BATCHED = "batched-64x16"
 CONFIG_ORDER = ["random-undirected-n8-m16", "grid-3x6", "random-directed-n20-m34", BATCHED,
                 "random-undirected-n24-m40"]
 
-# Launch shapes (walk arcs L, threads per block, prune mode, occupancy) the
-# bench pins per workload and kernel, from shape sweeps on GB300, so that the
-# timed launch is the one the instruction counts below were taken from
-# (--autotune lets the autotuner choose instead).  prune 2 = prune-aware
-# prefix arcs.
+# Launch shapes (walk arcs L, threads per block, prune mode, occupancy,
+# launches) the bench pins per workload and kernel, from shape sweeps on
+# GB300, so that the timed launches are the ones the instruction counts below
+# were taken from (--autotune lets the autotuner choose instead).  prune 2 =
+# prune-aware prefix arcs; launches 2 = the first launch resolves what the
+# prune can and defers the items left to walk to the second.
 SHAPES = {
-    "random-undirected-n24-m40": {"fused": (9, 256, 2, 2), "r_only": (9, 128, 2, 0)},
-    "random-directed-n20-m34": {"fused": (7, 192, 2, 0), "r_only": (8, 192, 2, 0)},
-    "grid-3x6": {"fused": (5, 128, 1, 0), "r_only": (5, 64, 1, 0)},
+    "random-undirected-n24-m40": {"fused": (9, 256, 2, 2, 2), "r_only": (9, 128, 2, 0, 1)},
+    "random-directed-n20-m34": {"fused": (7, 192, 2, 0, 1), "r_only": (8, 192, 2, 0, 1)},
+    "grid-3x6": {"fused": (5, 128, 1, 0, 1), "r_only": (5, 64, 1, 0, 1)},
 }
 
 # Per generated kernel source (first 16 hex digits of its SHA-256, as
@@ -79,16 +80,16 @@ SHAPES = {
 # kernel whose source has changed since has no entry, and its roofline
 # fraction is reported as null.
 COUNTS = {
-    # 24 nodes, 40 arcs: fused (L 9, 256 threads, prune 2, occupancy 2; its two launches
-    # summed) and R-only (L 9, 128, 2, 0)
-    "955f268a1ba972fb": (14332281402 / 2**40, 2065408, "profiles/bs_kernel_grad_undirected24x40.md"),
-    "51c3d7bb603a7930": (6496949619 / 2**40, 66304, "profiles/bs_kernel_undirected24x40.md"),
-    # directed, 20 nodes, 34 arcs: fused (7, 192, 2, 0) and R-only (8, 192, 2, 0)
-    "6c6a6d704fc7838e": (27930517 / 2**34, 110336, "profiles/bs_kernel_grad_directed20x34.md"),
-    "d264275e6a8b2fb8": (11970600 / 2**34, 64512, "profiles/bs_kernel_directed20x34.md"),
-    # 3x6 grid: fused (5, 128, 1, 0) and R-only (5, 64, 1, 0)
-    "ec6db57fa8c5e143": (17705145 / 2**27, 97280, "profiles/bs_kernel_grad_grid3x6.md"),
-    "fe6aa55f83b627cb": (8556685 / 2**27, 44032, "profiles/bs_kernel_grid3x6.md"),
+    # 24 nodes, 40 arcs: fused (L 9, 256 threads, prune 2, occupancy 2, its two launches
+    # summed) and R-only (L 9, 128, 2, 0, one launch)
+    "bc3c0781ca06bef2": (14333699417 / 2**40, 1683456, "profiles/bs_kernel_grad_undirected24x40.md"),
+    "9c5a3a090d17aa15": (6497309295 / 2**40, 226048, "profiles/bs_kernel_undirected24x40.md"),
+    # directed, 20 nodes, 34 arcs: fused (7, 192, 2, 0, 1) and R-only (8, 192, 2, 0, 1)
+    "b872621b02c552be": (27932078 / 2**34, 111104, "profiles/bs_kernel_grad_directed20x34.md"),
+    "a7b8b2dc1e6e0756": (11972630 / 2**34, 64512, "profiles/bs_kernel_directed20x34.md"),
+    # 3x6 grid: fused (5, 128, 1, 0, 1) and R-only (5, 64, 1, 0, 1)
+    "30249326f32d3992": (17694745 / 2**27, 96768, "profiles/bs_kernel_grad_grid3x6.md"),
+    "0ca3591646ebbbdc": (8533221 / 2**27, 44288, "profiles/bs_kernel_grid3x6.md"),
 }
 
 SM_COUNT = 152
@@ -101,7 +102,7 @@ def shape_opts(pb, workload: str, kind: str, **extra):
     sh = SHAPES.get(workload, {}).get(kind)
     if sh is None:
         return pb.options(**extra)
-    kw = dict(walk_bits=sh[0], block_threads=sh[1], prune=sh[2], occupancy=sh[3])
+    kw = dict(walk_bits=sh[0], block_threads=sh[1], prune=sh[2], occupancy=sh[3], launches=sh[4])
     kw.update(extra)
     return pb.options(**kw)
 
@@ -311,7 +312,8 @@ def _single_record(pb, name, steps, warmup, stream, flush, barrier, ws):
         ms, kern, _, res = _time_plan(plan, steps, warmup, stream, flush, barrier)
         out[kind] = res
         rec[kind] = {"value": ws * states / (ms / 1e3), "ms_per_step": ms, "kernel_ms": kern,
-                     "shape": dict(plan.describe(), prune=opts.prune, occupancy=opts.occupancy),
+                     "shape": dict(plan.describe(), prune=opts.prune, occupancy=opts.occupancy,
+                                   launches=opts.launches),
                      "walked_fraction": res.stats[0] / states,
                      "roofline": _roofline(kernel, key, states, kern)}
         plan.close()
@@ -497,12 +499,14 @@ def run_ours(a):
         "config": workload_config(name, net, ws,
                                   "flushed between steps (256 MiB write, outside the timed events)"),
         "roofline": roof,
-        "fused_shape": dict(fused.describe(), prune=f_opts.prune, occupancy=f_opts.occupancy),
+        "fused_shape": dict(fused.describe(), prune=f_opts.prune, occupancy=f_opts.occupancy,
+                            launches=f_opts.launches),
         "unpruned": {"value": ws * states / (ms_np / 1e3), "ms_per_step": ms_np, "kernel_ms": kern_np,
                      "what": "the fused kernel with the monotone prune off (every state walked)"},
         "r_only": {"value": ws * states / (ms_r / 1e3), "ms_per_step": ms_r, "kernel_ms": kern_r,
                    "kernel": "bs_kernel",
-                   "shape": dict(ronly.describe(), prune=r_opts.prune, occupancy=r_opts.occupancy),
+                   "shape": dict(ronly.describe(), prune=r_opts.prune, occupancy=r_opts.occupancy,
+                                 launches=r_opts.launches),
                    "roofline": _roofline("bs_kernel", source_key(pb, net, r_opts, False), states,
                                          kern_r)},
         "plain_gpu_bat": {"value": ws * plain_states / (ms_p / 1e3), "ms_per_step": ms_p,
@@ -641,7 +645,8 @@ def run_probe(a):
     print(json.dumps({"probe": a.probe, "workload": a.workload, "R": r.R, "source_key": key,
                       "kernel_ms": r.stats[4] / 1e6, "items": r.stats[6], "walked": r.stats[0],
                       "states": 2**net.m,
-                      "shape": dict(plan.describe(), prune=o.prune, occupancy=o.occupancy)}))
+                      "shape": dict(plan.describe(), prune=o.prune, occupancy=o.occupancy,
+                                    launches=o.launches)}))
     plan.close()
     return 0
 

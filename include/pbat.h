@@ -88,6 +88,12 @@ typedef struct pbat_options {
                            0 = the compiler's own register choice; -1 (default) = 0, or
                            the autotuner's choice when it runs.  Results do not depend on
                            it. */
+  int launches;         /* bit-sliced single-network kernels with the prune on: 1 = one
+                           launch; 2 = two launches, the first resolving what the prune can
+                           and deferring the work items left to walk, the second walking
+                           them (at most 2^24 items, else one launch); 0 (default) = two
+                           for the fused kernel with 2^18 to 2^24 items, else one, or the
+                           autotuner's choice when it runs.  Results do not depend on it. */
   int range_bits;       /* 0 (default) = whole space.  Otherwise only the states whose
                            first range_bits coordinates, read as an integer, lie in
                            [range_lo, range_hi) -- the divisions range_lo..range_hi-1 of

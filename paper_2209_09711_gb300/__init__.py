@@ -53,6 +53,7 @@ class Options(ctypes.Structure):
         ("prune", ctypes.c_int),
         ("autotune", ctypes.c_int),
         ("occupancy", ctypes.c_int),
+        ("launches", ctypes.c_int),
         ("range_bits", ctypes.c_int),
         ("range_lo", ctypes.c_uint64),
         ("range_hi", ctypes.c_uint64),

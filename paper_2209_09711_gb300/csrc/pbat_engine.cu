@@ -163,6 +163,8 @@ int validate_options(const pbat_options* o, int m) {
   if (o->prune < 0 || o->prune > 2) return fail(PBAT_EINVAL, "prune=%d not in {0,1,2}", o->prune);
   if (o->occupancy < -1 || o->occupancy > 8)
     return fail(PBAT_EINVAL, "occupancy=%d not in [-1,8]", o->occupancy);
+  if (o->launches < 0 || o->launches > 2)
+    return fail(PBAT_EINVAL, "launches=%d not in {0,1,2}", o->launches);
   if (!(o->time_budget_s >= 0.0)) return fail(PBAT_EINVAL, "time_budget_s must be >= 0");
   return PBAT_OK;
 }
@@ -470,11 +472,11 @@ void job_destroy(Job* J);
 // Candidates are timed on the real problem (CUDA events around the kernel,
 // best of two launches) and the fastest is kept per network structure, mode
 // and range -- in memory, and in the file named by PBAT_AUTOTUNE_CACHE if
-// that is set ("key walk_bits block_threads prune occupancy" lines).  Only
+// that is set ("key walk_bits block_threads prune occupancy launches" lines).  Only
 // problems of at least 2^26 states are tuned: below that a launch is too
 // short for the choice to matter.
 struct TuneChoice {
-  int L, nt, prune, occ;
+  int L, nt, prune, occ, launches;
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneChoice> g_tune;
@@ -484,7 +486,8 @@ static std::string tune_key(const GraphIn& g, bool grad, const pbat_options& o, 
   char head[180];
   snprintf(head, sizeof head, "d%d:g%d:n%d:m%d:dir%d:s%d:t%d:r%d:%llx:%llx:pr%d:oc%d:", device,
            grad ? 1 : 0, g.n, g.m, g.directed ? 1 : 0, g.source, g.sink, o.range_bits,
-           (unsigned long long)o.range_lo, (unsigned long long)o.range_hi, o.prune, o.occupancy);
+           (unsigned long long)o.range_lo, (unsigned long long)o.range_hi, o.prune,
+           o.occupancy * 4 + o.launches);
   std::string k = head;
   for (int i = 0; i < g.m; ++i) {
     char e[24];
@@ -504,8 +507,9 @@ static void tune_load_file() {
   char line[4400];
   while (fgets(line, sizeof line, f)) {
     char key[4096];
-    TuneChoice c{-1, 128, 1, 0};
-    if (sscanf(line, "%4095s %d %d %d %d", key, &c.L, &c.nt, &c.prune, &c.occ) == 5) g_tune[key] = c;
+    TuneChoice c{-1, 128, 1, 0, 1};
+    if (sscanf(line, "%4095s %d %d %d %d %d", key, &c.L, &c.nt, &c.prune, &c.occ, &c.launches) == 6)
+      g_tune[key] = c;
   }
   fclose(f);
 }
@@ -515,7 +519,7 @@ static void tune_store_file(const std::string& key, const TuneChoice& c) {
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d\n", key.c_str(), c.L, c.nt, c.prune, c.occ);
+  fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), c.L, c.nt, c.prune, c.occ, c.launches);
   fclose(f);
 }
 
@@ -584,6 +588,7 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
       o.block_threads = it->second.nt;
       o.prune = it->second.prune;
       o.occupancy = it->second.occ;
+      o.launches = it->second.launches;
       return PBAT_OK;
     }
   }
@@ -599,7 +604,7 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
     const double ta = tune_time(g, p, grad, a, st), tb = tune_time(g, p, grad, b, st);
     if (tb > 0 && (ta < 0 || tb < ta)) mode = 2;
   }
-  // stage 2: walk length x block size x occupancy.  Candidates run the whole
+  // stage 2: walk length x block size x occupancy x launches.  Candidates run the whole
   // problem: a block of the equal division is not a fair sample (which arcs
   // its range fixes changes how much the prune removes; the first block of
   // the 40-arc network favoured a shape 50% slower on the whole).  Large
@@ -617,25 +622,33 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
   // 40-arc network in prune-aware mode went from 26.0 to 24.7 ms with it
   if (o.occupancy >= 0) occs.push_back(o.occupancy);
   else occs = {0, 2};
+  // one launch or two (with the prune on): the deferral pays where walked
+  // items are long and few, or where the prune resolves nearly every item
+  std::vector<int> launch_modes;
+  if (o.launches) launch_modes.push_back(o.launches);
+  else if (mode) launch_modes = {1, 2};
+  else launch_modes.push_back(1);
   std::vector<pbat_options> cands;
   for (int L : Ls)
     for (int nt : nts)
-      for (int oc : occs) {
-        if (oc * nt > 2048) continue;
-        pbat_options t = o;
-        t.prune = mode;
-        t.walk_bits = L;
-        t.block_threads = nt;
-        t.occupancy = oc;
-        cands.push_back(t);
-      }
+      for (int oc : occs)
+        for (int nl : launch_modes) {
+          if (oc * nt > 2048) continue;
+          pbat_options t = o;
+          t.prune = mode;
+          t.walk_bits = L;
+          t.block_threads = nt;
+          t.occupancy = oc;
+          t.launches = nl;
+          cands.push_back(t);
+        }
   bs_precompile(g, p, grad, cands, dev);
   double best_ms = 1e300;
-  TuneChoice best{-1, 128, mode, 0};
+  TuneChoice best{-1, 128, mode, 0, 1};
   for (const pbat_options& t : cands) {
     const double ms = tune_time(g, p, grad, t, st);
     if (ms > 0 && ms < best_ms)
-      best_ms = ms, best = TuneChoice{t.walk_bits, t.block_threads, t.prune, t.occupancy};
+      best_ms = ms, best = TuneChoice{t.walk_bits, t.block_threads, t.prune, t.occupancy, t.launches};
   }
   cudaStreamDestroy(st);
   if (best.L < 0) return PBAT_OK;  // keep the planner's defaults
@@ -643,6 +656,7 @@ static int autotune(const GraphIn& g, const double* p, bool grad, pbat_options& 
   o.block_threads = best.nt;
   o.prune = best.prune;
   o.occupancy = best.occ;
+  o.launches = best.launches;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best;
   tune_store_file(key, best);
@@ -730,9 +744,12 @@ int job_create(const GraphIn& g, const double* p, bool grad, pbat_options* opt, 
   // ms at the best shapes).  The first launch visits the items with a fixed
   // warp stride and appends deferred items 32 at a time.  The R kernel's
   // items are shorter and it stays faster in one launch (7.7 against 8.0
-  // ms), so only the fused kernel defers.  Small item counts keep one launch
-  // (the second costs a launch latency).
-  J->two_phase = J->bs && grad && o.prune && n_items >= (1ull << 18) && n_items <= (1ull << 24);
+  // ms), so by default only the fused kernel defers; opt.launches (or the
+  // autotuner) chooses otherwise.  Small item counts keep one launch by
+  // default (the second costs a launch latency).
+  const bool can_two = J->bs && o.prune && n_items <= (1ull << 24);
+  J->two_phase = can_two && (o.launches == 2 ||
+                             (o.launches == 0 && grad && n_items >= (1ull << 18)));
   // the list has a slot for every item (at most 128 MiB), so it never fills
   const unsigned long long list_cap = J->two_phase ? n_items : 0;
   const long long warps_per_block = nthr / 32;
@@ -1056,6 +1073,7 @@ void pbat_options_init(pbat_options* o) {
   o->prune = 1;
   o->autotune = 1;
   o->occupancy = -1;
+  o->launches = 0;
 }
 
 int pbat_reliability(int n_nodes, int n_arcs, const int32_t* tail, const int32_t* head,

@@ -484,3 +484,40 @@ def test_batched_workload_gradient_one_launch(pb):
                 t1, t0 = sum(T1[i]), sum(T0[i])
                 gs = (T1[i][0] - T0[i][0]) + (T1[i][1] - T0[i][1])   # from the hi/lo pairs
                 assert abs(G[g][k][i] - gs) <= _grad_tol(gs, t1, t0, Rk), (g, k, i, G[g][k][i], gs)
+
+
+# ---------------------------------------------------------------------------
+# two-launch runs (the first resolves and defers, the second walks)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_two_launch_runs_against_oracle(pb, directed):
+    """launches = 2 on whole small networks (few items, many warps without
+    any), both kernels, both planning modes, several walk lengths; one
+    launch gives identical results."""
+    for seed in range(12):
+        rng = synth.SplitMix64(18100 + seed)
+        m = 8 + rng.below(12)
+        net = synth.random_small(18200 + seed, n=3 + rng.below(10), m=m, directed=directed,
+                                 p_lo=0.03, p_hi=0.97)
+        ref = oracle.enumerate_states(net, grad=True)
+        for prune in (1, 2):
+            for walk in (0, 2, 4):
+                o = dict(algo=pb.ALGO_BITSLICE, prune=prune, walk_bits=walk, launches=2)
+                check(run(pb, net, grad=True, **o), ref, True, f"seed={seed} p{prune} w{walk} fused")
+                check(run(pb, net, **o), ref, False, f"seed={seed} p{prune} w{walk} R")
+
+
+def test_two_launch_runs_on_sampled_divisions_and_empty_range(pb):
+    net = synth.workload_random_24_40()
+    bits = 24
+    for d in (5, 9_999_999):
+        ref = oracle.enumerate_states(net, prefix_bits=bits, prefix_lo=d, prefix_hi=d + 1, grad=True)
+        for L in (4, 9):
+            o = dict(prune=2, walk_bits=L, block_threads=256, range_bits=bits, range_lo=d,
+                     range_hi=d + 1, launches=2)
+            check(run(pb, net, grad=True, **o), ref, True, f"division {d} L={L} fused")
+            check(run(pb, net, **o), ref, False, f"division {d} L={L} R")
+    # an empty range: no item in either launch
+    r = run(pb, net, grad=True, range_bits=bits, range_lo=7, range_hi=7, launches=2, prune=2)
+    assert r.R == 0.0 and all(v == 0 for v in r.Nk) and all(g == 0.0 for g in r.grad)
