@@ -67,7 +67,7 @@ CONFIG_ORDER = ["random-undirected-n8-m16", "grid-3x6", "random-directed-n20-m34
 # prune can and defers the items left to walk to the second.
 SHAPES = {
     "random-undirected-n24-m40": {"fused": (9, 256, 2, 2, 2), "r_only": (9, 128, 2, 0, 1)},
-    "random-directed-n20-m34": {"fused": (7, 192, 2, 0, 1), "r_only": (8, 192, 2, 0, 1)},
+    "random-directed-n20-m34": {"fused": (7, 192, 2, 0, 2), "r_only": (7, 128, 2, 0, 2)},
     "grid-3x6": {"fused": (5, 128, 1, 0, 1), "r_only": (5, 64, 1, 0, 1)},
 }
 
@@ -82,14 +82,15 @@ SHAPES = {
 COUNTS = {
     # 24 nodes, 40 arcs: fused (L 9, 256 threads, prune 2, occupancy 2, its two launches
     # summed) and R-only (L 9, 128, 2, 0, one launch)
-    "bc3c0781ca06bef2": (14333699417 / 2**40, 1683456, "profiles/bs_kernel_grad_undirected24x40.md"),
-    "9c5a3a090d17aa15": (6497309295 / 2**40, 226048, "profiles/bs_kernel_undirected24x40.md"),
-    # directed, 20 nodes, 34 arcs: fused (7, 192, 2, 0, 1) and R-only (8, 192, 2, 0, 1)
-    "b872621b02c552be": (27932078 / 2**34, 111104, "profiles/bs_kernel_grad_directed20x34.md"),
-    "a7b8b2dc1e6e0756": (11972630 / 2**34, 64512, "profiles/bs_kernel_directed20x34.md"),
+    "2008dae66444650a": (13201992269 / 2**40, 1677312, "profiles/bs_kernel_grad_undirected24x40.md"),
+    "53d525b5025773de": (6498148066 / 2**40, 66560, "profiles/bs_kernel_undirected24x40.md"),
+    # directed, 20 nodes, 34 arcs: fused (7, 192, 2, 0, two launches) and R-only
+    # (7, 128, 2, 0, two launches)
+    "0a3efb3aeb28fa70": (21354355 / 2**34, 92928, "profiles/bs_kernel_grad_directed20x34.md"),
+    "1066b606e51cf77d": (14841156 / 2**34, 68352, "profiles/bs_kernel_directed20x34.md"),
     # 3x6 grid: fused (5, 128, 1, 0, 1) and R-only (5, 64, 1, 0, 1)
-    "30249326f32d3992": (17694745 / 2**27, 96768, "profiles/bs_kernel_grad_grid3x6.md"),
-    "0ca3591646ebbbdc": (8533221 / 2**27, 44288, "profiles/bs_kernel_grid3x6.md"),
+    "95fa0ca393eec59c": (17364783 / 2**27, 94464, "profiles/bs_kernel_grad_grid3x6.md"),
+    "360ccef42efbbdf4": (8547686 / 2**27, 44288, "profiles/bs_kernel_grid3x6.md"),
 }
 
 SM_COUNT = 152

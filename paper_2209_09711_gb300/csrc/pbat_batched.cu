@@ -335,6 +335,7 @@ static std::string batch_key(int device, int G, const pbat_graph* graphs, int K,
   std::string k;
   auto put = [&](long long v) { k.append((const char*)&v, sizeof v); };
   put(device); put(G); put(K); put(o.prune); put(o.walk_bits); put(o.block_threads);
+  put(o.occupancy); put(o.autotune);
   put((long long)(o.time_budget_s * 1e9));
   for (int i = 0; i < G; ++i) {
     const pbat_graph& g = graphs[i];

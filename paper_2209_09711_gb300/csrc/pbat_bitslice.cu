@@ -594,6 +594,7 @@ struct BGraphHost {
 };
 
 constexpr int kBsbThreads = 128;
+constexpr int kBsbMinBlocks = 4;  // default launch bounds: 4 blocks of 128 threads, <= 128 registers
 constexpr int kBsbMaxWalk = 5;  // 2^L connectivity words per thread staged in shared memory
 constexpr int kBsbLimbs = 8;    // 32-bit chunks of a 256-bit value at scale 2^250, in 64-bit atomics
 constexpr int kBsbMaxGraphs = 256;
@@ -602,6 +603,7 @@ struct BsBatch {
   std::string key;
   bool busy = false;
   int device = -1, G = 0, K = 0, Kp = 0, grid = 0, lmax = 0;
+  int minb = 4;                     // launch bounds: blocks per SM the registers must allow
   size_t smem = 0;
   JitEntry jit;
   std::vector<BsPlan> plans;        // input order
@@ -675,8 +677,10 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   std::stable_sort(E.order.begin(), E.order.end(), [&](int a, int b) { return items[a] > items[b]; });
   // source: prelude, one struct per network (launch order), item template, kernel
   const std::string tmpl = kBsTemplate;
+  E.minb = o.occupancy > 0 ? o.occupancy : kBsbMinBlocks;
   std::string src = "#define BSB_NTHR " + std::to_string(kBsbThreads) + "\n#define BSB_LMAX " +
-                    std::to_string(E.lmax) + "\n" + tmpl.substr(0, tmpl.find("//@@GENERATED@@"));
+                    std::to_string(E.lmax) + "\n#define BSB_MINB " + std::to_string(E.minb) + "\n" +
+                    tmpl.substr(0, tmpl.find("//@@GENERATED@@"));
   for (int r = 0; r < G; ++r) {
     const BsPlan& bp = E.plans[E.order[r]];
     std::string gen = bp.gen;
@@ -698,7 +702,7 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
   // shared memory: per-thread N_k bins, the item's connectivity words (and,
   // in the gradient module, their lane transposes), per-warp N_k counts
   std::string kern = E.grad ?
-      "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR, 4)\n"
+      "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR, BSB_MINB)\n"
       "bs_batch_grad(const BGraph* __restrict__ graphs, int G, int K, int Kp, u64 total,\n"
       "         const u64* __restrict__ lt, const u64* __restrict__ nt, const u64* __restrict__ wm2,\n"
       "         const mx* __restrict__ pt, const u64* __restrict__ thw, const u64* __restrict__ tt,\n"
@@ -716,7 +720,7 @@ static int bsb_source(BsBatch& E, int G, const pbat_graph* graphs, int K, const 
       "             (threadIdx.x >> 5) * 65;\n"
       "  for (int i = lane; i < 65; i += 32) nkw[i] = 0ull;\n"
     :
-      "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR, 4)\n"
+      "extern \"C\" __global__ void __launch_bounds__(BSB_NTHR, BSB_MINB)\n"
       "bs_batch(const BGraph* __restrict__ graphs, int G, int K, int Kp, u64 total,\n"
       "         const u64* __restrict__ lt, const u64* __restrict__ nt, const u64* __restrict__ wm,\n"
       "         const mx* __restrict__ pt, const u64* __restrict__ thw, u64* limbs, u64* nk,\n"
@@ -1029,14 +1033,16 @@ int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o
 }
 
 // The batch's walk length (split depth: each network's items are its
-// prefixes of d = m - 10 - L arcs) and, with the prune on, its planning mode
-// (source/sink-near or prune-aware prefix arcs): every candidate builds its
-// module and runs the batch once; the fastest launch wins.  The gradient
-// module (elig given) is tuned the same way.  Returns false when no
-// candidate ran (the planner's defaults are kept).
+// prefixes of d = m - 10 - L arcs), with the prune on its planning mode
+// (source/sink-near or prune-aware prefix arcs), then, unless the options
+// fix it, the module's register cap (launch bounds of 4, 6 or 8 blocks per
+// SM): every candidate builds its module and runs the batch once; the
+// fastest launch wins.  The gradient module (elig given) is tuned the same
+// way.  Returns false when no candidate ran (the planner's defaults are
+// kept).
 static bool bsb_tune(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
                      cudaStream_t st, const DeviceInfo& dev, const std::vector<std::string>* elig,
-                     int* best_L, int* best_prune) {
+                     int* best_L, int* best_prune, int* best_occ) {
   double best_ms = 1e300;
   bool found = false;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -1045,41 +1051,32 @@ static bool bsb_tune(int G, const pbat_graph* graphs, int K, const double* p, co
     cudaGetLastError();
     return false;
   }
-  std::vector<pbat_options> cands;
-  for (int mode : (o.prune == 1 ? std::vector<int>{1, 2} : std::vector<int>{o.prune}))
-    for (int L = 3; L <= kBsbMaxWalk; ++L) {
-      pbat_options t = o;
-      t.walk_bits = L;
-      t.prune = mode;
-      t.time_budget_s = 0;
-      cands.push_back(t);
+  auto new_batch = [&](BsBatch& T) {
+    if (elig) {
+      T.grad = true;
+      T.elig = *elig;
     }
-  {
-    // the candidates' modules compile at once on host threads
+  };
+  // the candidates' modules compile at once on host threads
+  auto precompile = [&](const std::vector<pbat_options>& cands) {
     std::vector<std::string> srcs;
     for (const pbat_options& t : cands) {
       BsBatch T;
-      if (elig) {
-        T.grad = true;
-        T.elig = *elig;
-      }
+      new_batch(T);
       std::vector<unsigned long long> items;
       std::string src;
       if (bsb_source(T, G, graphs, K, t, items, src) == PBAT_OK) srcs.push_back(std::move(src));
       else clear_error();
     }
     jit_precompile(srcs, dev.cc_major * 10 + dev.cc_minor);
-  }
-  for (const pbat_options& t : cands) {
+  };
+  auto run = [&](const pbat_options& t) {
     BsBatch T;
-    if (elig) {
-      T.grad = true;
-      T.elig = *elig;
-    }
+    new_batch(T);
     if (bsb_build(T, G, graphs, K, t, dev) != PBAT_OK) {
       if (T.scr) scratch_release(T.scr);
       clear_error();
-      continue;
+      return;
     }
     bsb_tables(T, graphs, p);
     bool ok = cudaMemcpyAsync(T.scr->dmem, T.scr->hmem, T.o_upload_end, cudaMemcpyHostToDevice, st) ==
@@ -1091,6 +1088,7 @@ static bool bsb_tune(int G, const pbat_graph* graphs, int K, const double* p, co
       best_ms = ms;
       *best_L = t.walk_bits;
       *best_prune = t.prune;
+      *best_occ = t.occupancy;
       found = true;
     }
     if (!ok) {
@@ -1098,6 +1096,31 @@ static bool bsb_tune(int G, const pbat_graph* graphs, int K, const double* p, co
       clear_error();
     }
     scratch_release(T.scr);
+  };
+  std::vector<pbat_options> cands;
+  for (int mode : (o.prune == 1 ? std::vector<int>{1, 2} : std::vector<int>{o.prune}))
+    for (int L = 3; L <= kBsbMaxWalk; ++L) {
+      pbat_options t = o;
+      t.walk_bits = L;
+      t.prune = mode;
+      t.occupancy = o.occupancy > 0 ? o.occupancy : 0;
+      t.time_budget_s = 0;
+      cands.push_back(t);
+    }
+  precompile(cands);
+  for (const pbat_options& t : cands) run(t);
+  if (found && o.occupancy < 0) {
+    cands.clear();
+    for (int oc : {6, 8}) {
+      pbat_options t = o;
+      t.walk_bits = *best_L;
+      t.prune = *best_prune;
+      t.occupancy = oc;
+      t.time_budget_s = 0;
+      cands.push_back(t);
+    }
+    precompile(cands);
+    for (const pbat_options& t : cands) run(t);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -1126,10 +1149,11 @@ int run_batched_bs(int G, const pbat_graph* graphs, int K, const double* p, cons
   if (!E) {
     pbat_options ob = o;
     if (o.autotune && o.walk_bits < 0) {
-      int L = -1, mode = o.prune;
-      if (bsb_tune(G, graphs, K, p, o, st, dev, elig, &L, &mode)) {
+      int L = -1, mode = o.prune, occ = o.occupancy;
+      if (bsb_tune(G, graphs, K, p, o, st, dev, elig, &L, &mode, &occ)) {
         ob.walk_bits = L;
         ob.prune = mode;
+        ob.occupancy = occ;
       }
     }
     std::unique_ptr<BsBatch> ne(new BsBatch());

@@ -202,6 +202,17 @@ __device__ __forceinline__ u64 bs_list_task(const BsWork& W) {
   const u64 i = atomicAdd(W.counter2, 1ull);
   return i < *W.list_n ? W.list[i] : ~0ull;
 }
+// The walking launch: true (in every thread of the block) when no deferred
+// item is left for it -- the list is empty, or blocks that started earlier
+// have taken every ticket -- so the block returns before it stages tables or
+// clears accumulators (it would add nothing to the results).
+__device__ __forceinline__ bool bs_list_done(const BsWork& W) {
+  __shared__ int s_done;
+  if (threadIdx.x == 0)
+    s_done = *(volatile const u64*)W.counter2 >= *(volatile const u64*)W.list_n;
+  __syncthreads();
+  return s_done != 0;
+}
 
 // Phase 1: a warp collects its deferred items one per lane (entry j in lane
 // j) and appends them to the list 32 at a time, with one atomic per batch.
@@ -347,6 +358,9 @@ __device__ __forceinline__ void bs_kernel_body(const BsParams& P, const u64* __r
   facc* s_acc = (facc*)(s_bins + (BS_L + 1) * BS_NTHR);     // [warps]: each warp's R
   u64* s_nbins = (u64*)(s_acc + BS_NTHR / 32);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if constexpr (PHASE == 2) {
+    if (bs_list_done(W)) return;
+  }
   for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
   for (int i = tid; i < (1 << BS_L); i += BS_NTHR) s_wmid[i] = wmid_tab[i];
   for (int i = tid; i <= BS_M; i += BS_NTHR) s_nbins[i] = 0ull;
@@ -422,6 +436,8 @@ __device__ __forceinline__ void bs_kernel_body(const BsParams& P, const u64* __r
 #pragma unroll
         for (int b = 0; b < BS_IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
         const u32 c = bs_var(e, w) & BS_LANE_MASK;
+        // (branching on the word's class measured faster here than the
+        // fused kernel's branch-free form: a cut word costs no table loads)
         if (c == BS_LANE_MASK) {
           // every lane state connected: the lane mass is exactly 1
           const u64 wm = s_wmid[(gout << BS_IN) | (u32)r];
@@ -532,6 +548,9 @@ __device__ __forceinline__ void bs_kernel_grad_body(
   // per warp, in global scratch: R, then A_k and B_k of every arc k
   facc* g_acc = W.wacc + (size_t)blockIdx.x * (BS_NTHR / 32) * (1 + 2 * BS_M);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if constexpr (PHASE == 2) {
+    if (bs_list_done(W)) return;
+  }
   if constexpr (PHASE != 1) {
     for (int i = tid; i < 4 * 256; i += BS_NTHR) s_lt[i] = ((const ulonglong2*)lane_tab)[i];
     for (int i = tid; i < 4 * 256; i += BS_NTHR) s_tt[i] = thr_tab[i];
@@ -641,46 +660,39 @@ __device__ __forceinline__ void bs_kernel_grad_body(
         u32 w[BS_L > 0 ? BS_L : 1];
 #pragma unroll
         for (int b = 0; b < BS_OUT; ++b) w[BS_IN + b] = 0u - ((gout >> b) & 1u);
+        // the inner words' packed counts by inner popcount, in registers
+        u64 nb[BS_IN + 1];
+#pragma unroll
+        for (int j = 0; j <= BS_IN; ++j) nb[j] = 0ull;
 #pragma unroll
         for (int r = 0; r < (1 << BS_IN); ++r) {
 #pragma unroll
           for (int b = 0; b < BS_IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
           const u32 g = (gout << BS_IN) | (u32)r;
           const u32 c = bs_var(e, w) & BS_LANE_MASK;
+          const ulonglong2 wv = s_wm[g];
+          // no branch on the word's class: a cut word reads the zero
+          // entries, a connected one the mass of all its lanes
+          const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
+          const ulonglong2 t2 = s_lt[2 * 256 + ((c >> 16) & 0xffu)], t3 = s_lt[3 * 256 + (c >> 24)];
+          const u128 x = mul64x128_shr64(t0.x + t1.x + t2.x + t3.x, wv.x, wv.y);
+          u128_add(T, x.lo, x.hi);
+#pragma unroll
+          for (int b = 0; b < BS_IN; ++b)
+            if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
+          nb[__popc(r)] += t0.y + t1.y + t2.y + t3.y;
           // words that are all connected or all cut in every lane add the
           // same amount to every lane pattern: no lane-arc pair differs
-          const bool mixed = __any_sync(0xffffffffu, c != 0u && c != BS_LANE_MASK);
-          const u32 ct = mixed ? bs_transpose32(c, tr) : 0u;
-          const ulonglong2 wv = s_wm[g];
-          if (c == BS_LANE_MASK) {
-            // lane mass exactly 1: the walk mass at scale 2^125
-            const u128 x = u128{(wv.x >> 2) | (wv.y << 62), wv.y >> 2};
-            u128_add(T, x.lo, x.hi);
-#pragma unroll
-            for (int b = 0; b < BS_IN; ++b)
-              if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
-            bins[(pco + __popc(r)) * BS_NTHR] += BS_FULL_COUNTS;
-          } else if (c) {
-            const int pc = pco + __popc(r);
-            const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
-            const ulonglong2 t2 = s_lt[2 * 256 + ((c >> 16) & 0xffu)], t3 = s_lt[3 * 256 + (c >> 24)];
-            const u128 x = mul64x128_shr64(t0.x + t1.x + t2.x + t3.x, wv.x, wv.y);
-            u128_add(T, x.lo, x.hi);
-#pragma unroll
-            for (int b = 0; b < BS_IN; ++b)
-              if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
-            bins[pc * BS_NTHR] += t0.y + t1.y + t2.y + t3.y;
-          }
-          if (ct == BS_THR_MASK) {
-            // every thread pattern connected: thread mass exactly 1
-            u128_add(T2, (wv.x >> 2) | (wv.y << 62), wv.y >> 2);
-          } else if (ct) {
+          if (__any_sync(0xffffffffu, c != 0u && c != BS_LANE_MASK)) {
+            const u32 ct = bs_transpose32(c, tr);
             const u64 s2 = s_tt[ct & 0xffu] + s_tt[256 + ((ct >> 8) & 0xffu)] +
                            s_tt[512 + ((ct >> 16) & 0xffu)] + s_tt[768 + (ct >> 24)];
             const u128 x2 = mul64x128_shr64(s2, wv.x, wv.y);
             u128_add(T2, x2.lo, x2.hi);
           }
         }
+#pragma unroll
+        for (int j = 0; j <= BS_IN; ++j) bins[(pco + j) * BS_NTHR] += nb[j];
       }
 #pragma unroll
       for (int b = 0; b < BS_OUT; ++b)

@@ -248,7 +248,8 @@ def test_batched_bitsliced_against_oracle_odd_many_pvectors(pb):
     """The bit-sliced batched module against the oracle: 19 p-vectors (one
     full register chunk of 16 plus a ragged 3, and an odd count that leaves a
     zero padding column in the tables), networks from 12 to 18 arcs so that
-    items have walk arcs and prefix arcs, with and without the prune."""
+    items have walk arcs and prefix arcs, with and without the prune, and
+    with the module's registers capped for 8 blocks per SM."""
     nets, pvecs = [], []
     for i in range(5):
         rng = synth.SplitMix64(71 + i)
@@ -256,8 +257,9 @@ def test_batched_bitsliced_against_oracle_odd_many_pvectors(pb):
         nets.append(synth.random_small(950 + i, n=5 + rng.below(5), m=m, directed=bool(i & 1)))
         pvecs.append([synth.uniform_p(rng, m, 0.05, 0.95) for _ in range(19)])
     refs = [[oracle.enumerate_states(net, p=pvecs[g][k]) for k in range(19)] for g, net in enumerate(nets)]
-    for prune in (1, 0):
-        R, Nk, _ = pb.reliability_batched(nets, pvecs, opts=pb.options(algo=pb.ALGO_BITSLICE, prune=prune))
+    for prune, occ in ((1, 0), (0, 0), (1, 8)):
+        R, Nk, _ = pb.reliability_batched(nets, pvecs, opts=pb.options(algo=pb.ALGO_BITSLICE, prune=prune,
+                                                                       occupancy=occ))
         for g in range(len(nets)):
             assert Nk[g] == refs[g][0].Nk
             for k in range(19):
@@ -358,7 +360,7 @@ def test_prune_aware_plans_sampled_divisions(pb, make, bits, picks):
 # ---------------------------------------------------------------------------
 
 def _small_r_network(seed, n_chain=14, extra=4, p_lo=0.15, p_hi=0.35):
-    """A chain from source to sink with a few shortcuts: R around 1e-6..1e-9."""
+    """A chain from source to sink with a few shortcuts: R between about 1e-7 and 1e-4."""
     rng = synth.SplitMix64(seed)
     tail = list(range(n_chain))
     head = list(range(1, n_chain + 1))
@@ -462,6 +464,11 @@ def test_batched_gradient_against_oracle_odd_many_pvectors(pb):
     # the same batch without the gradient gives the same R and N_k
     R2, Nk2, _ = pb.reliability_batched(nets, pvecs)
     assert Nk2 == Nk and np.all(np.abs(R2 - R) <= 1e-13 * R)
+    # the gradient module with its registers capped for 6 blocks per SM
+    R3, Nk3, G3 = pb.reliability_batched(nets, pvecs, grad=True, opts=pb.options(occupancy=6))
+    assert Nk3 == Nk and np.all(np.abs(R3 - R) <= 1e-13 * R)
+    for g, net in enumerate(nets):
+        assert np.all(np.abs(np.asarray(G3[g]) - np.asarray(G[g])) <= 1e-14)
 
 
 def test_batched_workload_gradient_one_launch(pb):
