@@ -81,16 +81,16 @@ SHAPES = {
 # fraction is reported as null.
 COUNTS = {
     # 24 nodes, 40 arcs: fused (L 9, 256 threads, prune 2, occupancy 2, its two launches
-    # summed) and R-only (L 9, 128, 2, 0, one launch)
-    "2008dae66444650a": (13201992269 / 2**40, 1677312, "profiles/bs_kernel_grad_undirected24x40.md"),
-    "53d525b5025773de": (6498148066 / 2**40, 66560, "profiles/bs_kernel_undirected24x40.md"),
+    # summed) and R-only (L 9, 128, 2, 0, one launch; four walk arcs unrolled)
+    "00d38992d763996b": (12386754834 / 2**40, 1673984, "profiles/bs_kernel_grad_undirected24x40.md"),
+    "a021a477d8944536": (6160084890 / 2**40, 74752, "profiles/bs_kernel_undirected24x40.md"),
     # directed, 20 nodes, 34 arcs: fused (7, 192, 2, 0, two launches) and R-only
     # (7, 128, 2, 0, two launches)
-    "0a3efb3aeb28fa70": (21354355 / 2**34, 92928, "profiles/bs_kernel_grad_directed20x34.md"),
-    "1066b606e51cf77d": (14841156 / 2**34, 68352, "profiles/bs_kernel_directed20x34.md"),
+    "7d09cf933b462497": (21353958 / 2**34, 95488, "profiles/bs_kernel_grad_directed20x34.md"),
+    "b0bc19009b12eb72": (14841317 / 2**34, 75776, "profiles/bs_kernel_directed20x34.md"),
     # 3x6 grid: fused (5, 128, 1, 0, 1) and R-only (5, 64, 1, 0, 1)
-    "95fa0ca393eec59c": (17364783 / 2**27, 94464, "profiles/bs_kernel_grad_grid3x6.md"),
-    "360ccef42efbbdf4": (8547686 / 2**27, 44288, "profiles/bs_kernel_grid3x6.md"),
+    "5881f0af3582c2b5": (15927627 / 2**27, 93184, "profiles/bs_kernel_grad_grid3x6.md"),
+    "e1081d13bf43836a": (8232195 / 2**27, 47872, "profiles/bs_kernel_grid3x6.md"),
 }
 
 SM_COUNT = 152

@@ -88,8 +88,7 @@ typedef struct pbat_options {
                            0 = the compiler's own register choice; -1 (default) = 0, or
                            the autotuner's choice when it runs.  The bit-sliced batched
                            module takes it as its launch bounds (128 threads, k blocks;
-                           0 = 4 blocks), and its autotuner tries 4, 6 and 8 when it is
-                           -1.  Results do not depend on it. */
+                           0 and -1 = 4 blocks).  Results do not depend on it. */
   int launches;         /* bit-sliced single-network kernels with the prune on: 1 = one
                            launch; 2 = two launches, the first resolving what the prune can
                            and deferring the work items left to walk, the second walking

@@ -225,8 +225,14 @@ static bool acc_in_registers(const BsPlan& bp) { return bp.L <= 6 || bp.ops_var 
 // 106.5 -> 87.8 ms, 34-arc directed 541 -> 495 us) and to the fused kernel
 // when its accumulators are in registers (34-arc 1437 -> 1385 us), but the
 // fused kernel with a large program loses registers to them (40-arc 147.4 ->
-// 154 ms) and keeps two.
-static int walk_unroll_bits(const BsPlan& bp) { return !bp.grad || acc_in_registers(bp) ? 3 : 2; }
+// 154 ms) and keeps two.  The R kernel of a short program (at most 64
+// operations per word) takes four (prune-aware 40-arc plan, 27 operations:
+// 7.69 -> 7.45 ms); the fused kernel measured slower with four (18.7 -> 22.7
+// ms).
+static int walk_unroll_bits(const BsPlan& bp) {
+  if (!bp.grad) return bp.ops_var <= 64 ? 4 : 3;
+  return acc_in_registers(bp) ? 3 : 2;
+}
 
 static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
   char defs[700];
@@ -1033,13 +1039,14 @@ int bsb_source_for(int G, const pbat_graph* graphs, int K, const pbat_options& o
 }
 
 // The batch's walk length (split depth: each network's items are its
-// prefixes of d = m - 10 - L arcs), with the prune on its planning mode
-// (source/sink-near or prune-aware prefix arcs), then, unless the options
-// fix it, the module's register cap (launch bounds of 4, 6 or 8 blocks per
-// SM): every candidate builds its module and runs the batch once; the
-// fastest launch wins.  The gradient module (elig given) is tuned the same
-// way.  Returns false when no candidate ran (the planner's defaults are
-// kept).
+// prefixes of d = m - 10 - L arcs) and, with the prune on, its planning mode
+// (source/sink-near or prune-aware prefix arcs): every candidate builds its
+// module and runs the batch once; the fastest launch wins.  The gradient
+// module (elig given) is tuned the same way.  The register cap is not
+// tuned: on GB300 the 64-network workload ran fastest at the default launch
+// bounds of 4 blocks per SM (R module 5.42 ms; 3, 6 and 2 blocks: 5.61, 6.82
+// and 5.91 ms).  Returns false when no candidate ran (the planner's
+// defaults are kept).
 static bool bsb_tune(int G, const pbat_graph* graphs, int K, const double* p, const pbat_options& o,
                      cudaStream_t st, const DeviceInfo& dev, const std::vector<std::string>* elig,
                      int* best_L, int* best_prune, int* best_occ) {
@@ -1109,19 +1116,6 @@ static bool bsb_tune(int G, const pbat_graph* graphs, int K, const double* p, co
     }
   precompile(cands);
   for (const pbat_options& t : cands) run(t);
-  if (found && o.occupancy < 0) {
-    cands.clear();
-    for (int oc : {6, 8}) {
-      pbat_options t = o;
-      t.walk_bits = *best_L;
-      t.prune = *best_prune;
-      t.occupancy = oc;
-      t.time_budget_s = 0;
-      cands.push_back(t);
-    }
-    precompile(cands);
-    for (const pbat_options& t : cands) run(t);
-  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   return found;

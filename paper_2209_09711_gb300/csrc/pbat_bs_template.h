@@ -671,24 +671,33 @@ __device__ __forceinline__ void bs_kernel_grad_body(
           const u32 g = (gout << BS_IN) | (u32)r;
           const u32 c = bs_var(e, w) & BS_LANE_MASK;
           const ulonglong2 wv = s_wm[g];
-          // no branch on the word's class: a cut word reads the zero
-          // entries, a connected one the mass of all its lanes
-          const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
-          const ulonglong2 t2 = s_lt[2 * 256 + ((c >> 16) & 0xffu)], t3 = s_lt[3 * 256 + (c >> 24)];
-          const u128 x = mul64x128_shr64(t0.x + t1.x + t2.x + t3.x, wv.x, wv.y);
-          u128_add(T, x.lo, x.hi);
-#pragma unroll
-          for (int b = 0; b < BS_IN; ++b)
-            if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
-          nb[__popc(r)] += t0.y + t1.y + t2.y + t3.y;
-          // words that are all connected or all cut in every lane add the
-          // same amount to every lane pattern: no lane-arc pair differs
           if (__any_sync(0xffffffffu, c != 0u && c != BS_LANE_MASK)) {
+            // some word of the warp is partly connected: no branch on the
+            // word's class (a cut word reads the zero entries, a connected
+            // one the mass of all its lanes), and the lane transpose
+            const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
+            const ulonglong2 t2 = s_lt[2 * 256 + ((c >> 16) & 0xffu)], t3 = s_lt[3 * 256 + (c >> 24)];
+            const u128 x = mul64x128_shr64(t0.x + t1.x + t2.x + t3.x, wv.x, wv.y);
+            u128_add(T, x.lo, x.hi);
+#pragma unroll
+            for (int b = 0; b < BS_IN; ++b)
+              if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
+            nb[__popc(r)] += t0.y + t1.y + t2.y + t3.y;
             const u32 ct = bs_transpose32(c, tr);
             const u64 s2 = s_tt[ct & 0xffu] + s_tt[256 + ((ct >> 8) & 0xffu)] +
                            s_tt[512 + ((ct >> 16) & 0xffu)] + s_tt[768 + (ct >> 24)];
             const u128 x2 = mul64x128_shr64(s2, wv.x, wv.y);
             u128_add(T2, x2.lo, x2.hi);
+          } else if (c) {
+            // every word of the warp is cut or fully connected (no lane-arc
+            // pair differs): a connected word's lane mass is exactly 1, the
+            // walk mass at scale 2^125
+            const u128 x = u128{(wv.x >> 2) | (wv.y << 62), wv.y >> 2};
+            u128_add(T, x.lo, x.hi);
+#pragma unroll
+            for (int b = 0; b < BS_IN; ++b)
+              if ((r >> b) & 1) u128_add(Ain[b], x.lo, x.hi);
+            nb[__popc(r)] += BS_FULL_COUNTS;
           }
         }
 #pragma unroll
@@ -721,8 +730,10 @@ __device__ __forceinline__ void bs_kernel_grad_body(
       for (int b = 0; b < BS_L; ++b) {
         const u128 Ab = b < BS_IN ? Ain[b < BS_IN ? b : 0] : A[(b >= BS_IN ? b - BS_IN : 0) * BS_NTHR];
         const u128 sa = warp_sum_u128(mul64x128_shr64(thw, Ab.lo, Ab.hi));
-        const u128 z = u128_sub(T, Ab);
-        const u128 sz = warp_sum_u128(mul64x128_shr64(thw, z.lo, z.hi));
+        // the failed half: S - sa, the lanes' truncated products of T less
+        // those of A (each lane's difference is that of T - A, or one unit
+        // more, at scale 2^124; never negative)
+        const u128 sz = u128_sub(S, sa);
         if (lane == BS_WALK0 + b) { myX = sa; myY = sz; }
       }
     }
@@ -1226,8 +1237,7 @@ __device__ __forceinline__ void bsb_finish_grad(
       for (int b = 0; b < 5; ++b) {
         if (b >= L) break;
         const u128 sa = warp_sum_u128(mul64x128_shr64(thwk, Aw[b].lo, Aw[b].hi));
-        const u128 z = u128_sub(T, Aw[b]);
-        const u128 sz = warp_sum_u128(mul64x128_shr64(thwk, z.lo, z.hi));
+        const u128 sz = u128_sub(S, sa);   // the failed half, as in the fused kernel
         if (lane == ell + tb + b) { myX = sa; myY = sz; }
       }
     }

@@ -160,7 +160,8 @@ def test_every_template_variant_compiles_with_nvrtc(pb):
     """The generated source takes different template paths by shape: the
     fused kernel's accumulators in registers (short walks or small programs)
     or in global slots (long walks of large programs), two or three unrolled
-    walk arcs, and with or without thread arcs.  Each combination compiles."""
+    walk arcs (three or four in the R kernel), and with or without thread
+    arcs.  Each combination compiles."""
     seen = set()
     cases = [(synth.workload_grid_3x6(), 5), (synth.workload_directed_20_34(), 10),
              (synth.workload_random_24_40(), 10), (synth.workload_random_24_40(), 4),
@@ -174,7 +175,8 @@ def test_every_template_variant_compiles_with_nvrtc(pb):
             seen.add(key)
             _nvrtc_compile(src.split("\n", 1)[1])
     variants = {(dict(k)["BS_GRAD"], dict(k)["BS_ACC_REG"], dict(k)["BS_IN_BITS"]) for k in seen}
-    assert ("1", "0", "2") in variants and ("1", "1", "3") in variants and ("0", "1", "3") in variants
+    assert ("1", "0", "2") in variants and ("1", "1", "3") in variants
+    assert {v[2] for v in variants if v[0] == "0"} >= {"3", "4"}
 
 
 @pytest.mark.parametrize("prune", [1, 2])
