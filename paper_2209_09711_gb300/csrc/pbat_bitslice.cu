@@ -249,7 +249,16 @@ static std::string bs_source(const GraphIn& g, const BsPlan& bp, int nthr) {
            bp.pex);
   const std::string tmpl = kBsTemplate;
   const size_t cut = tmpl.find("//@@GENERATED@@");
-  return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tmpl.substr(cut);
+  // only this plan's kernel: the other kernel's section is left out, so that
+  // a change to one kernel leaves the other's generated source unchanged
+  std::string tail = tmpl.substr(cut);
+  const size_t r0 = tail.find("#if !BS_GRAD\n"), f0 = tail.find("#if BS_GRAD\n");
+  const size_t f1 = tail.rfind("#endif");
+  if (r0 != std::string::npos && f0 != std::string::npos && f1 != std::string::npos && r0 < f0 && f0 < f1) {
+    if (bp.grad) tail.erase(r0, f0 - r0);
+    else tail.erase(f0, f1 + 6 - f0);
+  }
+  return std::string(defs) + tmpl.substr(0, cut) + bp.gen + tail;
 }
 
 // Generated source for a network (no device needed); see pbat_kernel_source.

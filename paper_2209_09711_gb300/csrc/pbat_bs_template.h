@@ -194,10 +194,12 @@ struct BsWork {
 
 // Work items of a launch.  One-launch runs (phase 0) take items by the
 // atomic ticket over [0, n_tasks).  Two-launch runs: the first (phase 1)
-// visits every item with a fixed warp stride -- no ticket, the items it
-// keeps are short -- resolves what the prune can and defers the items left
-// to walk; the second (phase 2) takes the deferred items by a ticket over
-// the list.  ~0: no item left.
+// takes items 16 at a time by an atomic ticket (its items are short: one
+// ticket per item would pack 2^21 atomics on one counter into the launch,
+// and a fixed warp stride gave warps runs of alike items that end unevenly),
+// resolves what the prune can and defers the items left to walk; the second
+// (phase 2) takes the deferred items by a ticket over the list.  ~0: no item
+// left.
 __device__ __forceinline__ u64 bs_list_task(const BsWork& W) {
   const u64 i = atomicAdd(W.counter2, 1ull);
   return i < *W.list_n ? W.list[i] : ~0ull;
@@ -375,16 +377,20 @@ __device__ __forceinline__ void bs_kernel_body(const BsParams& P, const u64* __r
   u32 a[BS_M];
   bs_init_arcs(a, lane);
   constexpr int phase = PHASE;
-  const u64 n_warps = (u64)gridDim.x * (BS_NTHR / 32);
-  u64 stride_task = (u64)blockIdx.x * (BS_NTHR / 32) + warp;   // phase 1
+  u64 chunk_next = 0, chunk_end = 0;   // phase 1: this warp's chunk of items
   u64 pend = 0;   // phase 1: this warp's deferred items, entry j in lane j
   int npend = 0;
 
   for (;;) {
     u64 task = 0;
     if constexpr (phase == 1) {
-      task = stride_task;
-      stride_task += n_warps;
+      if (chunk_next == chunk_end) {   // the next 16 items, by one atomic ticket
+        u64 base = 0;
+        if (lane == 0) base = atomicAdd(W.counter, 16ull);
+        chunk_next = __shfl_sync(0xffffffffu, base, 0);
+        chunk_end = chunk_next + 16;
+      }
+      task = chunk_next++;
     }
     if (lane == 0) {
       if constexpr (phase == 2) task = bs_list_task(W);
@@ -436,14 +442,11 @@ __device__ __forceinline__ void bs_kernel_body(const BsParams& P, const u64* __r
 #pragma unroll
         for (int b = 0; b < BS_IN; ++b) w[b] = ((r >> b) & 1) ? ~0u : 0u;
         const u32 c = bs_var(e, w) & BS_LANE_MASK;
-        // (branching on the word's class measured faster here than the
-        // fused kernel's branch-free form: a cut word costs no table loads)
-        if (c == BS_LANE_MASK) {
-          // every lane state connected: the lane mass is exactly 1
-          const u64 wm = s_wmid[(gout << BS_IN) | (u32)r];
-          u128_add(T, wm << 62, wm >> 2);
-          bins[(pco + __popc(r)) * BS_NTHR] += BS_FULL_COUNTS;
-        } else if (c) {
+        // one warp vote, as in the fused kernel: when some word of the warp
+        // is partly connected every word reads its lane-table entries (a
+        // cut word the zero entries); otherwise each word is cut or fully
+        // connected
+        if (__any_sync(0xffffffffu, c != 0u && c != BS_LANE_MASK)) {
           const u32 g = (gout << BS_IN) | (u32)r;
           const int pc = pco + __popc(r);
           const ulonglong2 t0 = s_lt[0 * 256 + (c & 0xffu)], t1 = s_lt[1 * 256 + ((c >> 8) & 0xffu)];
@@ -452,6 +455,11 @@ __device__ __forceinline__ void bs_kernel_body(const BsParams& P, const u64* __r
           const u64 wm = s_wmid[g];
           u128_add(T, sR * wm, __umul64hi(sR, wm));
           bins[pc * BS_NTHR] += t0.y + t1.y + t2.y + t3.y;
+        } else if (c) {
+          // every lane state connected: the lane mass is exactly 1
+          const u64 wm = s_wmid[(gout << BS_IN) | (u32)r];
+          u128_add(T, wm << 62, wm >> 2);
+          bins[(pco + __popc(r)) * BS_NTHR] += BS_FULL_COUNTS;
         }
       }
     }
@@ -581,16 +589,20 @@ __device__ __forceinline__ void bs_kernel_grad_body(
   u32 a[BS_M];
   bs_init_arcs(a, lane);
   constexpr int phase = PHASE;
-  const u64 n_warps = (u64)gridDim.x * (BS_NTHR / 32);
-  u64 stride_task = (u64)blockIdx.x * (BS_NTHR / 32) + warp;   // phase 1
+  u64 chunk_next = 0, chunk_end = 0;   // phase 1: this warp's chunk of items
   u64 pend = 0;   // phase 1: this warp's deferred items, entry j in lane j
   int npend = 0;
 
   for (;;) {
     u64 task = 0;
     if constexpr (phase == 1) {
-      task = stride_task;
-      stride_task += n_warps;
+      if (chunk_next == chunk_end) {   // the next 16 items, by one atomic ticket
+        u64 base = 0;
+        if (lane == 0) base = atomicAdd(W.counter, 16ull);
+        chunk_next = __shfl_sync(0xffffffffu, base, 0);
+        chunk_end = chunk_next + 16;
+      }
+      task = chunk_next++;
     }
     if (lane == 0) {
       if constexpr (phase == 2) task = bs_list_task(W);

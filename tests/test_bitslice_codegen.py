@@ -156,6 +156,19 @@ def test_generated_sources_compile_with_nvrtc(pb):
     _nvrtc_compile(pb.batch_kernel_source(nets, 3))
 
 
+def test_generated_source_holds_only_its_own_kernel(pb):
+    """The R source carries no fused kernel and the fused source no R
+    kernel, so a change to one kernel's template leaves the other's source
+    (and the bench's instruction counts keyed by its hash) unchanged."""
+    net = synth.workload_random_24_40()
+    r_src = pb.kernel_source(net, grad=False)
+    g_src = pb.kernel_source(net, grad=True)
+    assert "bs_kernel_body" in r_src and "bs_kernel_grad_body" not in r_src
+    assert "bs_kernel_grad_body" in g_src and "bs_kernel_body" not in g_src
+    assert "extern \"C\" __global__ void KERNEL_BOUNDS bs_kernel(" in r_src
+    assert "extern \"C\" __global__ void KERNEL_BOUNDS bs_kernel_grad(" in g_src
+
+
 def test_every_template_variant_compiles_with_nvrtc(pb):
     """The generated source takes different template paths by shape: the
     fused kernel's accumulators in registers (short walks or small programs)
