@@ -82,15 +82,15 @@ SHAPES = {
 COUNTS = {
     # 24 nodes, 40 arcs: fused (L 9, 256 threads, prune 2, occupancy 2, its two launches
     # summed) and R-only (L 9, 128, 2, 0, one launch; four walk arcs unrolled)
-    "69707031e7be5c65": (12414532136 / 2**40, 1675264, "profiles/bs_kernel_grad_undirected24x40.md"),
-    "8a2a1c4b4ef23025": (5901937872 / 2**40, 75264, "profiles/bs_kernel_undirected24x40.md"),
+    "b080d3e5392bd6e0": (12414443516 / 2**40, 1675264, "profiles/bs_kernel_grad_undirected24x40.md"),
+    "0871ac197eac0d1d": (5902219352 / 2**40, 77568, "profiles/bs_kernel_undirected24x40.md"),
     # directed, 20 nodes, 34 arcs: fused (7, 192, 2, 0, two launches) and R-only
     # (7, 128, 2, 0, two launches)
-    "7fad6008d61e7777": (22180276 / 2**34, 90624, "profiles/bs_kernel_grad_directed20x34.md"),
-    "c76071e22d9eb24e": (16057500 / 2**34, 75264, "profiles/bs_kernel_directed20x34.md"),
+    "8dff10689adf9178": (22081741 / 2**34, 98304, "profiles/bs_kernel_grad_directed20x34.md"),
+    "fc32829a911d714a": (16006400 / 2**34, 74752, "profiles/bs_kernel_directed20x34.md"),
     # 3x6 grid: fused (5, 128, 1, 0, 1) and R-only (5, 64, 1, 0, 1)
-    "82c65182d3e2eee1": (15952783 / 2**27, 92416, "profiles/bs_kernel_grad_grid3x6.md"),
-    "3b21b37cbedf0a89": (8056887 / 2**27, 51200, "profiles/bs_kernel_grid3x6.md"),
+    "23c0191c742fbc75": (15952825 / 2**27, 91904, "profiles/bs_kernel_grad_grid3x6.md"),
+    "96d74f15c7df157a": (8078163 / 2**27, 51456, "profiles/bs_kernel_grid3x6.md"),
 }
 
 SM_COUNT = 152

@@ -194,12 +194,12 @@ struct BsWork {
 
 // Work items of a launch.  One-launch runs (phase 0) take items by the
 // atomic ticket over [0, n_tasks).  Two-launch runs: the first (phase 1)
-// takes items 16 at a time by an atomic ticket (its items are short: one
-// ticket per item would pack 2^21 atomics on one counter into the launch,
-// and a fixed warp stride gave warps runs of alike items that end unevenly),
-// resolves what the prune can and defers the items left to walk; the second
-// (phase 2) takes the deferred items by a ticket over the list.  ~0: no item
-// left.
+// takes items 16 at a time -- a warp's first 16 fixed by its index, the
+// rest by an atomic ticket (its items are short: one ticket per item would
+// pack 2^21 atomics on one counter into the launch, and a fixed warp stride
+// gave warps runs of alike items that end unevenly) -- resolves what the
+// prune can and defers the items left to walk; the second (phase 2) takes
+// the deferred items by a ticket over the list.  ~0: no item left.
 __device__ __forceinline__ u64 bs_list_task(const BsWork& W) {
   const u64 i = atomicAdd(W.counter2, 1ull);
   return i < *W.list_n ? W.list[i] : ~0ull;
@@ -377,7 +377,9 @@ __device__ __forceinline__ void bs_kernel_body(const BsParams& P, const u64* __r
   u32 a[BS_M];
   bs_init_arcs(a, lane);
   constexpr int phase = PHASE;
-  u64 chunk_next = 0, chunk_end = 0;   // phase 1: this warp's chunk of items
+  // phase 1: this warp's chunk of items -- its first chunk is its own (no
+  // ticket at the start of a short launch), the later ones come by ticket
+  u64 chunk_next = ((u64)blockIdx.x * (BS_NTHR / 32) + warp) * 16, chunk_end = chunk_next + 16;
   u64 pend = 0;   // phase 1: this warp's deferred items, entry j in lane j
   int npend = 0;
 
@@ -386,7 +388,7 @@ __device__ __forceinline__ void bs_kernel_body(const BsParams& P, const u64* __r
     if constexpr (phase == 1) {
       if (chunk_next == chunk_end) {   // the next 16 items, by one atomic ticket
         u64 base = 0;
-        if (lane == 0) base = atomicAdd(W.counter, 16ull);
+        if (lane == 0) base = (u64)gridDim.x * (BS_NTHR / 32) * 16 + atomicAdd(W.counter, 16ull);
         chunk_next = __shfl_sync(0xffffffffu, base, 0);
         chunk_end = chunk_next + 16;
       }
@@ -589,7 +591,9 @@ __device__ __forceinline__ void bs_kernel_grad_body(
   u32 a[BS_M];
   bs_init_arcs(a, lane);
   constexpr int phase = PHASE;
-  u64 chunk_next = 0, chunk_end = 0;   // phase 1: this warp's chunk of items
+  // phase 1: this warp's chunk of items -- its first chunk is its own (no
+  // ticket at the start of a short launch), the later ones come by ticket
+  u64 chunk_next = ((u64)blockIdx.x * (BS_NTHR / 32) + warp) * 16, chunk_end = chunk_next + 16;
   u64 pend = 0;   // phase 1: this warp's deferred items, entry j in lane j
   int npend = 0;
 
@@ -598,7 +602,7 @@ __device__ __forceinline__ void bs_kernel_grad_body(
     if constexpr (phase == 1) {
       if (chunk_next == chunk_end) {   // the next 16 items, by one atomic ticket
         u64 base = 0;
-        if (lane == 0) base = atomicAdd(W.counter, 16ull);
+        if (lane == 0) base = (u64)gridDim.x * (BS_NTHR / 32) * 16 + atomicAdd(W.counter, 16ull);
         chunk_next = __shfl_sync(0xffffffffu, base, 0);
         chunk_end = chunk_next + 16;
       }
