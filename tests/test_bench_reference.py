@@ -28,3 +28,25 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_pinned_shapes_have_instruction_counts():
+    """Every kernel the bench times at a pinned shape has an entry in
+    bench.COUNTS under the hash of the source the library generates for it
+    now, and the profile page named there exists and carries that hash: a
+    kernel changed since its capture would otherwise report a null roofline
+    fraction.  Source generation needs no GPU."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2209_09711_gb300 import build
+    build.build()
+    import paper_2209_09711_gb300 as pb
+    for name, kinds in bench.SHAPES.items():
+        net = bench.WORKLOADS[name]()
+        for kind in kinds:
+            key = bench.source_key(pb, net, bench.shape_opts(pb, name, kind), kind == "fused")
+            assert key in bench.COUNTS, (name, kind, key)
+            per_state, dram, page = bench.COUNTS[key]
+            assert 0 < per_state < 1 and dram > 0
+            with open(os.path.join(ROOT, page)) as f:
+                assert key in f.read(), (page, key)
