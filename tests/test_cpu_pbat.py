@@ -97,3 +97,53 @@ def test_bad_input_is_rejected():
     net = synth.bridge([0.9] * 5)
     with pytest.raises(ValueError):
         cpu_pbat.enumerate_divisions(net, 2, [4], 1)          # division out of range
+
+
+def _stored(name):
+    """R, N_k and per-arc T1, T0 stored in tests/golden/ by make_golden.py
+    (the oracle over every state), as exact rationals where they are sums."""
+    import os
+    from fractions import Fraction
+    rows = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"{name}_full.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                w = line.split()
+                rows.setdefault(w[0], []).append(w[1:])
+
+    def val(hi, lo):
+        return Fraction(float.fromhex(hi)) + Fraction(float.fromhex(lo))
+
+    m = len(rows["NK"][0]) - 1
+    T1, T0 = [Fraction(0)] * m, [Fraction(0)] * m
+    for i, hi, lo in rows["T1"]:
+        T1[int(i)] = val(hi, lo)
+    for i, hi, lo in rows["T0"]:
+        T0[int(i)] = val(hi, lo)
+    return float(val(*rows["R"][0])), [int(v) for v in rows["NK"][0]], T1, T0
+
+
+def _check_whole_against_stored(name, net):
+    import os
+    R, Nk, g = cpu_pbat.whole(net, os.cpu_count() or 1, grad=True)
+    R0, N0, T1, T0 = _stored(name)
+    assert Nk == N0
+    assert abs(R - R0) <= 1e-12 * R0
+    for i in range(net.m):
+        gstar = float(T1[i] - T0[i])
+        assert abs(g[i] - gstar) <= _grad_tol(gstar, float(T1[i]), float(T0[i])), (i, g[i], gstar)
+
+
+def test_whole_grid_against_stored_values():
+    """The baseline over all 2^27 states of the 3x6 grid reproduces the
+    stored oracle values: a second, independent program (FP64 Kahan sums,
+    binary-addition order, PLSA on bitmasks) against the long-double brute
+    force (a few seconds on 8 cores)."""
+    _check_whole_against_stored("grid-3x6", synth.workload_grid_3x6())
+
+
+@pytest.mark.skipif(__import__("os").environ.get("PBAT_FULL_CPU") != "1",
+                    reason="2^34 states: about 5 minutes on 8 cores; set PBAT_FULL_CPU=1")
+def test_whole_directed_34_against_stored_values():
+    """The same over all 2^34 states of the directed 34-arc workload."""
+    _check_whole_against_stored("random-directed-n20-m34", synth.workload_directed_20_34())
